@@ -1,0 +1,191 @@
+/*
+ * hmgb300 — H-LU of point-cloud kernel matrices on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library libhmgb300.so.  The operations follow Börm, Christophersen and
+ * Kriemann, "Semi-Automatic Task Graph Construction for H-Matrix Arithmetic"
+ * (arXiv 1911.07531):
+ *
+ *   hm_build   H-matrix of a kernel matrix over a cluster tree (Def 2.1) and block tree
+ *              (Def 2.2) with standard admissibility min(diam t, diam s) <= eta dist(t, s)
+ *              (§5.1); admissible leaves stored low-rank (Def 2.3).
+ *   hm_lu      H-LU factorization A = L U (Alg 2, with Alg 1 and Alg 3), executed as the
+ *              task graph built by semi-automatic refinement (§3.1, Alg 9-11): the graph's
+ *              longest-path levels run as waves of batched CUDA kernels.
+ *   hm_solve   forward / backward substitution with the H-LU factors (the solves of Alg 3
+ *              applied to vectors), optionally refined against A.
+ *   hm_matvec  y = alpha op(M) x + beta y for M = A, L, U, P L U, or the exact kernel matrix.
+ *
+ * Conventions
+ *   - Every function returns an int status: HM_OK (0) or a negative HM_E* code; the message
+ *     of the last failure on the calling thread is returned by hm_last_error().
+ *   - Vectors and right-hand sides are DEVICE pointers, column-major with leading dimension
+ *     `ld` (>= n), in the ORIGINAL point order; the library applies its cluster permutation.
+ *     Points passed to hm_build are a HOST array (n x 3, row-major, x y z).
+ *   - The caller owns every buffer it passes; handles (hm_ctx, hm_matrix, hm_factor,
+ *     hm_structure) are owned by the library and released with their *_free / *_destroy.
+ *     A factor keeps a pointer to its matrix: free the factor before the matrix.
+ *   - Device memory of the library comes from the context's allocator callbacks (e.g. the
+ *     PyTorch caching allocator); with NULL callbacks cudaMalloc / cudaFree are used.
+ *   - All work is enqueued on the context's stream. hm_build, hm_lu, hm_solve and
+ *     hm_matvec synchronize that stream before returning (they report device status).
+ *   - Arithmetic is FP64.  There is no CPU fallback: without a usable CUDA device every
+ *     computing call fails with HM_ECUDA.
+ */
+#ifndef HMGB300_H
+#define HMGB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HM_OK = 0,
+  HM_EINVAL = -1,     /* invalid argument (NULL handle, n < 1, ld < n, ...) */
+  HM_ENOMEM = -2,     /* the allocator returned NULL; no state was changed */
+  HM_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  HM_ESINGULAR = -4,  /* a zero pivot in a diagonal leaf LU (the factor is still returned) */
+  HM_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  HM_ENOTCONV = -6,   /* iterative refinement did not reach refine_tol */
+  HM_EINTERNAL = -7   /* planner invariant violated */
+};
+
+enum { HM_OP_A = 0, HM_OP_L = 1, HM_OP_U = 2, HM_OP_LU = 3, HM_OP_EXACT = 4 };
+
+typedef struct hm_ctx hm_ctx;
+typedef struct hm_matrix hm_matrix;
+typedef struct hm_factor hm_factor;
+typedef struct hm_structure hm_structure;
+
+/* Device allocator callbacks. alloc returns NULL on failure; free receives the size. */
+typedef void* (*hm_alloc_fn)(size_t bytes, void* user);
+typedef void (*hm_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+  int leaf_size;     /* clusters with at most leaf_size points are leaves (default 64)   */
+  double eta;        /* admissibility parameter (default 2.0)                           */
+  double eps;        /* relative truncation accuracy of admissible blocks (default 1e-6)*/
+  int rank_cap;      /* maximal rank of a low-rank block, 1..64 (default 64)            */
+  double kernel_h;   /* regularisation h of 1/(4 pi (r + h)); <= 0: mean NN spacing     */
+} hm_build_opts;
+
+typedef struct {
+  double eps;        /* relative accuracy of every rounded addition during H-LU (<=0: the
+                        matrix's eps); the rank cap is the matrix's                        */
+  int precision;     /* 0 = FP64 (only mode)                                              */
+} hm_lu_opts;
+
+typedef struct {
+  double refine_tol; /* > 0: iterate x += LU^{-1} (b - A x) until |b - A x| <= tol |b|     */
+  int max_iter;      /* refinement steps (0: plain substitution)                          */
+  int residual_op;   /* HM_OP_A (H-matrix) or HM_OP_EXACT (kernel evaluated on the fly)   */
+} hm_solve_opts;
+
+typedef struct {
+  int iterations;          /* refinement steps taken                                     */
+  double rel_residual;     /* |b - A x| / |b| after the last step (max over columns); -1
+                              when no residual was computed                              */
+} hm_solve_info;
+
+typedef struct {
+  int64_t n;
+  int64_t nclusters, nleaf_clusters, depth;
+  int64_t nleaves_dense, nleaves_lowrank;
+  int64_t value_bytes;          /* device bytes of the block values                      */
+  double h;                     /* kernel regularisation used                            */
+  double eps;
+  int64_t rank_cap;
+  int64_t max_rank, sum_rank;   /* over low-rank leaves                                  */
+  int64_t dag_nodes, dag_edges, dag_levels;   /* task graph (0 before the first hm_lu)  */
+  double dag_seconds;           /* host time of the task graph construction (Alg 11)     */
+  int64_t plan_launches, plan_phases, plan_truncations;
+  int64_t scratch_bytes;        /* device scratch of the H-LU plan                       */
+  double plan_seconds;          /* host time of wave planning                            */
+  double seconds;               /* device time of the last hm_build / hm_lu (CUDA events) */
+  double flops[5];              /* model flops of the last hm_lu: getrf, trsm, gemm,
+                                   rounded truncation (QR + core + SVD + rebuild), other */
+  int64_t rank_cap_hits;        /* rounded additions that hit the rank cap               */
+  int64_t singular_pivots;      /* zero pivots met in diagonal leaves                    */
+  int64_t aca_unconverged;      /* ACA runs that hit their rank limit during hm_build    */
+  double kind_ms[8];            /* with profiling on: device ms per kernel kind          */
+  int64_t kind_launches[8];     /*   getrf trsm gemm copy stack core eval aca            */
+} hm_stats;
+
+/* Last error message of the calling thread ("" if none). */
+const char* hm_last_error(void);
+
+/* Context: device ordinal, a cudaStream_t (NULL = the legacy default stream) and the
+ * allocator callbacks (both NULL = cudaMalloc / cudaFree). */
+int hm_ctx_create(int device, void* cuda_stream, hm_alloc_fn alloc, hm_free_fn free_fn, void* user,
+                  hm_ctx** out);
+void hm_ctx_destroy(hm_ctx* ctx);
+/* With profiling on, every kernel launch of hm_lu is bracketed by CUDA events and the
+ * per-kind device time is reported in hm_stats.kind_ms (adds host overhead). */
+int hm_ctx_set_profiling(hm_ctx* ctx, int enable);
+
+/* Build the H-matrix of a_ij = 1/(4 pi (|x_i - x_j| + h)) (Def 2.1-2.3, §5.1): cluster
+ * tree by geometric bisection, block tree, dense leaves evaluated on the device,
+ * admissible leaves by ACA with partial pivoting to eps/10 and rounded truncation to eps.
+ * points: host, n x 3 row-major (copied). opts: NULL for defaults. */
+int hm_build(hm_ctx* ctx, const double* points_xyz, int64_t n, const hm_build_opts* opts, hm_matrix** out);
+void hm_matrix_free(hm_matrix* A);
+
+/* H-LU factorization (Alg 2) of A executed as the Alg 11 task graph in waves. A is not
+ * modified; the factor holds L (unit lower, with leaf pivots) and U in H-format. */
+int hm_lu(hm_ctx* ctx, hm_matrix* A, const hm_lu_opts* opts, hm_factor** out);
+void hm_factor_free(hm_factor* F);
+
+/* x = (P L U)^{-1} b for nrhs right-hand sides (device, column-major, leading dimension
+ * ld, original order). b and x may alias. With opts->max_iter > 0 and A != NULL, iterative
+ * refinement against op(A) (opts->residual_op) runs until the relative residual of every
+ * column is <= refine_tol (HM_ENOTCONV if max_iter is reached first). info may be NULL. */
+int hm_solve(hm_ctx* ctx, hm_factor* F, hm_matrix* A, const double* b, double* x, int64_t nrhs, int64_t ld,
+             const hm_solve_opts* opts, hm_solve_info* info);
+
+/* y = alpha op(M) x + beta y. op: HM_OP_A (A, F may be NULL), HM_OP_L / HM_OP_U / HM_OP_LU
+ * (the factors of F), HM_OP_EXACT (the exact kernel matrix of A's points, n^2 kernel
+ * evaluations).  x, y device, column-major, original order; x and y must not alias. */
+int hm_matvec(hm_ctx* ctx, hm_matrix* A, hm_factor* F, int op, double alpha, const double* x, double beta,
+              double* y, int64_t nrhs, int64_t ld);
+
+int hm_matrix_stats(const hm_matrix* A, hm_stats* out);
+int hm_factor_stats(const hm_factor* F, hm_stats* out);
+
+/* Rounded truncation of W Z^T (W: m x K, Z: n x K, device, column-major, ld >= m / n) to
+ * relative spectral accuracy eps (keep sigma_i > eps sigma_1) and rank <= cap (<= 64):
+ * U (m x k) and V (n x k, orthonormal columns) with U V^T ~ W Z^T. K <= 256. *k_out
+ * (host) receives k. This is the kernel the H-LU applies to every low-rank update
+ * (the "truncation operation" of §2.3); device scratch comes from the context allocator. */
+int hm_truncate(hm_ctx* ctx, int64_t m, int64_t n, int K, const double* W, int64_t ldw, const double* Z,
+                int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V, int64_t ldv, int* k_out);
+
+/* ---- host-only structure (no GPU needed): cluster tree, block tree, task graph -------- */
+typedef struct {
+  int64_t n, nclusters, nleaves, ntasks, nedges, nlevels;
+  double dag_seconds;
+  int64_t plan_launches, plan_phases, plan_gemm_ops, plan_truncations, plan_scratch_bytes;
+} hm_structure_info;
+
+/* Cluster tree (Def 2.1), block tree (Def 2.2) and the H-LU task graph of Alg 11 with its
+ * longest-path levels. points: host n x 3. with_plan != 0 also runs the H-LU planner. */
+int hm_structure_build(const double* points_xyz, int64_t n, int leaf_size, double eta, int with_plan,
+                       hm_structure** out);
+int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
+/* Export (any pointer may be NULL):
+ *   perm[n]                 original index of each permuted position
+ *   clusters[nclusters*6]   lo, hi, son0, son1, level, parent (depth-first pre-order ids)
+ *   leaves[nleaves*3]       row cluster, col cluster, admissible (block-tree pre-order)
+ *   tasks[ntasks*4]         type (0 lu, 1 mul, 2 trsl, 3 trsu), c1, c2, c3 (-1 unused)
+ *   edges[nedges*2]         src, dst task indices
+ *   levels[ntasks]          longest-path level of each task */
+int hm_structure_export(const hm_structure* S, int64_t* perm, int32_t* clusters, int32_t* leaves,
+                        int32_t* tasks, int32_t* edges, int32_t* levels);
+void hm_structure_free(hm_structure* S);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMGB300_H */

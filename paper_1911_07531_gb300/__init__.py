@@ -1,0 +1,362 @@
+"""Python binding of libhmgb300 (H-LU of point-cloud kernel matrices on one GB300).
+
+Argument marshalling only: every call goes through the C ABI declared in
+``include/hmgb300.h`` and every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the caching allocator, through the allocator
+callbacks of the context) and streams.  There is no CPU fallback: if the shared library
+has not been built, importing works but the first call raises ``HMError``.
+
+Functions keep the C names (``hm_build``, ``hm_lu``, ``hm_solve``, ``hm_matvec``,
+``hm_truncate``, ``hm_structure_build`` ...).  Device vectors are torch tensors in
+column-major layout (1-D of length n, or 2-D with stride(0) == 1), in the original point
+order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB, build as _build_lib
+
+__all__ = [
+    "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
+    "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate",
+    "hm_structure_build", "header_functions",
+    "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
+]
+
+HM_OP_A, HM_OP_L, HM_OP_U, HM_OP_LU, HM_OP_EXACT = 0, 1, 2, 3, 4
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hmgb300.h")
+ERRORS = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ECUDA", -4: "HM_ESINGULAR",
+          -5: "HM_ETIMEOUT", -6: "HM_ENOTCONV", -7: "HM_EINTERNAL"}
+KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
+
+
+class HMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("eta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("rank_cap", ctypes.c_int), ("kernel_h", ctypes.c_double)]
+
+
+class LuOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("refine_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("residual_op", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nclusters", ctypes.c_int64), ("nleaf_clusters", ctypes.c_int64),
+                ("depth", ctypes.c_int64), ("nleaves_dense", ctypes.c_int64),
+                ("nleaves_lowrank", ctypes.c_int64), ("value_bytes", ctypes.c_int64), ("h", ctypes.c_double),
+                ("eps", ctypes.c_double), ("rank_cap", ctypes.c_int64), ("max_rank", ctypes.c_int64),
+                ("sum_rank", ctypes.c_int64), ("dag_nodes", ctypes.c_int64), ("dag_edges", ctypes.c_int64),
+                ("dag_levels", ctypes.c_int64), ("dag_seconds", ctypes.c_double),
+                ("plan_launches", ctypes.c_int64), ("plan_phases", ctypes.c_int64),
+                ("plan_truncations", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+                ("plan_seconds", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("flops", ctypes.c_double * 5), ("rank_cap_hits", ctypes.c_int64),
+                ("singular_pivots", ctypes.c_int64), ("aca_unconverged", ctypes.c_int64),
+                ("kind_ms", ctypes.c_double * 8), ("kind_launches", ctypes.c_int64 * 8)]
+
+    def to_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class StructureInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nclusters", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("ntasks", ctypes.c_int64), ("nedges", ctypes.c_int64), ("nlevels", ctypes.c_int64),
+                ("dag_seconds", ctypes.c_double), ("plan_launches", ctypes.c_int64),
+                ("plan_phases", ctypes.c_int64), ("plan_gemm_ops", ctypes.c_int64),
+                ("plan_truncations", ctypes.c_int64), ("plan_scratch_bytes", ctypes.c_int64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+_lib = None
+
+
+def build_library(verbose: bool = False, force: bool = False) -> str:
+    return _build_lib(verbose=verbose, force=force)
+
+
+def header_functions():
+    """Names of the functions ``include/hmgb300.h`` declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(hm_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def load_library():
+    """Load libhmgb300.so (raises HMError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise HMError(-3, f"{LIB} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB)
+    P, I, I64, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, None
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "hm_last_error": ([], ctypes.c_char_p),
+        "hm_ctx_create": ([I, P, ALLOC_FN, FREE_FN, P, PP], I),
+        "hm_ctx_destroy": ([P], V),
+        "hm_ctx_set_profiling": ([P, I], I),
+        "hm_build": ([P, P, I64, ctypes.POINTER(BuildOpts), PP], I),
+        "hm_matrix_free": ([P], V),
+        "hm_lu": ([P, P, ctypes.POINTER(LuOpts), PP], I),
+        "hm_factor_free": ([P], V),
+        "hm_solve": ([P, P, P, P, P, I64, I64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)], I),
+        "hm_matvec": ([P, P, P, I, D, P, D, P, I64, I64], I),
+        "hm_matrix_stats": ([P, ctypes.POINTER(Stats)], I),
+        "hm_factor_stats": ([P, ctypes.POINTER(Stats)], I),
+        "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
+        "hm_structure_build": ([P, I64, I, D, I, PP], I),
+        "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
+        "hm_structure_export": ([P, P, P, P, P, P, P], I),
+        "hm_structure_free": ([P], V),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc, what=""):
+    if rc != 0:
+        msg = load_library().hm_last_error().decode()
+        raise HMError(rc, msg or what)
+
+
+def _col_major(t, n, name):
+    """(pointer, nrhs, ld) of a column-major torch tensor of n rows."""
+    if t.dtype.is_floating_point and t.element_size() != 8:
+        raise TypeError(f"{name} must be float64")
+    if t.dim() == 1:
+        if t.shape[0] != n or t.stride(0) != 1:
+            raise ValueError(f"{name}: expected a contiguous vector of length {n}")
+        return t.data_ptr(), 1, n
+    if t.dim() != 2 or t.shape[0] != n or (t.shape[1] > 1 and t.stride(0) != 1):
+        raise ValueError(f"{name}: expected an n x nrhs column-major tensor (stride(0) == 1)")
+    ld = t.stride(1) if t.shape[1] > 1 else n
+    return t.data_ptr(), t.shape[1], ld
+
+
+# --------------------------------------------------------------------------- thin C-named API
+class HMContext:
+    """hm_ctx with the PyTorch caching allocator and a torch stream."""
+
+    def __init__(self, device=0, stream=None, torch_allocator=True):
+        import torch
+        L = load_library()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._torch = torch
+        if torch_allocator:
+            dev, st = self.device, self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:   # out of memory -> NULL -> HM_ENOMEM
+                    return None
+
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._af, self._ff = ALLOC_FN(_alloc), FREE_FN(_free)
+        else:
+            self._af, self._ff = ALLOC_FN(), FREE_FN()
+        h = ctypes.c_void_p()
+        _check(L.hm_ctx_create(self.device, ctypes.c_void_p(self.stream.cuda_stream), self._af, self._ff, None,
+                               ctypes.byref(h)), "hm_ctx_create")
+        self.handle = h
+
+    def set_profiling(self, on: bool):
+        _check(load_library().hm_ctx_set_profiling(self.handle, int(bool(on))))
+
+    def close(self):
+        if self.handle:
+            load_library().hm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hm_ctx_create(device=0, stream=None):
+    return HMContext(device, stream)
+
+
+class HMatrix:
+    def __init__(self, ctx, handle, n):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def stats(self):
+        s = Stats()
+        _check(load_library().hm_matrix_stats(self.handle, ctypes.byref(s)))
+        return s.to_dict()
+
+    def free(self):
+        if self.handle:
+            load_library().hm_matrix_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class HFactor:
+    def __init__(self, ctx, handle, A):
+        self.ctx, self.handle, self.A = ctx, handle, A
+
+    def stats(self):
+        s = Stats()
+        _check(load_library().hm_factor_stats(self.handle, ctypes.byref(s)))
+        return s.to_dict()
+
+    def free(self):
+        if self.handle:
+            load_library().hm_factor_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h=-1.0):
+    """H-matrix of a_ij = 1/(4 pi (|x_i - x_j| + h)) for host points (n x 3 float64)."""
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    if p.ndim != 2 or p.shape[1] != 3:
+        raise ValueError("points must be n x 3")
+    o = BuildOpts(int(leaf_size), float(eta), float(eps), int(rank_cap), float(kernel_h))
+    h = ctypes.c_void_p()
+    _check(load_library().hm_build(ctx.handle, p.ctypes.data, p.shape[0], ctypes.byref(o), ctypes.byref(h)))
+    return HMatrix(ctx, h, p.shape[0])
+
+
+def hm_lu(ctx, A, eps=0.0, allow_singular=False):
+    o = LuOpts(float(eps), 0)
+    h = ctypes.c_void_p()
+    rc = load_library().hm_lu(ctx.handle, A.handle, ctypes.byref(o), ctypes.byref(h))
+    F = HFactor(ctx, h, A) if h.value else None
+    if rc != 0 and not (rc == -4 and allow_singular and F is not None):
+        if F is not None:
+            F.free()
+        _check(rc)
+    return F
+
+
+def hm_solve(ctx, F, b, x=None, A=None, refine_tol=0.0, max_iter=0, residual_op=HM_OP_A):
+    """x = (P L U)^{-1} b (device tensors); optional refinement against op(A)."""
+    n = F.A.n
+    if x is None:
+        x = ctx._torch.empty_like(b)
+    pb, nb, ldb = _col_major(b, n, "b")
+    px, nx, ldx = _col_major(x, n, "x")
+    if nb != nx or ldb != ldx:
+        raise ValueError("b and x must have the same shape and leading dimension")
+    o = SolveOpts(float(refine_tol), int(max_iter), int(residual_op))
+    info = SolveInfo()
+    _check(load_library().hm_solve(ctx.handle, F.handle, A.handle if A is not None else None, pb, px, nb, ldb,
+                                   ctypes.byref(o), ctypes.byref(info)))
+    return x, {"iterations": info.iterations, "rel_residual": info.rel_residual}
+
+
+def hm_matvec(ctx, A, op, x, y=None, alpha=1.0, beta=0.0, F=None):
+    n = A.n
+    if y is None:
+        y = ctx._torch.zeros_like(x)
+    px, nx, ldx = _col_major(x, n, "x")
+    py, ny, ldy = _col_major(y, n, "y")
+    if nx != ny or ldx != ldy:
+        raise ValueError("x and y must have the same shape and leading dimension")
+    _check(load_library().hm_matvec(ctx.handle, A.handle, F.handle if F is not None else None, int(op),
+                                    float(alpha), px, float(beta), py, nx, ldx))
+    return y
+
+
+def hm_truncate(ctx, W, Z, eps, cap=64):
+    """Rounded truncation of W Z^T (device tensors, column-major m x K and n x K)."""
+    torch = ctx._torch
+    m, K = W.shape
+    n = Z.shape[0]
+    if Z.shape[1] != K:
+        raise ValueError("W and Z need the same number of columns")
+    Wf = W.t().contiguous().t() if K > 1 else W.contiguous()
+    Zf = Z.t().contiguous().t() if K > 1 else Z.contiguous()
+    kc = min(cap, m, n)
+    U = torch.empty((kc, m), dtype=torch.float64, device=W.device).t()
+    V = torch.empty((kc, n), dtype=torch.float64, device=W.device).t()
+    k = ctypes.c_int(0)
+    _check(load_library().hm_truncate(ctx.handle, m, n, K, Wf.data_ptr(), m, Zf.data_ptr(), n, float(eps), int(cap),
+                                      U.data_ptr(), m, V.data_ptr(), n, ctypes.byref(k)))
+    return U[:, :k.value], V[:, :k.value]
+
+
+class Structure:
+    """Host-only cluster tree, block tree and H-LU task graph (no GPU needed)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = StructureInfo()
+        _check(load_library().hm_structure_info_get(handle, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in info._fields_}
+
+    def export(self):
+        i = self.info
+        perm = np.empty(i["n"], dtype=np.int64)
+        cl = np.empty((i["nclusters"], 6), dtype=np.int32)
+        lv = np.empty((i["nleaves"], 3), dtype=np.int32)
+        tasks = np.empty((i["ntasks"], 4), dtype=np.int32)
+        edges = np.empty((max(i["nedges"], 1), 2), dtype=np.int32)
+        levels = np.empty(i["ntasks"], dtype=np.int32)
+        _check(load_library().hm_structure_export(self.handle, perm.ctypes.data, cl.ctypes.data, lv.ctypes.data,
+                                                  tasks.ctypes.data, edges.ctypes.data, levels.ctypes.data))
+        return dict(perm=perm, clusters=cl, leaves=lv, tasks=tasks, edges=edges[: i["nedges"]], levels=levels)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load_library().hm_structure_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def hm_structure_build(points, leaf_size=64, eta=2.0, with_plan=False):
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load_library().hm_structure_build(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
+                                             int(bool(with_plan)), ctypes.byref(h)))
+    return Structure(h)

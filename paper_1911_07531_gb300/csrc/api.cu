@@ -1,0 +1,1007 @@
+// C ABI of libhmgb300 (see include/hmgb300.h): context, H-matrix build, H-LU, solve,
+// matvec, standalone rounded truncation, and the host-only structure export.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/hmgb300.h"
+#include "kernels.h"
+#include "plan.h"
+#include "structure.h"
+
+using namespace hm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct hm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  hm_alloc_fn af = nullptr;
+  hm_free_fn ff = nullptr;
+  void* user = nullptr;
+  bool profiling = false;
+};
+
+namespace {
+
+bool dalloc(hm_ctx* c, Buf& b, size_t bytes) {
+  b.bytes = bytes < 256 ? 256 : bytes;
+  if (c->af) {
+    b.p = c->af(b.bytes, c->user);
+  } else {
+    if (cudaMalloc(&b.p, b.bytes) != cudaSuccess) b.p = nullptr;
+  }
+  if (!b.p) b.bytes = 0;
+  return b.p != nullptr;
+}
+
+void dfree(hm_ctx* c, Buf& b) {
+  if (!b.p) return;
+  if (c->ff) c->ff(b.p, b.bytes, c->user);
+  else cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+#define CU(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(HM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevPlan {
+  Plan host;
+  Buf ops[NKIND];
+  Buf entries;
+  bool uploaded = false;
+  double eps = -1.0;
+  double plan_seconds = 0.0;
+};
+
+size_t op_size(int kind) {
+  switch (kind) {
+    case K_GETRF: return sizeof(GetrfOp);
+    case K_TRSM: return sizeof(TrsmOp);
+    case K_GEMM: return sizeof(GemmOp);
+    case K_COPY: return sizeof(CopyOp);
+    case K_STACK:
+    case K_CORE: return sizeof(TruncOp);
+    case K_EVAL: return sizeof(EvalOp);
+    default: return sizeof(AcaOp);
+  }
+}
+
+template <class T>
+int upload_vec(hm_ctx* c, Buf& b, const std::vector<T>& v) {
+  if (v.empty()) return HM_OK;
+  if (!dalloc(c, b, v.size() * sizeof(T))) return fail(HM_ENOMEM, "allocator returned NULL (plan upload)");
+  CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return HM_OK;
+}
+
+int upload(hm_ctx* c, DevPlan& dp) {
+  if (dp.uploaded) return HM_OK;
+  int rc;
+  if ((rc = upload_vec(c, dp.ops[K_GETRF], dp.host.getrf))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_TRSM], dp.host.trsm))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_GEMM], dp.host.gemm))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_COPY], dp.host.copy))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_STACK], dp.host.trunc))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_EVAL], dp.host.eval))) return rc;
+  if ((rc = upload_vec(c, dp.ops[K_ACA], dp.host.aca))) return rc;
+  if ((rc = upload_vec(c, dp.entries, dp.host.entries))) return rc;
+  CU(cudaStreamSynchronize(c->stream));
+  dp.uploaded = true;
+  return HM_OK;
+}
+
+void free_plan(hm_ctx* c, DevPlan& dp) {
+  for (int k = 0; k < NKIND; ++k) dfree(c, dp.ops[k]);
+  dfree(c, dp.entries);
+  dp.uploaded = false;
+}
+
+struct Profile {
+  double ms[NKIND] = {0};
+  int64_t launches[NKIND] = {0};
+};
+
+int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof) {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> evkind;
+  for (const Launch& L : dp.host.launches) {
+    const int buf = L.kind == K_CORE ? K_STACK : L.kind;
+    const char* base = (const char*)dp.ops[buf].p;
+    const void* ops = base + (size_t)L.begin * op_size(L.kind);
+    if (prof) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, c->stream);
+      ev.push_back(a);
+      ev.push_back(b);
+      evkind.push_back(L.kind);
+    }
+    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, c->stream);
+    if (e != cudaSuccess) return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (prof) cudaEventRecord(ev.back(), c->stream);
+  }
+  if (prof) {
+    CU(cudaStreamSynchronize(c->stream));
+    for (size_t q = 0; q < evkind.size(); ++q) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
+      prof->ms[evkind[q]] += ms;
+      prof->launches[evkind[q]] += 1;
+      cudaEventDestroy(ev[2 * q]);
+      cudaEventDestroy(ev[2 * q + 1]);
+    }
+  }
+  return HM_OK;
+}
+
+}  // namespace
+
+struct hm_matrix {
+  hm_ctx* ctx = nullptr;
+  int64_t n = 0;
+  hm_build_opts opts{};
+  double h = 0.0;
+  ClusterTree ct;
+  BlockTree bt;
+  Layout lay;
+  Buf perm, pts, pts_orig, vals, ranks;
+  TaskGraph dag;
+  bool dag_built = false;
+  DevPlan lu_plan;
+  DevPlan mv_plan;
+  Buf mv_work;
+  double build_seconds = 0.0;
+  int64_t aca_unconverged = 0;
+};
+
+struct hm_factor {
+  hm_ctx* ctx = nullptr;
+  hm_matrix* A = nullptr;
+  double eps = 0.0;
+  Buf vals, ranks, piv;
+  DevPlan solve_plan;
+  DevPlan mv_plan;
+  Buf work;   // SP_X buffer of the solve / matvec plans
+  hm_stats st{};
+};
+
+namespace {
+
+constexpr int SOLVE_CHUNK = 32;
+
+void fill_matrix_stats(const hm_matrix* A, hm_stats* s) {
+  std::memset(s, 0, sizeof(*s));
+  s->n = A->n;
+  s->nclusters = (int64_t)A->ct.cl.size();
+  for (const Cluster& c : A->ct.cl) s->nleaf_clusters += c.leaf() ? 1 : 0;
+  s->depth = A->ct.depth;
+  for (const LeafStore& L : A->lay.leaf) {
+    if (L.lr) s->nleaves_lowrank++;
+    else s->nleaves_dense++;
+  }
+  s->value_bytes = A->lay.nvalues * 8;
+  s->h = A->h;
+  s->eps = A->opts.eps;
+  s->rank_cap = A->opts.rank_cap;
+  s->dag_nodes = (int64_t)A->dag.nodes.size();
+  s->dag_edges = (int64_t)A->dag.edges.size();
+  s->dag_levels = A->dag.nlevels;
+  s->dag_seconds = A->dag.build_seconds;
+  s->plan_launches = (int64_t)A->lu_plan.host.launches.size();
+  s->plan_phases = A->lu_plan.host.nphases;
+  s->plan_truncations = A->lu_plan.host.ntrunc;
+  s->scratch_bytes = A->lu_plan.host.scratch_doubles * 8 + A->lu_plan.host.scratch_ints * 4;
+  s->plan_seconds = A->lu_plan.plan_seconds;
+  s->seconds = A->build_seconds;
+  s->aca_unconverged = A->aca_unconverged;
+}
+
+int read_ranks(hm_ctx* c, const Buf& ranks, int nr, int64_t* maxr, int64_t* sumr) {
+  std::vector<int> r(nr);
+  if (nr) CU(cudaMemcpyAsync(r.data(), ranks.p, nr * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *maxr = 0;
+  *sumr = 0;
+  for (int v : r) {
+    *maxr = std::max<int64_t>(*maxr, v);
+    *sumr += v;
+  }
+  return HM_OK;
+}
+
+struct Counters {
+  Buf b;   // NFC unsigned long long + 4 ints
+  unsigned long long* flops() { return (unsigned long long*)b.p; }
+  int* status() { return (int*)((char*)b.p + NFC * sizeof(unsigned long long)); }
+};
+
+int counters_init(hm_ctx* c, Counters& k) {
+  if (!dalloc(c, k.b, NFC * sizeof(unsigned long long) + 4 * sizeof(int)))
+    return fail(HM_ENOMEM, "allocator returned NULL (counters)");
+  CU(cudaMemsetAsync(k.b.p, 0, NFC * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
+  return HM_OK;
+}
+
+int counters_read(hm_ctx* c, Counters& k, unsigned long long* fl, int* st) {
+  CU(cudaMemcpyAsync(fl, k.b.p, NFC * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(st, k.status(), 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HM_OK;
+}
+
+Bases make_bases() {
+  Bases B;
+  std::memset(&B, 0, sizeof(B));
+  return B;
+}
+
+}  // namespace
+
+// ====================================================================================== ABI
+extern "C" {
+
+const char* hm_last_error(void) { return g_err.c_str(); }
+
+int hm_ctx_create(int device, void* stream, hm_alloc_fn af, hm_free_fn ff, void* user, hm_ctx** out) {
+  if (!out) return fail(HM_EINVAL, "hm_ctx_create: out is NULL");
+  if ((af == nullptr) != (ff == nullptr)) return fail(HM_EINVAL, "hm_ctx_create: give both allocator callbacks or none");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev <= 0) return fail(HM_ECUDA, "hm_ctx_create: no CUDA device available");
+  if (device < 0 || device >= ndev) return fail(HM_EINVAL, "hm_ctx_create: bad device ordinal");
+  CU(cudaSetDevice(device));
+  hm_ctx* c = new hm_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  c->af = af;
+  c->ff = ff;
+  c->user = user;
+  *out = c;
+  return HM_OK;
+}
+
+void hm_ctx_destroy(hm_ctx* c) { delete c; }
+
+int hm_ctx_set_profiling(hm_ctx* c, int enable) {
+  if (!c) return fail(HM_EINVAL, "hm_ctx_set_profiling: NULL context");
+  c->profiling = enable != 0;
+  return HM_OK;
+}
+
+// ------------------------------------------------------------------------------ build
+int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm_matrix** out) {
+  if (!c || !pts || !out) return fail(HM_EINVAL, "hm_build: NULL argument");
+  if (n < 1 || n > (int64_t)1 << 30) return fail(HM_EINVAL, "hm_build: n out of range");
+  hm_build_opts opts{64, 2.0, 1e-6, 64, -1.0};
+  if (o) opts = *o;
+  if (opts.leaf_size < 1 || opts.leaf_size > 64) return fail(HM_EINVAL, "hm_build: leaf_size must be in 1..64");
+  if (!(opts.eta >= 0.0)) return fail(HM_EINVAL, "hm_build: eta must be >= 0");
+  if (!(opts.eps > 0.0) || opts.eps >= 1.0) return fail(HM_EINVAL, "hm_build: eps must be in (0, 1)");
+  if (opts.rank_cap < 1 || opts.rank_cap > 64) return fail(HM_EINVAL, "hm_build: rank_cap must be in 1..64");
+  CU(cudaSetDevice(c->device));
+  auto A = std::make_unique<hm_matrix>();
+  A->ctx = c;
+  A->n = n;
+  A->opts = opts;
+  try {
+    build_cluster_tree(pts, n, opts.leaf_size, A->ct);
+    build_block_tree(A->ct, opts.eta, A->bt);
+    build_layout(A->ct, A->bt, opts.rank_cap, A->lay);
+  } catch (const std::exception& ex) {
+    return fail(HM_EINTERNAL, std::string("hm_build: ") + ex.what());
+  }
+  auto cleanup = [&](int rc) {
+    dfree(c, A->perm);
+    dfree(c, A->pts);
+    dfree(c, A->pts_orig);
+    dfree(c, A->vals);
+    dfree(c, A->ranks);
+    return rc;
+  };
+  if (!dalloc(c, A->perm, n * sizeof(int64_t)) || !dalloc(c, A->pts, n * 3 * sizeof(double)) ||
+      !dalloc(c, A->pts_orig, n * 3 * sizeof(double)) || !dalloc(c, A->vals, A->lay.nvalues * sizeof(double)) ||
+      !dalloc(c, A->ranks, std::max(1, A->lay.nranks) * sizeof(int)))
+    return cleanup(fail(HM_ENOMEM, "hm_build: allocator returned NULL"));
+  cudaStream_t s = c->stream;
+  int rc = HM_OK;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  do {
+    if (cudaMemcpyAsync(A->perm.p, A->ct.perm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(A->pts_orig.p, pts, n * 3 * sizeof(double), cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(A->ranks.p, 0, std::max(1, A->lay.nranks) * sizeof(int), s)) {
+      rc = fail(HM_ECUDA, "hm_build: copy of the inputs failed");
+      break;
+    }
+    cudaEventRecord(e0, s);
+    if (launch_permute_points((double*)A->pts_orig.p, (int64_t*)A->perm.p, (int)n, (double*)A->pts.p, s)) {
+      rc = fail(HM_ECUDA, "hm_build: permute kernel failed");
+      break;
+    }
+    // h = mean nearest-neighbour distance (deterministic host sum of device minima)
+    if (opts.kernel_h > 0.0) {
+      A->h = opts.kernel_h;
+    } else if (n == 1) {
+      A->h = 1.0;
+    } else {
+      Buf nn;
+      if (!dalloc(c, nn, n * sizeof(double))) {
+        rc = fail(HM_ENOMEM, "hm_build: allocator returned NULL");
+        break;
+      }
+      std::vector<double> d2(n);
+      cudaError_t e = launch_nn2((double*)A->pts_orig.p, (int)n, (double*)nn.p, s);
+      if (!e) e = cudaMemcpyAsync(d2.data(), nn.p, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (!e) e = cudaStreamSynchronize(s);
+      dfree(c, nn);
+      if (e) {
+        rc = fail(HM_ECUDA, std::string("hm_build: nearest-neighbour kernel: ") + cudaGetErrorString(e));
+        break;
+      }
+      double sum = 0.0;
+      for (int64_t i = 0; i < n; ++i) sum += std::sqrt(d2[i]);
+      A->h = sum / (double)n;
+      if (!(A->h > 0.0)) A->h = 1.0;
+    }
+    // dense leaves by evaluation; admissible leaves by ACA + rounded truncation
+    DevPlan dp;
+    try {
+      plan_build(A->ct, A->bt, A->lay, opts.eps, 160, (int64_t)1 << 28, dp.host);
+    } catch (const std::exception& ex) {
+      rc = fail(HM_EINTERNAL, std::string("hm_build: ") + ex.what());
+      break;
+    }
+    if ((rc = upload(c, dp)) != HM_OK) {
+      free_plan(c, dp);
+      break;
+    }
+    Buf sd, si;
+    Counters k;
+    if (!dalloc(c, sd, std::max<int64_t>(1, dp.host.scratch_doubles) * 8) ||
+        !dalloc(c, si, std::max<int64_t>(1, dp.host.scratch_ints) * 4)) {
+      dfree(c, sd);
+      free_plan(c, dp);
+      rc = fail(HM_ENOMEM, "hm_build: allocator returned NULL (scratch)");
+      break;
+    }
+    if ((rc = counters_init(c, k)) != HM_OK) {
+      dfree(c, sd);
+      dfree(c, si);
+      free_plan(c, dp);
+      break;
+    }
+    Bases B = make_bases();
+    B.d[SP_A] = (double*)A->vals.p;
+    B.d[SP_S] = (double*)sd.p;
+    B.d[SP_P] = (double*)A->pts.p;
+    B.i[IS_ARANK] = (int*)A->ranks.p;
+    B.i[IS_S] = (int*)si.p;
+    B.flops = k.flops();
+    B.status = k.status();
+    rc = run_plan(c, dp, B, A->h, nullptr);
+    unsigned long long fl[NFC];
+    int st[4];
+    if (rc == HM_OK) rc = counters_read(c, k, fl, st);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    A->build_seconds = ms * 1e-3;
+    if (rc == HM_OK) A->aca_unconverged = st[2];
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, k.b);
+    free_plan(c, dp);
+  } while (false);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HM_OK) return cleanup(rc);
+  *out = A.release();
+  return HM_OK;
+}
+
+void hm_matrix_free(hm_matrix* A) {
+  if (!A) return;
+  hm_ctx* c = A->ctx;
+  free_plan(c, A->lu_plan);
+  free_plan(c, A->mv_plan);
+  dfree(c, A->mv_work);
+  dfree(c, A->perm);
+  dfree(c, A->pts);
+  dfree(c, A->pts_orig);
+  dfree(c, A->vals);
+  dfree(c, A->ranks);
+  delete A;
+}
+
+// ------------------------------------------------------------------------------ H-LU
+int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
+  if (!c || !A || !out) return fail(HM_EINVAL, "hm_lu: NULL argument");
+  double eps = (o && o->eps > 0.0) ? o->eps : A->opts.eps;
+  if (o && o->precision != 0) return fail(HM_EINVAL, "hm_lu: only precision 0 (FP64) is available");
+  CU(cudaSetDevice(c->device));
+  try {
+    if (!A->dag_built) {
+      build_task_graph(A->ct, A->bt, A->dag);
+      if (!compute_levels(A->dag)) return fail(HM_EINTERNAL, "hm_lu: task graph has a cycle");
+      A->dag_built = true;
+    }
+    if (A->lu_plan.eps != eps) {
+      free_plan(c, A->lu_plan);
+      auto t0 = std::chrono::steady_clock::now();
+      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host);
+      A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      A->lu_plan.eps = eps;
+    }
+  } catch (const std::exception& ex) {
+    return fail(HM_EINTERNAL, std::string("hm_lu: ") + ex.what());
+  }
+  int rc = upload(c, A->lu_plan);
+  if (rc) return rc;
+  auto F = std::make_unique<hm_factor>();
+  F->ctx = c;
+  F->A = A;
+  F->eps = eps;
+  Buf sd, si;
+  Counters k;
+  auto cleanup = [&](int r) {
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, k.b);
+    dfree(c, F->vals);
+    dfree(c, F->ranks);
+    dfree(c, F->piv);
+    return r;
+  };
+  const Plan& P = A->lu_plan.host;
+  if (!dalloc(c, F->vals, A->lay.nvalues * 8) || !dalloc(c, F->ranks, std::max(1, A->lay.nranks) * 4) ||
+      !dalloc(c, F->piv, std::max<int64_t>(1, A->lay.npiv) * 4) ||
+      !dalloc(c, sd, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
+      !dalloc(c, si, std::max<int64_t>(1, P.scratch_ints) * 4))
+    return cleanup(fail(HM_ENOMEM, "hm_lu: allocator returned NULL"));
+  if ((rc = counters_init(c, k))) return cleanup(rc);
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t ce = cudaMemcpyAsync(F->vals.p, A->vals.p, A->lay.nvalues * 8, cudaMemcpyDeviceToDevice, s);
+  if (!ce) ce = cudaMemcpyAsync(F->ranks.p, A->ranks.p, std::max(1, A->lay.nranks) * 4, cudaMemcpyDeviceToDevice, s);
+  if (ce) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cleanup(fail(HM_ECUDA, std::string("hm_lu: copy of A: ") + cudaGetErrorString(ce)));
+  }
+  Bases B = make_bases();
+  B.d[SP_F] = (double*)F->vals.p;
+  B.d[SP_S] = (double*)sd.p;
+  B.d[SP_A] = (double*)A->vals.p;
+  B.d[SP_P] = (double*)A->pts.p;
+  B.i[IS_RANK] = (int*)F->ranks.p;
+  B.i[IS_PIV] = (int*)F->piv.p;
+  B.i[IS_S] = (int*)si.p;
+  B.i[IS_ARANK] = (int*)A->ranks.p;
+  B.flops = k.flops();
+  B.status = k.status();
+  Profile prof;
+  rc = run_plan(c, A->lu_plan, B, A->h, c->profiling ? &prof : nullptr);
+  cudaEventRecord(e1, s);
+  cudaError_t se = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return cleanup(rc);
+  if (se) return cleanup(fail(HM_ECUDA, std::string("hm_lu: ") + cudaGetErrorString(se)));
+  unsigned long long fl[NFC];
+  int st[4];
+  if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
+  fill_matrix_stats(A, &F->st);
+  F->st.eps = eps;
+  F->st.seconds = ms * 1e-3;
+  for (int q = 0; q < 5; ++q) F->st.flops[q] = (double)fl[q];
+  F->st.singular_pivots = st[0];
+  F->st.rank_cap_hits = st[1];
+  for (int q = 0; q < NKIND; ++q) {
+    F->st.kind_ms[q] = prof.ms[q];
+    F->st.kind_launches[q] = prof.launches[q];
+  }
+  if ((rc = read_ranks(c, F->ranks, A->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
+  dfree(c, sd);
+  dfree(c, si);
+  dfree(c, k.b);
+  hm_factor* f = F.release();
+  *out = f;
+  if (st[0] > 0) return fail(HM_ESINGULAR, "hm_lu: zero pivot in a diagonal leaf");
+  return HM_OK;
+}
+
+void hm_factor_free(hm_factor* F) {
+  if (!F) return;
+  hm_ctx* c = F->ctx;
+  free_plan(c, F->solve_plan);
+  free_plan(c, F->mv_plan);
+  dfree(c, F->work);
+  dfree(c, F->vals);
+  dfree(c, F->ranks);
+  dfree(c, F->piv);
+  delete F;
+}
+
+}  // extern "C"
+
+namespace {
+
+// run a solve / matvec plan on the SP_X work buffer; `nv` goes to scratch int 0
+int run_aux(hm_ctx* c, hm_matrix* A, hm_factor* F, DevPlan& dp, Buf& work, int nv) {
+  Buf sd, si;
+  Counters k;
+  auto done = [&](int r) {
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, k.b);
+    return r;
+  };
+  if (!dalloc(c, sd, std::max<int64_t>(1, dp.host.scratch_doubles) * 8) ||
+      !dalloc(c, si, std::max<int64_t>(8, dp.host.scratch_ints) * 4))
+    return done(fail(HM_ENOMEM, "allocator returned NULL (scratch)"));
+  int rc = counters_init(c, k);
+  if (rc) return done(rc);
+  if (launch_set_int((int*)si.p, nv, c->stream)) return done(fail(HM_ECUDA, "set-int kernel failed"));
+  Bases B = make_bases();
+  B.d[SP_S] = (double*)sd.p;
+  B.d[SP_X] = (double*)work.p;
+  B.d[SP_A] = (double*)A->vals.p;
+  B.d[SP_P] = (double*)A->pts.p;
+  B.i[IS_S] = (int*)si.p;
+  B.i[IS_ARANK] = (int*)A->ranks.p;
+  if (F) {
+    B.d[SP_F] = (double*)F->vals.p;
+    B.i[IS_RANK] = (int*)F->ranks.p;
+    B.i[IS_PIV] = (int*)F->piv.p;
+  }
+  B.flops = k.flops();
+  B.status = k.status();
+  rc = run_plan(c, dp, B, A->h, nullptr);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) rc = fail(HM_ECUDA, std::string("plan execution: ") + cudaGetErrorString(e));
+  }
+  return done(rc);
+}
+
+int plain_solve(hm_ctx* c, hm_factor* F, const double* b, double* x, int64_t nrhs, int64_t ld) {
+  hm_matrix* A = F->A;
+  const int n = (int)A->n;
+  if (!F->solve_plan.uploaded) {
+    try {
+      plan_solve(A->ct, A->bt, A->lay, SOLVE_CHUNK, F->solve_plan.host);
+    } catch (const std::exception& ex) {
+      return fail(HM_EINTERNAL, std::string("hm_solve: ") + ex.what());
+    }
+    int rc = upload(c, F->solve_plan);
+    if (rc) return rc;
+  }
+  if (!F->work.p && !dalloc(c, F->work, (size_t)n * 4 * SOLVE_CHUNK * 8))
+    return fail(HM_ENOMEM, "hm_solve: allocator returned NULL");
+  for (int64_t c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
+    const int nc = (int)std::min<int64_t>(SOLVE_CHUNK, nrhs - c0);
+    if (launch_permute(b + c0 * ld, ld, (double*)F->work.p, n, (int64_t*)A->perm.p, n, nc, 0, 1.0, 0.0, 0,
+                       c->stream))
+      return fail(HM_ECUDA, "hm_solve: permute kernel failed");
+    int rc = run_aux(c, A, F, F->solve_plan, F->work, nc);
+    if (rc) return rc;
+    if (launch_permute((double*)F->work.p, n, x + c0 * ld, ld, (int64_t*)A->perm.p, n, nc, 1, 1.0, 0.0, 0,
+                       c->stream))
+      return fail(HM_ECUDA, "hm_solve: permute kernel failed");
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return HM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hm_matvec(hm_ctx* c, hm_matrix* A, hm_factor* F, int op, double alpha, const double* x, double beta, double* y,
+              int64_t nrhs, int64_t ld) {
+  if (!c || !A || !x || !y) return fail(HM_EINVAL, "hm_matvec: NULL argument");
+  if (nrhs < 0 || ld < A->n) return fail(HM_EINVAL, "hm_matvec: bad nrhs or ld");
+  if (op < HM_OP_A || op > HM_OP_EXACT) return fail(HM_EINVAL, "hm_matvec: unknown op");
+  if (op >= HM_OP_L && op <= HM_OP_LU && !F) return fail(HM_EINVAL, "hm_matvec: op needs a factor");
+  if (F && F->A != A) return fail(HM_EINVAL, "hm_matvec: factor belongs to another matrix");
+  if (nrhs == 0) return HM_OK;
+  CU(cudaSetDevice(c->device));
+  const int n = (int)A->n;
+  if (op == HM_OP_EXACT) {
+    Buf t;
+    if (!dalloc(c, t, (size_t)n * nrhs * 8)) return fail(HM_ENOMEM, "hm_matvec: allocator returned NULL");
+    cudaError_t e = launch_exact_mv((double*)A->pts_orig.p, n, A->h, x, ld, (double*)t.p, n, (int)nrhs, c->stream);
+    if (!e) e = launch_axpby((double*)t.p, n, y, ld, n, (int)nrhs, alpha, beta, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    dfree(c, t);
+    if (e) return fail(HM_ECUDA, std::string("hm_matvec: ") + cudaGetErrorString(e));
+    return HM_OK;
+  }
+  DevPlan& dp = F ? F->mv_plan : A->mv_plan;
+  Buf& work = F ? F->work : A->mv_work;
+  const int want = op;
+  if (dp.uploaded && (int)dp.eps != want) free_plan(c, dp);
+  if (!dp.uploaded) {
+    try {
+      plan_matvec(A->ct, A->bt, A->lay, want, SOLVE_CHUNK, dp.host);
+    } catch (const std::exception& ex) {
+      return fail(HM_EINTERNAL, std::string("hm_matvec: ") + ex.what());
+    }
+    dp.eps = want;
+    int rc = upload(c, dp);
+    if (rc) return rc;
+  }
+  if (!work.p && !dalloc(c, work, (size_t)n * 4 * SOLVE_CHUNK * 8))
+    return fail(HM_ENOMEM, "hm_matvec: allocator returned NULL");
+  double* W = (double*)work.p;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
+    const int nc = (int)std::min<int64_t>(SOLVE_CHUNK, nrhs - c0);
+    if (launch_permute(x + c0 * ld, ld, W, n, (int64_t*)A->perm.p, n, nc, 0, 1.0, 0.0, 0, c->stream))
+      return fail(HM_ECUDA, "hm_matvec: permute kernel failed");
+    int rc = run_aux(c, A, F, dp, work, nc);
+    if (rc) return rc;
+    if (launch_permute(W + (size_t)SOLVE_CHUNK * n, n, y + c0 * ld, ld, (int64_t*)A->perm.p, n, nc, 1, alpha, beta,
+                       1, c->stream))
+      return fail(HM_ECUDA, "hm_matvec: permute kernel failed");
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return HM_OK;
+}
+
+int hm_solve(hm_ctx* c, hm_factor* F, hm_matrix* A, const double* b, double* x, int64_t nrhs, int64_t ld,
+             const hm_solve_opts* o, hm_solve_info* info) {
+  if (!c || !F || !b || !x) return fail(HM_EINVAL, "hm_solve: NULL argument");
+  if (nrhs < 0 || ld < F->A->n) return fail(HM_EINVAL, "hm_solve: bad nrhs or ld");
+  if (A && A != F->A) return fail(HM_EINVAL, "hm_solve: A is not the factored matrix");
+  if (info) {
+    info->iterations = 0;
+    info->rel_residual = -1.0;
+  }
+  if (nrhs == 0) return HM_OK;
+  CU(cudaSetDevice(c->device));
+  const int n = (int)F->A->n;
+  const bool refine = o && o->max_iter > 0 && A;
+  if (refine && o->residual_op != HM_OP_A && o->residual_op != HM_OP_EXACT)
+    return fail(HM_EINVAL, "hm_solve: residual_op must be HM_OP_A or HM_OP_EXACT");
+  Buf bb, r, d, nrm;
+  auto done = [&](int rc) {
+    dfree(c, bb);
+    dfree(c, r);
+    dfree(c, d);
+    dfree(c, nrm);
+    return rc;
+  };
+  if (refine) {
+    // keep b: x and b may alias
+    if (!dalloc(c, bb, (size_t)n * nrhs * 8) || !dalloc(c, r, (size_t)n * nrhs * 8) ||
+        !dalloc(c, d, (size_t)n * nrhs * 8) || !dalloc(c, nrm, (size_t)2 * nrhs * 8))
+      return done(fail(HM_ENOMEM, "hm_solve: allocator returned NULL"));
+    if (launch_axpby(b, ld, (double*)bb.p, n, n, (int)nrhs, 1.0, 0.0, c->stream))
+      return done(fail(HM_ECUDA, "hm_solve: copy kernel failed"));
+  }
+  int rc = plain_solve(c, F, b, x, nrhs, ld);
+  if (rc || !refine) return done(rc);
+  std::vector<double> hn(2 * nrhs);
+  if (launch_colnorm2((double*)bb.p, n, n, (int)nrhs, (double*)nrm.p, c->stream))
+    return done(fail(HM_ECUDA, "hm_solve: norm kernel failed"));
+  CU(cudaMemcpyAsync(hn.data(), nrm.p, nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  std::vector<double> bnorm(hn.begin(), hn.begin() + nrhs);
+  double rel = 0.0;
+  int it = 0;
+  for (;;) {
+    // r = b - A x
+    if (launch_axpby((double*)bb.p, n, (double*)r.p, n, n, (int)nrhs, 1.0, 0.0, c->stream))
+      return done(fail(HM_ECUDA, "hm_solve: copy kernel failed"));
+    if ((rc = hm_matvec(c, F->A, nullptr, o->residual_op, -1.0, x, 1.0, (double*)r.p, nrhs, ld))) return done(rc);
+    if (launch_colnorm2((double*)r.p, n, n, (int)nrhs, (double*)nrm.p, c->stream))
+      return done(fail(HM_ECUDA, "hm_solve: norm kernel failed"));
+    CU(cudaMemcpyAsync(hn.data(), nrm.p, nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    rel = 0.0;
+    for (int64_t q = 0; q < nrhs; ++q)
+      rel = std::max(rel, bnorm[q] > 0 ? std::sqrt(hn[q] / bnorm[q]) : std::sqrt(hn[q]));
+    if (info) {
+      info->iterations = it;
+      info->rel_residual = rel;
+    }
+    if (rel <= o->refine_tol || it >= o->max_iter) break;
+    if ((rc = plain_solve(c, F, (double*)r.p, (double*)d.p, nrhs, n))) return done(rc);
+    if (launch_axpby((double*)d.p, n, x, ld, n, (int)nrhs, 1.0, 1.0, c->stream))
+      return done(fail(HM_ECUDA, "hm_solve: update kernel failed"));
+    ++it;
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  if (rel > o->refine_tol) return done(fail(HM_ENOTCONV, "hm_solve: refinement did not reach refine_tol"));
+  return done(HM_OK);
+}
+
+int hm_matrix_stats(const hm_matrix* A, hm_stats* out) {
+  if (!A || !out) return fail(HM_EINVAL, "hm_matrix_stats: NULL argument");
+  fill_matrix_stats(A, out);
+  int rc = read_ranks(A->ctx, A->ranks, A->lay.nranks, &out->max_rank, &out->sum_rank);
+  return rc;
+}
+
+int hm_factor_stats(const hm_factor* F, hm_stats* out) {
+  if (!F || !out) return fail(HM_EINVAL, "hm_factor_stats: NULL argument");
+  *out = F->st;
+  return HM_OK;
+}
+
+// ------------------------------------------------------------------------------ truncate
+int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t ldw, const double* Z, int64_t ldz,
+                double eps, int cap, double* U, int64_t ldu, double* V, int64_t ldv, int* k_out) {
+  if (!c || !W || !Z || !U || !V || !k_out) return fail(HM_EINVAL, "hm_truncate: NULL argument");
+  if (m < 1 || n < 1 || K < 0 || K > 256 || cap < 1 || cap > 64 || ldw < m || ldz < n || ldu < m || ldv < n)
+    return fail(HM_EINVAL, "hm_truncate: bad sizes (1 <= m, n; 0 <= K <= 256; 1 <= cap <= 64; ld >= rows)");
+  if (!(eps > 0.0)) return fail(HM_EINVAL, "hm_truncate: eps must be > 0");
+  if (m > (int64_t)1 << 30 || n > (int64_t)1 << 30) return fail(HM_EINVAL, "hm_truncate: m or n too large");
+  CU(cudaSetDevice(c->device));
+  const int capk = (int)std::min<int64_t>(cap, std::min(m, n));
+  const int Kc = std::max(2, (K + 1) / 2 * 2);
+  // scratch layout (doubles): Uo m*capk | Vo n*capk | Wst m*Kc | Zst n*Kc | Gw | Gz | Tw | Tz | work
+  const int64_t a = 32;
+  auto al = [&](int64_t v) { return (v + a - 1) / a * a; };
+  int64_t off = 0;
+  const int64_t oU = off; off += al(m * capk);
+  const int64_t oV = off; off += al(n * capk);
+  const int64_t oW = off; off += al(m * Kc);
+  const int64_t oZ = off; off += al(n * Kc);
+  const int64_t oGw = off; off += al((int64_t)Kc * Kc);
+  const int64_t oGz = off; off += al((int64_t)Kc * Kc);
+  const int64_t oTw = off; off += al((int64_t)Kc * capk);
+  const int64_t oTz = off; off += al((int64_t)Kc * capk);
+  const int64_t oWk = off; off += al(4 * (int64_t)Kc * Kc);
+  Buf sd, si, ops, ent;
+  Counters k;
+  auto done = [&](int r) {
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, ops);
+    dfree(c, ent);
+    dfree(c, k.b);
+    return r;
+  };
+  if (!dalloc(c, sd, off * 8) || !dalloc(c, si, 64)) return done(fail(HM_ENOMEM, "hm_truncate: allocator returned NULL"));
+  int rc = counters_init(c, k);
+  if (rc) return done(rc);
+  // one piece: W Z^T over the whole target; target starts empty (rank 0)
+  StackEntry e;
+  std::memset(&e, 0, sizeof(e));
+  e.W = mkref(SP_X, 0);
+  e.w_rs = 1;
+  e.w_cs = ldw;
+  e.Z = mkref(SP_A, 0);
+  e.z_rs = 1;
+  e.z_cs = ldz;
+  e.k = K;
+  e.nrows = (int)m;
+  e.ncols = (int)n;
+  e.alpha = 1.0;
+  TruncOp t;
+  std::memset(&t, 0, sizeof(t));
+  t.U = mkref(SP_S, oU);
+  t.V = mkref(SP_S, oV);
+  t.rank = mkref(IS_S, 0);
+  t.m = (int)m;
+  t.n = (int)n;
+  t.cap = capk;
+  t.Kcap = Kc;
+  t.first_entry = 0;
+  t.n_entries = 1;
+  t.Wst = mkref(SP_S, oW);
+  t.Zst = mkref(SP_S, oZ);
+  t.Gw = mkref(SP_S, oGw);
+  t.Gz = mkref(SP_S, oGz);
+  t.Tw = mkref(SP_S, oTw);
+  t.Tz = mkref(SP_S, oTz);
+  t.work = mkref(SP_S, oWk);
+  t.Kd = mkref(IS_S, 8);
+  t.eps = eps;
+  GemmOp g[4];
+  std::memset(g, 0, sizeof(g));
+  const int64_t rows[2] = {m, n};
+  const uint64_t st[2] = {t.Wst, t.Zst}, gr[2] = {t.Gw, t.Gz}, tr[2] = {t.Tw, t.Tz}, out[2] = {t.U, t.V};
+  for (int q = 0; q < 2; ++q) {   // Gram matrices
+    g[q].A = st[q];
+    g[q].a_rs = rows[q];
+    g[q].a_cs = 1;
+    g[q].B = st[q];
+    g[q].b_rs = 1;
+    g[q].b_cs = rows[q];
+    g[q].C = gr[q];
+    g[q].c_rs = 1;
+    g[q].c_cs = Kc;
+    g[q].md = t.Kd;
+    g[q].nd = t.Kd;
+    g[q].k = (int)rows[q];
+    g[q].flags = GF_ATOMIC;
+    g[q].alpha = 1.0;
+    g[q].fclass = FC_NONE;
+  }
+  for (int q = 0; q < 2; ++q) {   // rebuild
+    g[2 + q].A = st[q];
+    g[2 + q].a_rs = 1;
+    g[2 + q].a_cs = rows[q];
+    g[2 + q].B = tr[q];
+    g[2 + q].b_rs = 1;
+    g[2 + q].b_cs = Kc;
+    g[2 + q].C = out[q];
+    g[2 + q].c_rs = 1;
+    g[2 + q].c_cs = rows[q];
+    g[2 + q].m = (int)rows[q];
+    g[2 + q].nd = t.rank;
+    g[2 + q].kd = t.Kd;
+    g[2 + q].flags = GF_OVERWRITE;
+    g[2 + q].alpha = 1.0;
+    g[2 + q].fclass = FC_NONE;
+  }
+  if (!dalloc(c, ops, sizeof(t) + sizeof(g)) || !dalloc(c, ent, sizeof(e)))
+    return done(fail(HM_ENOMEM, "hm_truncate: allocator returned NULL"));
+  cudaStream_t s = c->stream;
+  CU(cudaMemcpyAsync(ops.p, &t, sizeof(t), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync((char*)ops.p + sizeof(t), g, sizeof(g), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ent.p, &e, sizeof(e), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(si.p, 0, 64, s));
+  Bases B = make_bases();
+  B.d[SP_S] = (double*)sd.p;
+  B.d[SP_X] = const_cast<double*>(W);
+  B.d[SP_A] = const_cast<double*>(Z);
+  B.i[IS_S] = (int*)si.p;
+  B.flops = k.flops();
+  B.status = k.status();
+  const TruncOp* dt = (const TruncOp*)ops.p;
+  const GemmOp* dg = (const GemmOp*)((char*)ops.p + sizeof(t));
+  cudaError_t ce = launch_kind(K_STACK, dt, 1, (const StackEntry*)ent.p, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s);
+  if (ce) return done(fail(HM_ECUDA, std::string("hm_truncate: ") + cudaGetErrorString(ce)));
+  int kk = 0;
+  CU(cudaMemcpyAsync(&kk, si.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (kk > 0) {
+    CU(cudaMemcpy2DAsync(U, ldu * 8, (double*)sd.p + oU, m * 8, m * 8, kk, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpy2DAsync(V, ldv * 8, (double*)sd.p + oV, n * 8, n * 8, kk, cudaMemcpyDeviceToDevice, s));
+  }
+  CU(cudaStreamSynchronize(s));
+  *k_out = kk;
+  return done(HM_OK);
+}
+
+// ------------------------------------------------------------------------------ structure (host only)
+}  // extern "C"
+
+struct hm_structure {
+  int64_t n = 0;
+  ClusterTree ct;
+  BlockTree bt;
+  TaskGraph g;
+  Plan plan;
+  bool planned = false;
+};
+
+extern "C" {
+
+int hm_structure_build(const double* pts, int64_t n, int leaf_size, double eta, int with_plan, hm_structure** out) {
+  if (!pts || !out || n < 1) return fail(HM_EINVAL, "hm_structure_build: bad argument");
+  if (leaf_size < 1 || leaf_size > 64) return fail(HM_EINVAL, "hm_structure_build: leaf_size must be in 1..64");
+  auto S = std::make_unique<hm_structure>();
+  S->n = n;
+  try {
+    build_cluster_tree(pts, n, leaf_size, S->ct);
+    build_block_tree(S->ct, eta, S->bt);
+    build_task_graph(S->ct, S->bt, S->g);
+    if (!compute_levels(S->g)) return fail(HM_EINTERNAL, "hm_structure_build: task graph has a cycle");
+    if (with_plan) {
+      Layout lay;
+      build_layout(S->ct, S->bt, 64, lay);
+      plan_lu(S->ct, S->bt, lay, S->g, 1e-6, S->plan);
+      S->planned = true;
+    }
+  } catch (const std::exception& ex) {
+    return fail(HM_EINTERNAL, std::string("hm_structure_build: ") + ex.what());
+  }
+  *out = S.release();
+  return HM_OK;
+}
+
+int hm_structure_info_get(const hm_structure* S, hm_structure_info* o) {
+  if (!S || !o) return fail(HM_EINVAL, "hm_structure_info_get: NULL argument");
+  std::memset(o, 0, sizeof(*o));
+  o->n = S->n;
+  o->nclusters = (int64_t)S->ct.cl.size();
+  o->nleaves = (int64_t)S->bt.leaves.size();
+  o->ntasks = (int64_t)S->g.nodes.size();
+  o->nedges = (int64_t)S->g.edges.size();
+  o->nlevels = S->g.nlevels;
+  o->dag_seconds = S->g.build_seconds;
+  if (S->planned) {
+    o->plan_launches = (int64_t)S->plan.launches.size();
+    o->plan_phases = S->plan.nphases;
+    o->plan_gemm_ops = (int64_t)S->plan.gemm.size();
+    o->plan_truncations = S->plan.ntrunc;
+    o->plan_scratch_bytes = S->plan.scratch_doubles * 8 + S->plan.scratch_ints * 4;
+  }
+  return HM_OK;
+}
+
+int hm_structure_export(const hm_structure* S, int64_t* perm, int32_t* clusters, int32_t* leaves, int32_t* tasks,
+                        int32_t* edges, int32_t* levels) {
+  if (!S) return fail(HM_EINVAL, "hm_structure_export: NULL structure");
+  if (perm)
+    for (int64_t i = 0; i < S->n; ++i) perm[i] = S->ct.perm[i];
+  if (clusters)
+    for (size_t i = 0; i < S->ct.cl.size(); ++i) {
+      const Cluster& c = S->ct.cl[i];
+      int32_t* r = clusters + 6 * i;
+      r[0] = c.lo;
+      r[1] = c.hi;
+      r[2] = c.son0;
+      r[3] = c.son1;
+      r[4] = c.level;
+      r[5] = c.parent;
+    }
+  if (leaves)
+    for (size_t i = 0; i < S->bt.leaves.size(); ++i) {
+      const BlockNode& b = S->bt.nodes[S->bt.leaves[i]];
+      leaves[3 * i] = b.row;
+      leaves[3 * i + 1] = b.col;
+      leaves[3 * i + 2] = b.adm ? 1 : 0;
+    }
+  if (tasks)
+    for (size_t i = 0; i < S->g.nodes.size(); ++i) {
+      const Task& t = S->g.nodes[i];
+      tasks[4 * i] = t.type;
+      tasks[4 * i + 1] = t.a;
+      tasks[4 * i + 2] = t.b;
+      tasks[4 * i + 3] = t.c;
+    }
+  if (edges)
+    for (size_t i = 0; i < S->g.edges.size(); ++i) {
+      edges[2 * i] = S->g.edges[i].first;
+      edges[2 * i + 1] = S->g.edges[i].second;
+    }
+  if (levels)
+    for (size_t i = 0; i < S->g.nodes.size(); ++i) levels[i] = S->g.level[i];
+  return HM_OK;
+}
+
+void hm_structure_free(hm_structure* S) { delete S; }
+
+}  // extern "C"

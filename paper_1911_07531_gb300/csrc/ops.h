@@ -1,0 +1,127 @@
+// Batched micro-op descriptors shared by the host planner and the CUDA kernels.
+//
+// The H-LU task graph (Alg 11) is executed wave by wave; every task of a wave is expanded
+// into micro-ops of a few kinds (dense leaf LU, triangular solves, small GEMMs, copies,
+// stacked rounded truncation), and all micro-ops of one kind in one phase of a wave are
+// launched as one batched kernel, one CTA per micro-op.
+//
+// Addresses are stored as 64-bit references into a handful of memory spaces so that one
+// plan can be replayed on any factor / scratch / right-hand-side buffers:
+//   ref = ((space + 1) << 60) | element_offset,   ref == 0 means "none".
+// Dimensions are a static part plus an optional dynamic part read from device memory
+// (the rank of a low-rank block, known only on the device).
+#pragma once
+
+#include <cstdint>
+
+namespace hm {
+
+enum DSpace : int { SP_F = 0, SP_S = 1, SP_X = 2, SP_A = 3, SP_P = 4, NDSPACE = 5 };
+// SP_F factor values, SP_S scratch, SP_X right-hand-side work buffer,
+// SP_A matrix values, SP_P permuted points (n x 3, row-major)
+enum ISpace : int { IS_RANK = 0, IS_PIV = 1, IS_S = 2, IS_ARANK = 3, NISPACE = 4 };
+
+constexpr uint64_t REF_MASK = (1ull << 60) - 1;
+inline uint64_t mkref(int space, int64_t off) { return ((uint64_t)(space + 1) << 60) | (uint64_t)off; }
+
+struct Bases {
+  double* d[NDSPACE];
+  int* i[NISPACE];
+  unsigned long long* flops;   // per-kernel-class model flop counters
+  int* status;                 // [0] singular pivot count, [1] rank-cap hits, [2] aca non-converged
+};
+
+// flop accounting classes (model of the truncation counts QR + core + SVD + rebuild)
+enum FlopClass : int { FC_GETRF = 0, FC_TRSM = 1, FC_GEMM = 2, FC_TRUNC = 3, FC_NONE = 4, NFC = 5 };
+
+enum GemmFlags : int { GF_ATOMIC = 1, GF_OVERWRITE = 2, GF_A_UPPER = 4, GF_A_UNITLOWER = 8 };
+
+// C(i,j) (+)= alpha * sum_l A(i,l) B(l,j),  X(i,j) = X[i*rs + j*cs]
+struct GemmOp {
+  uint64_t A, B, C;
+  int64_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+  uint64_t md, nd, kd;   // dynamic dimension adders (int refs)
+  int m, n, k;
+  int flags;
+  double alpha;
+  int fclass;
+  int pad;
+};
+
+// batched vector triangular kernels on the packed LU of a diagonal leaf (b x b, ld = b)
+enum TrsmMode : int {
+  TM_L_PIV = 0,    // x := L^{-1} P^T x   (unit lower, pivots)
+  TM_UT = 1,       // x := U^{-T} x
+  TM_U = 2,        // x := U^{-1} x
+  TM_MUL_U = 3,    // x := U x
+  TM_MUL_PL = 4    // x := P L x
+};
+struct TrsmOp {
+  uint64_t T;      // packed LU, col-major b x b
+  uint64_t piv;    // int ref to b pivots (0-based, LAPACK order)
+  uint64_t X;      // vectors: element e of vector v at X[e*x_es + v*x_vs]
+  int64_t x_es, x_vs;
+  uint64_t nvd;    // dynamic vector count adder
+  int nv, b, mode, pad;
+};
+
+struct GetrfOp {
+  uint64_t A;      // b x b col-major (ld = b), factored in place
+  uint64_t piv;    // int ref
+  int b, pad;
+};
+
+enum CopyMode : int { CM_ZERO = 0, CM_IDENTITY = 1, CM_COPY = 2, CM_ADD = 3 };
+struct CopyOp {
+  uint64_t src; int64_t s_rs, s_cs;
+  uint64_t dst; int64_t d_rs, d_cs;
+  uint64_t md, nd;
+  int m, n, mode, pad;
+  double alpha;
+};
+
+// one stacked piece of a rounded addition: alpha * W Z^T on rows [row_off, row_off+nrows),
+// cols [col_off, col_off+ncols) of the target; W(i,l) = W[i*w_rs + l*w_cs], Z likewise.
+struct StackEntry {
+  uint64_t W; int64_t w_rs, w_cs;
+  uint64_t Z; int64_t z_rs, z_cs;
+  uint64_t kd;     // dynamic rank adder
+  int k;
+  int row_off, nrows, col_off, ncols, pad;
+  double alpha;
+};
+
+// rounded addition of a group of pieces into one low-rank leaf U V^T (m x n, cap)
+struct TruncOp {
+  uint64_t U, V;       // target factors, ld m and n, cap columns
+  uint64_t rank;       // int ref
+  int m, n, cap, Kcap;
+  int first_entry, n_entries;
+  uint64_t Wst, Zst;   // m x Kcap and n x Kcap stacks
+  uint64_t Gw, Gz;     // Kcap x Kcap Gram matrices (ld Kcap)
+  uint64_t Tw, Tz;     // Kcap x cap coefficient matrices (ld Kcap)
+  uint64_t work;       // 4 * Kcap * Kcap doubles
+  uint64_t Kd;         // int ref: stacked rank
+  double eps;
+};
+
+// dense leaf assembly: D(i,j) = 1 / (4 pi (|p_{r0+i} - p_{c0+j}| + h)), permuted points
+struct EvalOp {
+  uint64_t D;
+  int r0, c0, m, n;
+};
+
+// adaptive cross approximation of an admissible leaf into scratch factors
+struct AcaOp {
+  int r0, c0, m, n;
+  uint64_t U, V;       // m x kmax and n x kmax (ld m, n)
+  uint64_t used;       // int ref: m row flags
+  uint64_t kd;         // int ref: resulting rank
+  int kmax, pad;
+  double tol;
+};
+
+enum OpKind : int { K_GETRF = 0, K_TRSM = 1, K_GEMM = 2, K_COPY = 3, K_STACK = 4, K_CORE = 5,
+                    K_EVAL = 6, K_ACA = 7, NKIND = 8 };
+
+}  // namespace hm

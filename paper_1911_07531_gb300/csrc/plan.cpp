@@ -1,0 +1,760 @@
+// Planner: expansion of H-LU tasks (and of solves / matvecs) into batched micro-ops.
+//
+// The task graph of Alg 11 is executed in waves (its longest-path levels). A task of a
+// wave is a leaf task of the refinement: hlu on a diagonal leaf, htrsl / htrsu on a leaf
+// block (possibly with a structured triangle), or hmul with at least one leaf operand
+// (Alg 1, non-recursive branch). Each is expanded here into micro-ops in phases:
+//
+//   phase 0..2   leaf LU, triangular solves, and the products A B of hmul formed as
+//                low-rank pieces W Z^T (thin H-matrix products through the leaves of the
+//                structured operand);
+//   phase 3..    application of the pieces: atomic GEMMs into dense leaves; for low-rank
+//                leaves, one rounded addition per leaf and wave that stacks the leaf and
+//                all pieces reaching it (STACK -> Gram GEMMs -> CORE -> rebuild GEMMs),
+//                repeated in rounds when the stacked rank would exceed KMAX.
+//
+// Two updates of one block inside a wave have no edge between them (Def 3.2 only orders
+// writes before reads); they commute up to rounding, so merging them into one rounded
+// addition is a valid schedule of the same task graph.
+#include "plan.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+
+namespace hm {
+
+namespace {
+
+constexpr int KMAX_STACK = 256;     // largest stacked rank of one rounded addition
+constexpr int GEMM_MCHUNK = 512;    // row chunk of a GEMM micro-op
+constexpr int GEMM_KCHUNK = 2048;   // reduction chunk of an accumulating GEMM micro-op
+constexpr int TRSM_VCHUNK = 256;    // vectors of one triangular-solve micro-op
+constexpr int64_t ALIGN = 32;       // doubles (256 bytes)
+
+inline int64_t align_up(int64_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct View {
+  uint64_t ref;
+  int64_t es, vs;   // element (row) stride, vector (column) stride
+  View off(int64_t rows) const { return {ref + (uint64_t)(rows * es), es, vs}; }
+};
+
+struct Dim {
+  int s;
+  uint64_t d;
+};
+
+struct Piece {
+  View W, Z;
+  Dim k;
+  int kmax;
+  int ro, nrows, co, ncols;
+  double alpha;
+};
+
+struct TargetEntries {
+  int leaf;
+  std::vector<std::pair<StackEntry, int>> e;   // entry, static max rank
+};
+
+struct Wave {
+  std::vector<std::vector<GetrfOp>> getrf;
+  std::vector<std::vector<TrsmOp>> trsm;
+  std::vector<std::vector<GemmOp>> gemm;
+  std::vector<std::vector<CopyOp>> copy;
+  std::vector<std::vector<TruncOp>> stack, core;
+  std::vector<std::vector<EvalOp>> eval;
+  std::vector<std::vector<AcaOp>> aca;
+  std::vector<std::vector<std::vector<StackEntry>>> stack_entries;   // per phase, per stack op
+  int64_t sd = 0, si = 0;
+  std::map<int, int> target_index;
+  std::vector<TargetEntries> targets;
+  int nph = 0;
+  void need(int ph) {
+    if (ph + 1 > nph) nph = ph + 1;
+    if ((int)gemm.size() <= ph) {
+      getrf.resize(ph + 1);
+      trsm.resize(ph + 1);
+      gemm.resize(ph + 1);
+      copy.resize(ph + 1);
+      stack.resize(ph + 1);
+      core.resize(ph + 1);
+      eval.resize(ph + 1);
+      aca.resize(ph + 1);
+      stack_entries.resize(ph + 1);
+    }
+  }
+  int64_t alloc_d(int64_t n) {
+    int64_t o = sd;
+    sd += align_up(n);
+    return o;
+  }
+  int64_t alloc_i(int64_t n) {
+    int64_t o = si;
+    si += (n + 7) / 8 * 8;
+    return o;
+  }
+};
+
+struct Ctx {
+  const ClusterTree& ct;
+  const BlockTree& bt;
+  const Layout& lay;
+  Spaces sp;
+  Plan& plan;
+  Wave w;
+  Ctx(const ClusterTree& c, const BlockTree& b, const Layout& l, Spaces s, Plan& p)
+      : ct(c), bt(b), lay(l), sp(s), plan(p) {}
+
+  const Cluster& cl(int id) const { return ct.cl[id]; }
+  const BlockNode& node(int id) const { return bt.nodes[id]; }
+  const LeafStore& leaf_of(int nodeid) const { return lay.leaf[bt.nodes[nodeid].leaf]; }
+  int find(int r, int c) const {
+    int id = bt.find(r, c);
+    if (id < 0) throw std::runtime_error("planner: block not in block tree");
+    return id;
+  }
+  uint64_t dref(int64_t off) const { return mkref(sp.d, off); }
+  uint64_t rref(const LeafStore& L) const { return mkref(sp.r, L.rank_idx); }
+  uint64_t sref(int64_t off) const { return mkref(SP_S, off); }
+
+  // ---------------------------------------------------------------- micro-op emitters
+  void gemm(int ph, uint64_t A, int64_t ars, int64_t acs, uint64_t B, int64_t brs, int64_t bcs, uint64_t C,
+            int64_t crs, int64_t ccs, Dim m, Dim n, Dim k, double alpha, int flags, int fclass) {
+    w.need(ph);
+    // split static rows (always legal) and, for accumulating outputs, the static reduction
+    int mstep = (m.d || m.s <= GEMM_MCHUNK) ? std::max(m.s, 1) : GEMM_MCHUNK;
+    bool ksplit = (flags & GF_ATOMIC) && !k.d && k.s > GEMM_KCHUNK;
+    int kstep = ksplit ? GEMM_KCHUNK : std::max(k.s, 1);
+    for (int i0 = 0; i0 < std::max(m.s, 1); i0 += mstep) {
+      int mi = m.d ? m.s : std::min(mstep, m.s - i0);
+      for (int l0 = 0; l0 < std::max(k.s, 1); l0 += kstep) {
+        int kl = k.d ? k.s : (ksplit ? std::min(kstep, k.s - l0) : k.s);
+        GemmOp g;
+        std::memset(&g, 0, sizeof(g));
+        g.A = A + (uint64_t)(i0 * ars + l0 * acs);
+        g.B = B + (uint64_t)(l0 * brs);
+        g.C = C + (uint64_t)(i0 * crs);
+        g.a_rs = ars;
+        g.a_cs = acs;
+        g.b_rs = brs;
+        g.b_cs = bcs;
+        g.c_rs = crs;
+        g.c_cs = ccs;
+        g.m = mi;
+        g.md = m.d;
+        g.n = n.s;
+        g.nd = n.d;
+        g.k = kl;
+        g.kd = k.d;
+        g.flags = flags;
+        g.alpha = alpha;
+        g.fclass = fclass;
+        w.gemm[ph].push_back(g);
+        if (k.d) break;
+      }
+      if (m.d) break;
+    }
+  }
+  void copy(int ph, int mode, uint64_t src, int64_t srs, int64_t scs, uint64_t dst, int64_t drs, int64_t dcs,
+            Dim m, Dim n, double alpha = 1.0) {
+    w.need(ph);
+    CopyOp c;
+    std::memset(&c, 0, sizeof(c));
+    c.src = src;
+    c.s_rs = srs;
+    c.s_cs = scs;
+    c.dst = dst;
+    c.d_rs = drs;
+    c.d_cs = dcs;
+    c.m = m.s;
+    c.md = m.d;
+    c.n = n.s;
+    c.nd = n.d;
+    c.mode = mode;
+    c.alpha = alpha;
+    w.copy[ph].push_back(c);
+  }
+  void trsm(int ph, int mode, const LeafStore& D, View X, Dim nv) {
+    w.need(ph);
+    int vstep = nv.d ? std::max(nv.s, 1) : TRSM_VCHUNK;
+    for (int v0 = 0; v0 < std::max(nv.s, 1); v0 += vstep) {
+      TrsmOp t;
+      std::memset(&t, 0, sizeof(t));
+      t.T = dref(D.off);
+      t.piv = (mode == TM_L_PIV || mode == TM_MUL_PL) ? mkref(IS_PIV, D.piv_off) : 0;
+      t.X = X.ref + (uint64_t)(v0 * X.vs);
+      t.x_es = X.es;
+      t.x_vs = X.vs;
+      t.nv = nv.d ? nv.s : std::min(vstep, nv.s - v0);
+      t.nvd = nv.d;
+      t.b = D.m;
+      t.mode = mode;
+      w.trsm[ph].push_back(t);
+      if (nv.d) break;
+    }
+  }
+
+  // Y[out] += alpha * op(M_node) X[in] for all leaves of the (sub-)block `nodeid`.
+  // Phases: ph zero of temporaries, ph+1 partial products and dense leaves, ph+2 the
+  // low-rank second factor. X must be final by ph+1; Y must be initialised by ph+1.
+  // `filter`: 0 all leaves, 1 strictly upper, 2 strictly lower.
+  int block_mv(int ph, int nodeid, View X, View Y, double alpha, bool trans, Dim nv, int nvmax,
+               int filter = 0) {
+    std::vector<int> leaves;
+    collect_leaves(bt, nodeid, leaves);
+    const BlockNode& N = node(nodeid);
+    const int base_r = cl(N.row).lo, base_c = cl(N.col).lo;
+    for (int lid : leaves) {
+      const LeafStore& L = leaf_of(lid);
+      const int r0 = cl(L.row).lo, c0 = cl(L.col).lo;
+      if (filter == 1 && !(r0 < c0)) continue;
+      if (filter == 2 && !(r0 > c0)) continue;
+      const int ro = r0 - base_r, co = c0 - base_c;
+      const View Xi = X.off(trans ? ro : co);
+      const View Yo = Y.off(trans ? co : ro);
+      if (!L.lr) {
+        if (!trans)
+          gemm(ph + 1, dref(L.off), 1, L.m, Xi.ref, Xi.es, Xi.vs, Yo.ref, Yo.es, Yo.vs, {L.m, 0}, nv, {L.n, 0},
+               alpha, GF_ATOMIC, FC_GEMM);
+        else
+          gemm(ph + 1, dref(L.off), L.m, 1, Xi.ref, Xi.es, Xi.vs, Yo.ref, Yo.es, Yo.vs, {L.n, 0}, nv, {L.m, 0},
+               alpha, GF_ATOMIC, FC_GEMM);
+      } else {
+        const int64_t T = w.alloc_d((int64_t)L.cap * nvmax);
+        const Dim rk{0, rref(L)};
+        copy(ph, CM_ZERO, 0, 0, 0, sref(T), 1, L.cap, rk, nv);
+        // T = V^T X (or U^T X when transposed), reduction split across CTAs
+        const int64_t first = trans ? L.off : L.voff;
+        const int ld1 = trans ? L.m : L.n;
+        gemm(ph + 1, dref(first), ld1, 1, Xi.ref, Xi.es, Xi.vs, sref(T), 1, L.cap, rk, nv, {ld1, 0}, 1.0,
+             GF_ATOMIC, FC_GEMM);
+        const int64_t second = trans ? L.voff : L.off;
+        const int ld2 = trans ? L.n : L.m;
+        gemm(ph + 2, dref(second), 1, ld2, sref(T), 1, L.cap, Yo.ref, Yo.es, Yo.vs, {ld2, 0}, nv, rk, alpha,
+             GF_ATOMIC, FC_GEMM);
+      }
+    }
+    return ph + 3;
+  }
+
+  // ---------------------------------------------------------------- structured solves
+  // X := L_tt^{-1} P^T X (rows of cluster t), block forward substitution (Alg 3 leaf case)
+  int lsolve(int ph, int t, View X, Dim nv, int nvmax) {
+    const int id = find(t, t);
+    if (node(id).is_leaf()) {
+      trsm(ph, TM_L_PIV, leaf_of(id), X, nv);
+      return ph + 1;
+    }
+    const Cluster& C = cl(t);
+    const int t0 = C.son0, t1 = C.son1;
+    const int n0 = cl(t0).size();
+    int p = lsolve(ph, t0, X, nv, nvmax);
+    p = block_mv(p - 1, find(t1, t0), X, X.off(n0), -1.0, false, nv, nvmax);
+    return lsolve(p, t1, X.off(n0), nv, nvmax);
+  }
+  // X := U_tt^{-T} X
+  int utsolve(int ph, int t, View X, Dim nv, int nvmax) {
+    const int id = find(t, t);
+    if (node(id).is_leaf()) {
+      trsm(ph, TM_UT, leaf_of(id), X, nv);
+      return ph + 1;
+    }
+    const Cluster& C = cl(t);
+    const int t0 = C.son0, t1 = C.son1;
+    const int n0 = cl(t0).size();
+    int p = utsolve(ph, t0, X, nv, nvmax);
+    p = block_mv(p - 1, find(t0, t1), X, X.off(n0), -1.0, true, nv, nvmax);
+    return utsolve(p, t1, X.off(n0), nv, nvmax);
+  }
+  // X := U_tt^{-1} X (backward substitution)
+  int usolve(int ph, int t, View X, Dim nv, int nvmax) {
+    const int id = find(t, t);
+    if (node(id).is_leaf()) {
+      trsm(ph, TM_U, leaf_of(id), X, nv);
+      return ph + 1;
+    }
+    const Cluster& C = cl(t);
+    const int t0 = C.son0, t1 = C.son1;
+    const int n0 = cl(t0).size();
+    int p = usolve(ph, t1, X.off(n0), nv, nvmax);
+    p = block_mv(p - 1, find(t0, t1), X.off(n0), X, -1.0, false, nv, nvmax);
+    return usolve(p, t0, X, nv, nvmax);
+  }
+
+  // ---------------------------------------------------------------- tasks
+  void task_lu(int t) {
+    const int id = find(t, t);
+    const LeafStore& L = leaf_of(id);
+    w.need(0);
+    GetrfOp g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = dref(L.off);
+    g.piv = mkref(IS_PIV, L.piv_off);
+    g.b = L.m;
+    w.getrf[0].push_back(g);
+  }
+  void task_trsl(int t, int s) {   // L_tt X_ts = M_ts, (t, s) a leaf block
+    const LeafStore& M = leaf_of(find(t, s));
+    if (M.lr)
+      lsolve(0, t, View{dref(M.off), 1, M.m}, Dim{0, rref(M)}, M.cap);
+    else
+      lsolve(0, t, View{dref(M.off), 1, M.m}, Dim{M.n, 0}, M.n);
+  }
+  void task_trsu(int t, int s) {   // X_st U_tt = M_st, (s, t) a leaf block
+    const LeafStore& M = leaf_of(find(s, t));
+    if (M.lr)
+      utsolve(0, t, View{dref(M.voff), 1, M.n}, Dim{0, rref(M)}, M.cap);
+    else   // rows of M^T: element e (of t) of vector v (of s) is M[v + e*ld]
+      utsolve(0, t, View{dref(M.off), M.m, 1}, Dim{M.m, 0}, M.m);
+  }
+
+  int64_t identity(int k) {
+    const int64_t I = w.alloc_d((int64_t)k * k);
+    copy(0, CM_IDENTITY, 0, 0, 0, sref(I), 1, k, {k, 0}, {k, 0});
+    return I;
+  }
+
+  // pieces of A_ab B_bc (relative offsets ro, co inside the target) -- phases 0..2
+  void product_pieces(int An, int Bn, int ro, int co, std::vector<Piece>& out) {
+    const BlockNode& A = node(An);
+    const BlockNode& B = node(Bn);
+    const int a = A.row, b = A.col, c = B.col;
+    const int ma = cl(a).size(), mb = cl(b).size(), mc = cl(c).size();
+    const bool Aleaf = A.is_leaf(), Bleaf = B.is_leaf();
+    if (Aleaf && leaf_of(An).lr) {
+      const LeafStore& LA = leaf_of(An);
+      const int64_t Z = w.alloc_d((int64_t)mc * LA.cap);
+      copy(0, CM_ZERO, 0, 0, 0, sref(Z), 1, mc, {mc, 0}, {LA.cap, 0});
+      block_mv(0, Bn, View{dref(LA.voff), 1, mb}, View{sref(Z), 1, mc}, 1.0, true, {0, rref(LA)}, LA.cap);
+      out.push_back({View{dref(LA.off), 1, ma}, View{sref(Z), 1, mc}, {0, rref(LA)}, LA.cap, ro, ma, co, mc, -1.0});
+      return;
+    }
+    if (Bleaf && leaf_of(Bn).lr) {
+      const LeafStore& LB = leaf_of(Bn);
+      const int64_t W = w.alloc_d((int64_t)ma * LB.cap);
+      copy(0, CM_ZERO, 0, 0, 0, sref(W), 1, ma, {ma, 0}, {LB.cap, 0});
+      block_mv(0, An, View{dref(LB.off), 1, mb}, View{sref(W), 1, ma}, 1.0, false, {0, rref(LB)}, LB.cap);
+      out.push_back({View{sref(W), 1, ma}, View{dref(LB.voff), 1, mc}, {0, rref(LB)}, LB.cap, ro, ma, co, mc, -1.0});
+      return;
+    }
+    if (Aleaf && Bleaf) {
+      const LeafStore& LA = leaf_of(An);
+      const LeafStore& LB = leaf_of(Bn);
+      if (mb <= std::min(ma, mc)) {
+        out.push_back({View{dref(LA.off), 1, ma}, View{dref(LB.off), mb, 1}, {mb, 0}, mb, ro, ma, co, mc, -1.0});
+        return;
+      }
+      const int64_t P = w.alloc_d((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, sref(P), 1, ma, {ma, 0}, {mc, 0});
+      gemm(1, dref(LA.off), 1, ma, dref(LB.off), 1, mb, sref(P), 1, ma, {ma, 0}, {mc, 0}, {mb, 0}, 1.0, GF_ATOMIC,
+           FC_GEMM);
+      if (ma <= mc) {
+        const int64_t I = identity(ma);
+        out.push_back({View{sref(I), 1, ma}, View{sref(P), ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
+      } else {
+        const int64_t I = identity(mc);
+        out.push_back({View{sref(P), 1, ma}, View{sref(I), 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
+      }
+      return;
+    }
+    if (Aleaf) {   // A dense with a leaf row cluster, B structured: (I, B^T A^T)
+      const LeafStore& LA = leaf_of(An);
+      const int64_t S = w.alloc_d((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, sref(S), 1, ma, {ma, 0}, {mc, 0});
+      block_mv(0, Bn, View{dref(LA.off), ma, 1}, View{sref(S), ma, 1}, 1.0, true, {ma, 0}, ma);
+      const int64_t I = identity(ma);
+      out.push_back({View{sref(I), 1, ma}, View{sref(S), ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
+      return;
+    }
+    if (Bleaf) {   // B dense with a leaf column cluster, A structured: (A B, I)
+      const LeafStore& LB = leaf_of(Bn);
+      const int64_t S = w.alloc_d((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, sref(S), 1, ma, {ma, 0}, {mc, 0});
+      block_mv(0, An, View{dref(LB.off), 1, mb}, View{sref(S), 1, ma}, 1.0, false, {mc, 0}, mc);
+      const int64_t I = identity(mc);
+      out.push_back({View{sref(S), 1, ma}, View{sref(I), 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
+      return;
+    }
+    const Cluster& Ca = cl(a);
+    const Cluster& Cb = cl(b);
+    const Cluster& Cc = cl(c);
+    const int as[2] = {Ca.son0, Ca.son1}, bs[2] = {Cb.son0, Cb.son1}, cs[2] = {Cc.son0, Cc.son1};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j)
+        for (int l = 0; l < 2; ++l)
+          product_pieces(find(as[i], bs[l]), find(bs[l], cs[j]), ro + cl(as[i]).lo - Ca.lo,
+                         co + cl(cs[j]).lo - Cc.lo, out);
+  }
+
+  // dense target: C += alpha A B accumulated directly -- phases 0..3
+  void product_dense(int An, int Bn, const LeafStore& C, double alpha) {
+    const BlockNode& A = node(An);
+    const BlockNode& B = node(Bn);
+    const int a = A.row, b = A.col, c = B.col;
+    const int ma = cl(a).size(), mb = cl(b).size(), mc = cl(c).size();
+    const View Cv{dref(C.off), 1, C.m};
+    if (A.is_leaf() && leaf_of(An).lr) {
+      const LeafStore& LA = leaf_of(An);
+      const int64_t Z = w.alloc_d((int64_t)mc * LA.cap);
+      copy(0, CM_ZERO, 0, 0, 0, sref(Z), 1, mc, {mc, 0}, {LA.cap, 0});
+      block_mv(0, Bn, View{dref(LA.voff), 1, mb}, View{sref(Z), 1, mc}, 1.0, true, {0, rref(LA)}, LA.cap);
+      gemm(3, dref(LA.off), 1, ma, sref(Z), mc, 1, Cv.ref, 1, C.m, {ma, 0}, {mc, 0}, {0, rref(LA)}, alpha,
+           GF_ATOMIC, FC_GEMM);
+      return;
+    }
+    if (B.is_leaf() && leaf_of(Bn).lr) {
+      const LeafStore& LB = leaf_of(Bn);
+      const int64_t W = w.alloc_d((int64_t)ma * LB.cap);
+      copy(0, CM_ZERO, 0, 0, 0, sref(W), 1, ma, {ma, 0}, {LB.cap, 0});
+      block_mv(0, An, View{dref(LB.off), 1, mb}, View{sref(W), 1, ma}, 1.0, false, {0, rref(LB)}, LB.cap);
+      gemm(3, sref(W), 1, ma, dref(LB.voff), mc, 1, Cv.ref, 1, C.m, {ma, 0}, {mc, 0}, {0, rref(LB)}, alpha,
+           GF_ATOMIC, FC_GEMM);
+      return;
+    }
+    if (A.is_leaf() && B.is_leaf()) {
+      gemm(1, dref(leaf_of(An).off), 1, ma, dref(leaf_of(Bn).off), 1, mb, Cv.ref, 1, C.m, {ma, 0}, {mc, 0},
+           {mb, 0}, alpha, GF_ATOMIC, FC_GEMM);
+      return;
+    }
+    if (A.is_leaf()) {   // C^T += alpha B^T A^T
+      const LeafStore& LA = leaf_of(An);
+      block_mv(0, Bn, View{dref(LA.off), ma, 1}, View{Cv.ref, C.m, 1}, alpha, true, {ma, 0}, ma);
+      return;
+    }
+    if (B.is_leaf()) {
+      const LeafStore& LB = leaf_of(Bn);
+      block_mv(0, An, View{dref(LB.off), 1, mb}, Cv, alpha, false, {mc, 0}, mc);
+      return;
+    }
+    throw std::runtime_error("planner: dense target with two structured operands");
+  }
+
+  void add_entry(int leafidx, const Piece& p, int row_off, int nrows, int col_off, int ncols, int wrow,
+                 int zrow) {
+    StackEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.W = p.W.ref + (uint64_t)(wrow * p.W.es);
+    e.w_rs = p.W.es;
+    e.w_cs = p.W.vs;
+    e.Z = p.Z.ref + (uint64_t)(zrow * p.Z.es);
+    e.z_rs = p.Z.es;
+    e.z_cs = p.Z.vs;
+    e.k = p.k.s;
+    e.kd = p.k.d;
+    e.row_off = row_off;
+    e.nrows = nrows;
+    e.col_off = col_off;
+    e.ncols = ncols;
+    e.alpha = p.alpha;
+    auto it = w.target_index.find(leafidx);
+    int ti;
+    if (it == w.target_index.end()) {
+      ti = (int)w.targets.size();
+      w.target_index[leafidx] = ti;
+      w.targets.push_back({leafidx, {}});
+    } else {
+      ti = it->second;
+    }
+    w.targets[ti].e.push_back({e, p.kmax});
+  }
+
+  // apply the pieces (relative to the origin of block Cn) to the leaves of Cn -- phase 3
+  void apply_pieces(int Cn, const std::vector<Piece>& pieces) {
+    std::vector<int> leaves;
+    collect_leaves(bt, Cn, leaves);
+    const BlockNode& C = node(Cn);
+    const int br = cl(C.row).lo, bc = cl(C.col).lo;
+    for (int lid : leaves) {
+      const LeafStore& L = leaf_of(lid);
+      const int lr0 = cl(L.row).lo - br, lr1 = lr0 + L.m;
+      const int lc0 = cl(L.col).lo - bc, lc1 = lc0 + L.n;
+      for (const Piece& p : pieces) {
+        const int ir0 = std::max(p.ro, lr0), ir1 = std::min(p.ro + p.nrows, lr1);
+        const int ic0 = std::max(p.co, lc0), ic1 = std::min(p.co + p.ncols, lc1);
+        if (ir0 >= ir1 || ic0 >= ic1) continue;
+        if (!L.lr) {
+          const View Wv = p.W.off(ir0 - p.ro), Zv = p.Z.off(ic0 - p.co);
+          const uint64_t Cref = dref(L.off) + (uint64_t)((ir0 - lr0) + (int64_t)(ic0 - lc0) * L.m);
+          gemm(3, Wv.ref, Wv.es, Wv.vs, Zv.ref, Zv.vs, Zv.es, Cref, 1, L.m, {ir1 - ir0, 0}, {ic1 - ic0, 0}, p.k,
+               p.alpha, GF_ATOMIC, FC_GEMM);
+        } else {
+          add_entry(bt.nodes[lid].leaf, p, ir0 - lr0, ir1 - ir0, ic0 - lc0, ic1 - ic0, ir0 - p.ro, ic0 - p.co);
+        }
+      }
+    }
+  }
+
+  void task_mul(int t, int r, int s) {
+    const int An = find(t, r), Bn = find(r, s), Cn = find(t, s);
+    const BlockNode& C = node(Cn);
+    if (C.is_leaf() && !leaf_of(Cn).lr) {
+      product_dense(An, Bn, leaf_of(Cn), -1.0);
+      return;
+    }
+    std::vector<Piece> pieces;
+    product_pieces(An, Bn, 0, 0, pieces);
+    apply_pieces(Cn, pieces);
+  }
+
+  // rounded additions of all pieces that reached low-rank leaves in this wave
+  void emit_truncations(int ph0, double eps, bool target_rank_zero = false) {
+    for (const TargetEntries& T : w.targets) {
+      const LeafStore& L = lay.leaf[T.leaf];
+      const int selfmax = target_rank_zero ? 0 : L.cap;
+      size_t e0 = 0;
+      int round = 0;
+      while (e0 < T.e.size()) {
+        int sum = selfmax;
+        size_t e1 = e0;
+        while (e1 < T.e.size() && (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
+          sum += T.e[e1].second;
+          ++e1;
+        }
+        if (sum > KMAX_STACK) throw std::runtime_error("planner: piece rank exceeds the stack limit");
+        const int Kc = (sum + 1) / 2 * 2;
+        const int ph = ph0 + 4 * round;
+        w.need(ph + 3);
+        TruncOp op;
+        std::memset(&op, 0, sizeof(op));
+        op.U = dref(L.off);
+        op.V = dref(L.voff);
+        op.rank = rref(L);
+        op.m = L.m;
+        op.n = L.n;
+        op.cap = L.cap;
+        op.Kcap = Kc;
+        op.Wst = sref(w.alloc_d((int64_t)L.m * Kc));
+        op.Zst = sref(w.alloc_d((int64_t)L.n * Kc));
+        op.Gw = sref(w.alloc_d((int64_t)Kc * Kc));
+        op.Gz = sref(w.alloc_d((int64_t)Kc * Kc));
+        op.Tw = sref(w.alloc_d((int64_t)Kc * L.cap));
+        op.Tz = sref(w.alloc_d((int64_t)Kc * L.cap));
+        op.work = sref(w.alloc_d(4 * (int64_t)Kc * Kc));
+        op.Kd = mkref(IS_S, w.alloc_i(1));
+        op.eps = eps;
+        std::vector<StackEntry> es;
+        for (size_t q = e0; q < e1; ++q) es.push_back(T.e[q].first);
+        w.stack[ph].push_back(op);
+        w.stack_entries[ph].push_back(es);
+        const Dim Kd{0, op.Kd};
+        for (int i0 = 0; i0 < L.m; i0 += 4096) {
+          int mi = std::min(4096, L.m - i0);
+          gemm(ph + 1, op.Wst + (uint64_t)i0, L.m, 1, op.Wst + (uint64_t)i0, 1, L.m, op.Gw, 1, Kc, Kd, Kd,
+               {mi, 0}, 1.0, GF_ATOMIC, FC_NONE);
+        }
+        for (int i0 = 0; i0 < L.n; i0 += 4096) {
+          int ni = std::min(4096, L.n - i0);
+          gemm(ph + 1, op.Zst + (uint64_t)i0, L.n, 1, op.Zst + (uint64_t)i0, 1, L.n, op.Gz, 1, Kc, Kd, Kd,
+               {ni, 0}, 1.0, GF_ATOMIC, FC_NONE);
+        }
+        w.core[ph + 2].push_back(op);
+        const Dim rk{0, op.rank};
+        gemm(ph + 3, op.Wst, 1, L.m, op.Tw, 1, Kc, op.U, 1, L.m, {L.m, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
+        gemm(ph + 3, op.Zst, 1, L.n, op.Tz, 1, Kc, op.V, 1, L.n, {L.n, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
+        plan.ntrunc++;
+        e0 = e1;
+        ++round;
+        target_rank_zero = false;
+      }
+    }
+  }
+
+  // append the wave's phases to the plan in execution order
+  void flush() {
+    for (int ph = 0; ph < w.nph; ++ph) {
+      if ((int)w.gemm.size() <= ph) break;
+      auto put = [&](int kind, int count, int begin) {
+        if (count > 0) plan.launches.push_back({kind, begin, count});
+      };
+      put(K_GETRF, (int)w.getrf[ph].size(), (int)plan.getrf.size());
+      plan.getrf.insert(plan.getrf.end(), w.getrf[ph].begin(), w.getrf[ph].end());
+      put(K_EVAL, (int)w.eval[ph].size(), (int)plan.eval.size());
+      plan.eval.insert(plan.eval.end(), w.eval[ph].begin(), w.eval[ph].end());
+      put(K_ACA, (int)w.aca[ph].size(), (int)plan.aca.size());
+      plan.aca.insert(plan.aca.end(), w.aca[ph].begin(), w.aca[ph].end());
+      put(K_COPY, (int)w.copy[ph].size(), (int)plan.copy.size());
+      plan.copy.insert(plan.copy.end(), w.copy[ph].begin(), w.copy[ph].end());
+      put(K_TRSM, (int)w.trsm[ph].size(), (int)plan.trsm.size());
+      plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
+      put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
+      plan.gemm.insert(plan.gemm.end(), w.gemm[ph].begin(), w.gemm[ph].end());
+      if (!w.stack[ph].empty()) {
+        put(K_STACK, (int)w.stack[ph].size(), (int)plan.trunc.size());
+        for (size_t q = 0; q < w.stack[ph].size(); ++q) {
+          TruncOp op = w.stack[ph][q];
+          op.first_entry = (int)plan.entries.size();
+          op.n_entries = (int)w.stack_entries[ph][q].size();
+          plan.entries.insert(plan.entries.end(), w.stack_entries[ph][q].begin(), w.stack_entries[ph][q].end());
+          plan.trunc.push_back(op);
+        }
+      }
+      put(K_CORE, (int)w.core[ph].size(), (int)plan.trunc.size());
+      plan.trunc.insert(plan.trunc.end(), w.core[ph].begin(), w.core[ph].end());
+    }
+    plan.nphases += w.nph;
+    plan.scratch_doubles = std::max(plan.scratch_doubles, w.sd);
+    plan.scratch_ints = std::max(plan.scratch_ints, w.si);
+    plan.nwaves++;
+    w = Wave();
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ layout
+void build_layout(const ClusterTree& ct, const BlockTree& bt, int rank_cap, Layout& lay) {
+  lay = Layout();
+  lay.rank_cap = rank_cap;
+  lay.leaf.resize(bt.leaves.size());
+  int64_t off = 0;
+  for (size_t q = 0; q < bt.leaves.size(); ++q) {
+    const BlockNode& b = bt.nodes[bt.leaves[q]];
+    LeafStore& L = lay.leaf[q];
+    L.node = bt.leaves[q];
+    L.row = b.row;
+    L.col = b.col;
+    L.m = ct.cl[b.row].size();
+    L.n = ct.cl[b.col].size();
+    L.lr = b.adm;
+    if (L.lr) {
+      L.cap = std::min(rank_cap, std::min(L.m, L.n));
+      L.off = off;
+      off += align_up((int64_t)L.m * L.cap);
+      L.voff = off;
+      off += align_up((int64_t)L.n * L.cap);
+      L.rank_idx = lay.nranks++;
+    } else {
+      L.off = off;
+      off += align_up((int64_t)L.m * L.n);
+      if (b.row == b.col) {
+        L.piv_off = lay.npiv;
+        lay.npiv += L.m;
+      }
+    }
+  }
+  lay.nvalues = off;
+}
+
+// ------------------------------------------------------------------------------ H-LU
+void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
+             Plan& plan) {
+  plan = Plan();
+  std::vector<std::vector<int>> byl(g.nlevels);
+  for (size_t i = 0; i < g.nodes.size(); ++i) byl[g.level[i]].push_back((int)i);
+  Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
+  for (int lv = 0; lv < g.nlevels; ++lv) {
+    for (int ti : byl[lv]) {
+      const Task& t = g.nodes[ti];
+      switch (t.type) {
+        case T_LU: c.task_lu(t.a); break;
+        case T_TRSL: c.task_trsl(t.a, t.b); break;
+        case T_TRSU: c.task_trsu(t.a, t.b); break;
+        default: c.task_mul(t.a, t.b, t.c); break;
+      }
+      plan.ntasks++;
+    }
+    c.emit_truncations(3, eps);
+    c.flush();
+  }
+}
+
+// ------------------------------------------------------------------------------ build
+void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, double eps, int aca_kmax,
+                int64_t scratch_budget, Plan& plan) {
+  plan = Plan();
+  Ctx c(ct, bt, lay, Spaces{SP_A, IS_ARANK}, plan);
+  // dense leaves: one wave
+  for (const LeafStore& L : lay.leaf)
+    if (!L.lr) {
+      c.w.need(0);
+      EvalOp e{mkref(SP_A, L.off), ct.cl[L.row].lo, ct.cl[L.col].lo, L.m, L.n};
+      c.w.eval[0].push_back(e);
+    }
+  c.flush();
+  // admissible leaves: ACA into scratch, then a rounded truncation into the leaf; waves are
+  // cut so that each stays within the scratch budget
+  for (size_t q = 0; q < lay.leaf.size(); ++q) {
+    const LeafStore& L = lay.leaf[q];
+    if (!L.lr) continue;
+    const int kmax = std::min(aca_kmax, std::min(L.m, L.n));
+    const int Kc = (kmax + 1) / 2 * 2;
+    int64_t need = (int64_t)(L.m + L.n) * kmax * 2 + 8 * (int64_t)Kc * Kc + 2 * (int64_t)Kc * L.cap + 256;
+    if (c.w.sd > 0 && c.w.sd + need > scratch_budget) {
+      c.emit_truncations(1, eps, true);
+      c.flush();
+    }
+    c.w.need(0);
+    AcaOp a;
+    std::memset(&a, 0, sizeof(a));
+    a.r0 = ct.cl[L.row].lo;
+    a.c0 = ct.cl[L.col].lo;
+    a.m = L.m;
+    a.n = L.n;
+    a.U = mkref(SP_S, c.w.alloc_d((int64_t)L.m * kmax));
+    a.V = mkref(SP_S, c.w.alloc_d((int64_t)L.n * kmax));
+    a.used = mkref(IS_S, c.w.alloc_i(L.m));
+    a.kd = mkref(IS_S, c.w.alloc_i(1));
+    a.kmax = kmax;
+    a.tol = eps / 10.0;
+    c.w.aca[0].push_back(a);
+    Piece p{View{a.U, 1, L.m}, View{a.V, 1, L.n}, Dim{0, a.kd}, kmax, 0, L.m, 0, L.n, 1.0};
+    c.add_entry((int)q, p, 0, L.m, 0, L.n, 0, 0);
+  }
+  if (!c.w.targets.empty() || c.w.nph > 0) {
+    c.emit_truncations(1, eps, true);
+    c.flush();
+  }
+}
+
+// ------------------------------------------------------------------------------ solve
+void plan_solve(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, int nrhs_max, Plan& plan) {
+  plan = Plan();
+  Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
+  const int n = ct.cl[0].size();
+  const Dim nv{0, mkref(IS_S, c.w.alloc_i(1))};   // scratch int 0: number of right-hand sides
+  const View X{mkref(SP_X, 0), 1, n};
+  int p = c.lsolve(0, 0, X, nv, nrhs_max);
+  c.usolve(p, 0, X, nv, nrhs_max);
+  c.flush();
+}
+
+// ------------------------------------------------------------------------------ matvec
+void plan_matvec(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, int op, int nrhs_max,
+                 Plan& plan) {
+  plan = Plan();
+  const int n = ct.cl[0].size();
+  Ctx c(ct, bt, lay, op == 0 ? Spaces{SP_A, IS_ARANK} : Spaces{SP_F, IS_RANK}, plan);
+  const Dim nv{0, mkref(IS_S, c.w.alloc_i(1))};
+  auto col = [&](int blk) { return View{mkref(SP_X, (int64_t)blk * nrhs_max * n), 1, n}; };
+  const View X = col(0), Y = col(1), Z = col(2), V = col(3);
+  auto diag_apply = [&](int ph, int mode, View T) {
+    for (const LeafStore& L : lay.leaf)
+      if (!L.lr && L.row == L.col) c.trsm(ph, mode, L, T.off(ct.cl[L.row].lo), nv);
+  };
+  // out = tri(M) in: strictly-triangular leaves plus the diagonal leaves applied in place
+  auto tri = [&](int ph, View in, View out, int mode, int filter) {
+    c.copy(ph, CM_ZERO, 0, 0, 0, out.ref, 1, n, {n, 0}, nv);
+    c.copy(ph, CM_COPY, in.ref, 1, n, V.ref, 1, n, {n, 0}, nv);
+    diag_apply(ph + 1, mode, V);
+    int p = c.block_mv(ph, 0, in, out, 1.0, false, nv, nrhs_max, filter);
+    c.copy(p, CM_ADD, V.ref, 1, n, out.ref, 1, n, {n, 0}, nv);
+    return p + 1;
+  };
+  if (op == 0) {
+    c.copy(0, CM_ZERO, 0, 0, 0, Y.ref, 1, n, {n, 0}, nv);
+    c.block_mv(0, 0, X, Y, 1.0, false, nv, nrhs_max);
+  } else if (op == 1) {
+    tri(0, X, Y, TM_MUL_PL, 2);
+  } else if (op == 2) {
+    tri(0, X, Y, TM_MUL_U, 1);
+  } else {
+    int p = tri(0, X, Z, TM_MUL_U, 1);
+    tri(p, Z, Y, TM_MUL_PL, 2);
+  }
+  c.flush();
+}
+
+}  // namespace hm

@@ -1,0 +1,76 @@
+// Planner: turns the H-LU task graph (or a solve / matvec) into batched micro-op launches.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "ops.h"
+#include "structure.h"
+
+namespace hm {
+
+// Storage of one leaf block in a value arena (column-major).
+struct LeafStore {
+  int node = -1, row = -1, col = -1;
+  int m = 0, n = 0;
+  bool lr = false;
+  int cap = 0;          // low-rank capacity (columns of U and V)
+  int64_t off = 0;      // dense: D (ld m); low-rank: U (ld m)
+  int64_t voff = 0;     // low-rank: V (ld n)
+  int rank_idx = -1;    // low-rank: index into the rank array
+  int64_t piv_off = -1; // diagonal dense leaf: offset into the pivot array
+};
+
+struct Layout {
+  std::vector<LeafStore> leaf;   // indexed by BlockTree leaf index
+  int64_t nvalues = 0;
+  int nranks = 0;
+  int64_t npiv = 0;
+  int rank_cap = 64;
+};
+
+void build_layout(const ClusterTree& ct, const BlockTree& bt, int rank_cap, Layout& lay);
+
+struct Launch {
+  int kind, begin, count;
+};
+
+struct Plan {
+  std::vector<GetrfOp> getrf;
+  std::vector<TrsmOp> trsm;
+  std::vector<GemmOp> gemm;
+  std::vector<CopyOp> copy;
+  std::vector<TruncOp> trunc;      // shared by K_STACK and K_CORE launches
+  std::vector<StackEntry> entries;
+  std::vector<EvalOp> eval;
+  std::vector<AcaOp> aca;
+  std::vector<Launch> launches;    // execution order
+  int64_t scratch_doubles = 0;
+  int64_t scratch_ints = 0;
+  int nwaves = 0;
+  int nphases = 0;
+  int ntasks = 0;
+  int64_t ntrunc = 0;
+};
+
+// Memory spaces the planner addresses (factor vs. matrix storage).
+struct Spaces {
+  int d;   // SP_F or SP_A
+  int r;   // IS_RANK or IS_ARANK
+};
+
+// H-LU: every wave of the levelled task graph expanded into phases of micro-ops.
+void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
+             double eps, Plan& plan);
+// hm_build: dense leaf assembly, ACA + rounded truncation of the admissible leaves.
+void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, double eps, int aca_kmax,
+                int64_t scratch_budget_doubles, Plan& plan);
+// forward / backward substitution with the factors for up to nrhs_max right-hand sides in
+// the SP_X work buffer (n x nrhs_max, permuted order); the dynamic count is scratch int 0.
+void plan_solve(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, int nrhs_max, Plan& plan);
+// y = op(M) x on the SP_X buffer: columns [0, nrhs_max) hold x, [nrhs_max, 2 nrhs_max) get y.
+// op: 0 = the H-matrix A (SP_A), 1 = L (unit lower incl. pivots), 2 = U, 3 = P L U.
+void plan_matvec(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, int op, int nrhs_max,
+                 Plan& plan);
+
+}  // namespace hm

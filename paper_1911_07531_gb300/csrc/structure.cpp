@@ -1,0 +1,367 @@
+// Cluster tree, block tree and the semi-automatic H-LU task graph (host side).
+// Paper: Def 2.1 (cluster tree), Def 2.2 (block tree), §5.1 (standard admissibility),
+// Table 1 (task data dependencies), Def 3.2 (task relation), Alg 9-11 (refinement).
+#include "structure.h"
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <functional>
+
+namespace hm {
+
+// ------------------------------------------------------------------ cluster tree (Def 2.1)
+namespace {
+
+struct CtBuilder {
+  const double* p;
+  int leaf_size;
+  ClusterTree* ct;
+  std::vector<int64_t> idx;   // working permutation; each cluster owns a contiguous range
+
+  int build(int64_t lo, int64_t hi, int level, int parent) {
+    int id = (int)ct->cl.size();
+    ct->cl.emplace_back();
+    {
+      Cluster& c = ct->cl[id];
+      c.lo = (int)lo;
+      c.hi = (int)hi;
+      c.level = level;
+      c.parent = parent;
+      for (int a = 0; a < 3; ++a) {
+        c.bmin[a] = p[3 * idx[lo] + a];
+        c.bmax[a] = p[3 * idx[lo] + a];
+      }
+      for (int64_t k = lo + 1; k < hi; ++k)
+        for (int a = 0; a < 3; ++a) {
+          double v = p[3 * idx[k] + a];
+          if (v < c.bmin[a]) c.bmin[a] = v;
+          if (v > c.bmax[a]) c.bmax[a] = v;
+        }
+    }
+    if (level > ct->depth) ct->depth = level;
+    if (hi - lo <= leaf_size) return id;
+    double ext[3];
+    int axis = 0;
+    double mid;
+    {
+      const Cluster& c = ct->cl[id];
+      for (int a = 0; a < 3; ++a) ext[a] = c.bmax[a] - c.bmin[a];
+      for (int a = 1; a < 3; ++a)
+        if (ext[a] > ext[axis]) axis = a;
+      mid = 0.5 * (c.bmin[axis] + c.bmax[axis]);
+    }
+    auto first = idx.begin() + lo, last = idx.begin() + hi;
+    auto split = std::stable_partition(first, last, [&](int64_t i) { return p[3 * i + axis] < mid; });
+    int64_t nleft = split - first;
+    if (nleft == 0 || nleft == hi - lo) {
+      // median split in (coordinate, original index) order; each half in ascending index
+      std::sort(first, last, [&](int64_t x, int64_t y) {
+        double cx = p[3 * x + axis], cy = p[3 * y + axis];
+        return cx < cy || (cx == cy && x < y);
+      });
+      nleft = (hi - lo) / 2;
+      std::sort(first, first + nleft);
+      std::sort(first + nleft, last);
+    }
+    int s0 = build(lo, lo + nleft, level + 1, id);
+    int s1 = build(lo + nleft, hi, level + 1, id);
+    ct->cl[id].son0 = s0;
+    ct->cl[id].son1 = s1;
+    return id;
+  }
+};
+
+}  // namespace
+
+void build_cluster_tree(const double* pts, int64_t n, int leaf_size, ClusterTree& ct) {
+  ct = ClusterTree();
+  ct.leaf_size = leaf_size;
+  CtBuilder b{pts, leaf_size, &ct, {}};
+  b.idx.resize(n);
+  for (int64_t i = 0; i < n; ++i) b.idx[i] = i;
+  if (n > 0) b.build(0, n, 0, -1);
+  ct.perm = b.idx;
+}
+
+// ------------------------------------------------------------------ admissibility (§5.1)
+static double diam2(const Cluster& c) {
+  double e0 = c.bmax[0] - c.bmin[0];
+  double e1 = c.bmax[1] - c.bmin[1];
+  double e2 = c.bmax[2] - c.bmin[2];
+  return e0 * e0 + e1 * e1 + e2 * e2;
+}
+
+static double dist2(const Cluster& t, const Cluster& s) {
+  double d[3];
+  for (int a = 0; a < 3; ++a) {
+    double g = std::max(s.bmin[a] - t.bmax[a], t.bmin[a] - s.bmax[a]);
+    d[a] = g > 0.0 ? g : 0.0;
+  }
+  return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+bool admissible(const Cluster& t, const Cluster& s, double eta) {
+  double dd = dist2(t, s);
+  if (!(dd > 0.0)) return false;
+  return std::min(diam2(t), diam2(s)) <= (eta * eta) * dd;
+}
+
+// ------------------------------------------------------------------ block tree (Def 2.2)
+void build_block_tree(const ClusterTree& ct, double eta, BlockTree& bt) {
+  bt = BlockTree();
+  bt.ncl = (int)ct.cl.size();
+  if (ct.cl.empty()) return;
+  std::function<int(int, int)> rec = [&](int r, int c) -> int {
+    int id = (int)bt.nodes.size();
+    bt.nodes.emplace_back();
+    bt.index[(uint64_t)r * (uint64_t)bt.ncl + (uint64_t)c] = id;
+    const Cluster& t = ct.cl[r];
+    const Cluster& s = ct.cl[c];
+    bool adm = admissible(t, s, eta);
+    bt.nodes[id].row = r;
+    bt.nodes[id].col = c;
+    bt.nodes[id].adm = adm;
+    if (!adm && !t.leaf() && !s.leaf()) {
+      int tr[2] = {t.son0, t.son1}, sc[2] = {s.son0, s.son1};
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int child = rec(tr[i], sc[j]);
+          bt.nodes[id].sons[2 * i + j] = child;
+        }
+    } else {
+      bt.nodes[id].leaf = (int)bt.leaves.size();
+      bt.leaves.push_back(id);
+    }
+    return id;
+  };
+  rec(0, 0);
+}
+
+void collect_leaves(const BlockTree& bt, int node, std::vector<int>& out) {
+  const BlockNode& b = bt.nodes[node];
+  if (b.is_leaf()) {
+    out.push_back(node);
+    return;
+  }
+  for (int q = 0; q < 4; ++q) collect_leaves(bt, b.sons[q], out);
+}
+
+// ------------------------------------------------------------------ task graph (§3.1)
+namespace {
+
+enum { ID_A = 0, ID_L = 1, ID_U = 2 };
+
+struct Dep {
+  int id, r, c;
+};
+
+struct DagBuilder {
+  const ClusterTree& ct;
+  const BlockTree& bt;
+  std::vector<Task> tasks;
+  std::vector<std::vector<int>> succ;
+  std::vector<int> sub_first, sub_count;
+
+  DagBuilder(const ClusterTree& c, const BlockTree& b) : ct(c), bt(b) {}
+
+  // Table 1 with the identifiers H-LU passes (Alg 2 / Alg 3 arguments).
+  static int ins(const Task& t, Dep* d) {
+    switch (t.type) {
+      case T_LU: d[0] = {ID_A, t.a, t.a}; return 1;
+      case T_TRSL: d[0] = {ID_L, t.a, t.a}; d[1] = {ID_A, t.a, t.b}; return 2;
+      case T_TRSU: d[0] = {ID_U, t.a, t.a}; d[1] = {ID_A, t.b, t.a}; return 2;
+      default: d[0] = {ID_L, t.a, t.b}; d[1] = {ID_U, t.b, t.c}; return 2;
+    }
+  }
+  static int outs(const Task& t, Dep* d) {
+    switch (t.type) {
+      case T_LU: d[0] = {ID_L, t.a, t.a}; d[1] = {ID_U, t.a, t.a}; return 2;
+      case T_TRSL: d[0] = {ID_U, t.a, t.b}; return 1;
+      case T_TRSU: d[0] = {ID_L, t.b, t.a}; return 1;
+      default: d[0] = {ID_A, t.a, t.c}; return 1;
+    }
+  }
+  bool overlap(int x, int y) const {
+    const Cluster& cx = ct.cl[x];
+    const Cluster& cy = ct.cl[y];
+    return cx.lo < cy.hi && cy.lo < cx.hi;
+  }
+  // Def 3.2
+  bool precedes(int i, int j) const {
+    if (i == j) return false;
+    Dep o[2], in[2];
+    int no = outs(tasks[i], o), ni = ins(tasks[j], in);
+    for (int p = 0; p < no; ++p)
+      for (int q = 0; q < ni; ++q)
+        if (o[p].id == in[q].id && overlap(o[p].r, in[q].r) && overlap(o[p].c, in[q].c)) return true;
+    return false;
+  }
+  bool leaf_block(int r, int c) const {
+    int id = bt.find(r, c);
+    return bt.nodes[id].is_leaf();
+  }
+  int add(int type, int a, int b, int c) {
+    tasks.push_back({type, a, b, c});
+    succ.emplace_back();
+    sub_first.push_back(-1);
+    sub_count.push_back(0);
+    return (int)tasks.size() - 1;
+  }
+  // recursive bodies of Alg 2, Alg 3, its upper mirror and Alg 1, in program order
+  void generate(int g) {
+    Task t = tasks[g];
+    int first = (int)tasks.size();
+    const Cluster& A = ct.cl[t.a];
+    if (t.type == T_LU) {
+      if (leaf_block(t.a, t.a)) return;
+      int t0 = A.son0, t1 = A.son1;
+      add(T_LU, t0, t0, -1);
+      add(T_TRSU, t0, t1, -1);
+      add(T_TRSL, t0, t1, -1);
+      add(T_MUL, t1, t0, t1);
+      add(T_LU, t1, t1, -1);
+    } else if (t.type == T_TRSL) {
+      if (leaf_block(t.a, t.b)) return;
+      const Cluster& S = ct.cl[t.b];
+      int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
+      add(T_TRSL, t0, s0, -1);
+      add(T_TRSL, t0, s1, -1);
+      add(T_MUL, t1, t0, s0);
+      add(T_MUL, t1, t0, s1);
+      add(T_TRSL, t1, s0, -1);
+      add(T_TRSL, t1, s1, -1);
+    } else if (t.type == T_TRSU) {
+      if (leaf_block(t.b, t.a)) return;
+      const Cluster& S = ct.cl[t.b];
+      int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
+      add(T_TRSU, t0, s0, -1);
+      add(T_TRSU, t0, s1, -1);
+      add(T_MUL, s0, t0, t1);
+      add(T_MUL, s1, t0, t1);
+      add(T_TRSU, t1, s0, -1);
+      add(T_TRSU, t1, s1, -1);
+    } else {
+      if (leaf_block(t.a, t.b) || leaf_block(t.b, t.c) || leaf_block(t.a, t.c)) return;
+      const Cluster& R = ct.cl[t.b];
+      const Cluster& C = ct.cl[t.c];
+      int ai[2] = {A.son0, A.son1}, bl[2] = {R.son0, R.son1}, cj[2] = {C.son0, C.son1};
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int l = 0; l < 2; ++l) add(T_MUL, ai[i], bl[l], cj[j]);
+    }
+    int cnt = (int)tasks.size() - first;
+    sub_first[g] = first;
+    sub_count[g] = cnt;
+    // automatic local edges: t_i -> t_j for i < j whenever Def 3.2 holds
+    for (int i = 0; i < cnt; ++i)
+      for (int j = i + 1; j < cnt; ++j)
+        if (precedes(first + i, first + j)) succ[first + i].push_back(first + j);
+  }
+};
+
+}  // namespace
+
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g) {
+  auto t0 = std::chrono::steady_clock::now();
+  g = TaskGraph();
+  if (ct.cl.empty()) return;
+  DagBuilder b(ct, bt);
+  b.tasks.reserve(1 << 16);
+  int root = b.add(T_LU, 0, 0, -1);
+  std::vector<int> work{root}, next;
+  std::vector<int> retired;
+  std::vector<int> newsucc;
+  while (!work.empty()) {
+    for (int w : work) b.generate(w);
+    next.clear();
+    for (int w : work) {
+      if (b.sub_count[w] == 0) {
+        // Alg 10: refine the dependencies of an unrefined task
+        bool changed = false;
+        newsucc.clear();
+        for (int x : b.succ[w]) {
+          if (b.sub_count[x] > 0) {
+            changed = true;
+            for (int s = b.sub_first[x]; s < b.sub_first[x] + b.sub_count[x]; ++s)
+              if (b.precedes(w, s)) newsucc.push_back(s);
+          } else if (b.precedes(w, x)) {
+            newsucc.push_back(x);
+          }
+        }
+        b.succ[w] = newsucc;
+        if (changed)
+          next.push_back(w);
+        else
+          retired.push_back(w);
+      } else {
+        // Alg 9: inherit the dependencies on the sub-tasks
+        int f = b.sub_first[w], cnt = b.sub_count[w];
+        for (int x : b.succ[w]) {
+          int xf = x, xc = 1;
+          if (b.sub_count[x] > 0) {
+            xf = b.sub_first[x];
+            xc = b.sub_count[x];
+          }
+          for (int tp = f; tp < f + cnt; ++tp)
+            for (int s = xf; s < xf + xc; ++s)
+              if (b.precedes(tp, s)) b.succ[tp].push_back(s);
+        }
+        for (int tp = f; tp < f + cnt; ++tp) next.push_back(tp);
+      }
+    }
+    // refined tasks leave the graph; mark them so that no stale reference survives
+    for (int w : work)
+      if (b.sub_count[w] > 0) std::vector<int>().swap(b.succ[w]);
+    // sub-task counts only describe refinement within one iteration of Alg 11
+    for (int w : work)
+      if (b.sub_count[w] > 0) b.sub_count[w] = -1;
+    work.swap(next);
+  }
+  // compact the retired tasks into the output graph
+  std::vector<int> remap(b.tasks.size(), -1);
+  g.nodes.reserve(retired.size());
+  for (int r : retired) {
+    remap[r] = (int)g.nodes.size();
+    g.nodes.push_back(b.tasks[r]);
+  }
+  size_t ne = 0;
+  for (int r : retired) ne += b.succ[r].size();
+  g.edges.reserve(ne);
+  for (int r : retired)
+    for (int s : b.succ[r]) g.edges.emplace_back(remap[r], remap[s]);
+  g.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bool compute_levels(TaskGraph& g) {
+  size_t n = g.nodes.size();
+  std::vector<int> indeg(n, 0), start(n + 1, 0), adj(g.edges.size());
+  for (auto& e : g.edges) {
+    indeg[e.second]++;
+    start[e.first + 1]++;
+  }
+  for (size_t i = 0; i < n; ++i) start[i + 1] += start[i];
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (auto& e : g.edges) adj[fill[e.first]++] = e.second;
+  g.level.assign(n, 0);
+  std::deque<int> q;
+  for (size_t i = 0; i < n; ++i)
+    if (indeg[i] == 0) q.push_back((int)i);
+  size_t seen = 0;
+  int maxl = -1;
+  while (!q.empty()) {
+    int t = q.front();
+    q.pop_front();
+    ++seen;
+    if (g.level[t] > maxl) maxl = g.level[t];
+    for (int k = start[t]; k < start[t + 1]; ++k) {
+      int s = adj[k];
+      if (g.level[t] + 1 > g.level[s]) g.level[s] = g.level[t] + 1;
+      if (--indeg[s] == 0) q.push_back(s);
+    }
+  }
+  g.nlevels = maxl + 1;
+  return seen == n;
+}
+
+}  // namespace hm

@@ -1,0 +1,84 @@
+"""Host logic of the CUDA library against the oracle, bit for bit (CPU only).
+
+The library's cluster tree, block tree and Alg 11 task graph are plain host C++; they must
+equal the oracle's exactly (same permutation, same clusters, same leaves and admissibility
+decisions, same task set, same edge set) on the seeded workloads, and the library must load
+and export every function the public header declares.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import hm_workloads as W
+import paper_1911_07531_gb300 as hm
+from oracle import dag as D
+from oracle.trees import BlockTree, ClusterTree
+
+TYPES = {0: D.LU, 1: D.MUL, 2: D.TRSL, 3: D.TRSU}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hm.build_library()
+    return hm.load_library()
+
+
+def test_library_exports_every_header_symbol(lib):
+    names = hm.header_functions()
+    assert "hm_lu" in names and "hm_build" in names and "hm_solve" in names and "hm_matvec" in names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def _compare(points, leaf, eta, check_dag=True):
+    S = hm.hm_structure_build(points, leaf, eta).export()
+    ct = ClusterTree(points, leaf)
+    bt = BlockTree(ct, eta)
+    assert np.array_equal(S["perm"], ct.perm)
+    got = [tuple(r) for r in S["clusters"][:, :4].tolist()]
+    ref = [(c.lo, c.hi, c.sons[0].id if c.sons else -1, c.sons[1].id if c.sons else -1) for c in ct.clusters]
+    assert got == ref
+    lv = {(r, c): a for r, c, a in S["leaves"].tolist()}
+    assert lv == {b.key: int(b.adm) for b in bt.leaves()}
+    if not check_dag:
+        return S
+    b = D.TaskGraphBuilder(ct, bt)
+    nodes, edges = b.compute_dag()
+    tasks = [(TYPES[t[0]], t[1], t[2], t[3]) for t in S["tasks"].tolist()]
+    assert sorted(tasks) == sorted(nodes)
+    e_lib = {(tasks[s], tasks[d]) for s, d in S["edges"].tolist()}
+    assert len(e_lib) == len(S["edges"])
+    assert e_lib == set(edges)
+    lev = D.levels(nodes, edges)
+    assert all(lev[t] == S["levels"][i] for i, t in enumerate(tasks))
+    return S
+
+
+@pytest.mark.parametrize("geom,n,eta", [("line", 512, 0.0), ("line", 128, 2.0), ("sphere", 2048, 2.0),
+                                        ("cube", 3000, 2.0), ("ellipsoid", 1500, 2.0)])
+def test_structure_bit_exact_with_oracle(lib, geom, n, eta):
+    _compare(W.points_for(geom, n, 21), 64, eta)
+
+
+def test_structure_trees_bit_exact_larger(lib):
+    # trees and admissibility only (the oracle's task graph is slow in Python at this size)
+    _compare(W.cube_surface(32768, 31), 64, 2.0, check_dag=False)
+
+
+def test_structure_degenerate_inputs(lib):
+    S = hm.hm_structure_build(np.zeros((1, 3)), 64, 2.0).export()
+    assert S["tasks"].tolist() == [[0, 0, 0, -1]] and len(S["edges"]) == 0
+    # coincident points force the median split
+    p = np.zeros((300, 3))
+    _compare(p, 64, 2.0)
+    with pytest.raises(hm.HMError):
+        hm.hm_structure_build(np.zeros((10, 3)), 0, 2.0)
+
+
+def test_plan_builds_on_host(lib):
+    S = hm.hm_structure_build(W.fibonacci_sphere(4096, 11), 64, 2.0, with_plan=True)
+    i = S.info
+    assert i["plan_launches"] > 0 and i["plan_phases"] >= i["nlevels"]
+    assert i["plan_truncations"] > 0 and i["plan_scratch_bytes"] > 0
