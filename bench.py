@@ -1,0 +1,322 @@
+"""Benchmark: H-LU factorization throughput (model GFLOP/s) on one GB300, plus solve latency.
+
+A step is one hm_lu of the resident H-matrix: the task graph of the paper's semi-automatic
+construction executed wave by wave in batched FP64 kernels (dense leaf LU / solves / GEMMs
+and rounded truncations of every low-rank update).  Default workload: n = 131072 points
+uniform on the unit-cube surface, a_ij = 1/(4 pi (|x_i - x_j| + h)), leaf 64, eta 2,
+eps 1e-6, rank cap 64 (the metric's configuration); the 13 GB of block values are far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line.  N > 1 (torchrun) runs one independent replica per GPU (the H-LU of
+one matrix does not shard); value = all replicas' flops / max wall time.  --impl reference
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hm_workloads as W  # noqa: E402
+
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
+WORKLOAD_TEXT = {
+    "cube131072": "n=131072 uniform on the unit-cube surface, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
+    "sphere32768": "n=32768 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
+    "sphere2048": "n=2048 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-4, rank cap 64, FP64",
+}
+ORACLE_SAMPLE = {"cube131072": ("cube", 2048, 1e-6), "sphere32768": ("sphere", 2048, 1e-6),
+                 "sphere2048": ("sphere", 2048, 1e-4)}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        try:
+            p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                  "--format=csv,noheader,nounits", "-lms", "200"],
+                                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self._p = p
+        for line in p.stdout:
+            if self._stop.is_set():
+                break
+            self.rows.append([x.strip() for x in line.split(",")])
+        p.terminate()
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        try:
+            self._p.terminate()
+        except Exception:
+            pass
+        self._t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(workload, steps=1):
+    """Model GFLOP/s of the FP64 oracle's recursive H-LU on a bounded sample of the workload."""
+    from oracle.hlu import HLUFactor
+    from oracle.hmatrix import HMatrix
+    geom, n, eps = ORACLE_SAMPLE[workload]
+    cfg = W.WORKLOADS[workload]
+    p = W.points_for(geom, n, cfg["seed"])
+    hmo = HMatrix(p, cfg["leaf"], cfg["eta"], eps, cfg["rank_cap"])
+    rates, secs = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        f = HLUFactor(hmo).factor()
+        dt = time.perf_counter() - t0
+        secs.append(dt)
+        rates.append(f.stats.flops / dt * 1e-9)
+    cores = 1
+    try:
+        import threadpoolctl
+        cores = max([1] + [i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": statistics.median(rates), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"recursive FP64 H-LU of n={n} {geom} points (eps {eps}, leaf 64, eta 2, cap 64), "
+                      f"median of {steps} run(s), {statistics.median(secs):.1f} s each",
+            "seconds": statistics.median(secs)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.workload, 1)
+    t0 = time.perf_counter()
+    cb = cpu_oracle_sample(args.workload, args.steps)
+    wall = time.perf_counter() - t0
+    line = {"metric": f"H-LU factorization GFLOP/s (model flops) at {args.workload}", "value": cb["value"],
+            "unit": "GFLOP/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": cb["sample"]},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cube131072", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solves", type=int, default=30)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_1911_07531_gb300 as hm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    hm.build_library()
+    cfg = W.WORKLOADS[args.workload]
+    n = cfg["n"]
+    pts = W.points_for(cfg["geometry"], n, cfg["seed"] + rank)
+    ctx = hm.HMContext(local)
+    stream = ctx.stream
+
+    A = hm.hm_build(ctx, pts, cfg["leaf"], cfg["eta"], cfg["eps"], cfg["rank_cap"])
+    # warm-up (the first hm_lu also builds the task graph and the wave plan on the host)
+    for _ in range(max(args.warmup, 0)):
+        F = hm.hm_lu(ctx, A)
+        F.free()
+    st0 = A.stats()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    flops, step_ms, launches = [], [], 0
+    last = None
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            F = hm.hm_lu(ctx, A)
+            s1.record(stream)
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            fs = F.stats()
+            flops.append(sum(fs["flops"][:4]))
+            launches += fs["launches"]
+            if last is not None:
+                last.free()
+            last = F
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t_wall0
+    total_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([total_ms, sum(flops)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, all_flops = float(mx[0]), float(t[1])
+    else:
+        total_ms_max, all_flops = total_ms, sum(flops)
+    value = all_flops / (total_ms_max * 1e-3) * 1e-9
+    fstats = last.stats()
+
+    # one profiled step: per-kernel-kind device time for the roofline of the dominant kernel
+    ctx.set_profiling(True)
+    Fp = hm.hm_lu(ctx, A)
+    ctx.set_profiling(False)
+    ps = Fp.stats()
+    Fp.free()
+    kind_ms = dict(zip(KINDS, ps["kind_ms"]))
+    kind_fl = dict(zip(KINDS, ps["kind_flops"]))
+    kind_n = dict(zip(KINDS, ps["kind_launches"]))
+    dom = max(KINDS, key=lambda k: kind_ms[k])
+    achieved = kind_fl[dom] / (kind_ms[dom] * 1e-3) * 1e-9 if kind_ms[dom] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_basis": "derived FP64 DFMA peak: 152 SM x 2 FMA/clk x 2 x 2.07 GHz",
+                "launches_per_step": kind_n[dom],
+                "share": kind_ms[dom] / max(sum(kind_ms.values()), 1e-9),
+                "per_kind_ms": {k: round(v, 3) for k, v in kind_ms.items() if v > 0},
+                "per_kind_gflops": {k: round(kind_fl[k] / (kind_ms[k] * 1e-3) * 1e-9, 1)
+                                    for k in KINDS if kind_ms[k] > 0}}
+
+    # solve latency with resident factors (1 right-hand side, device buffers)
+    b = torch.from_numpy(W.gaussian_rhs(n, 1, cfg["rhs_seed"])[:, 0]).to(f"cuda:{local}")
+    x = torch.empty_like(b)
+    lat = []
+    for i in range(args.solves + 2):
+        t0 = time.perf_counter()
+        hm.hm_solve(ctx, last, b, x)
+        dt = time.perf_counter() - t0
+        if i >= 2:
+            lat.append(dt * 1e3)
+    lat.sort()
+    p50 = lat[len(lat) // 2] if lat else None
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None
+
+    # end to end through the public API with host buffers: points -> build -> LU -> solve -> x
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bh = torch.from_numpy(W.gaussian_rhs(n, 1, cfg["rhs_seed"])[:, 0]).pin_memory()
+    A2 = hm.hm_build(ctx, pts, cfg["leaf"], cfg["eta"], cfg["eps"], cfg["rank_cap"])
+    F2 = hm.hm_lu(ctx, A2)
+    bd = bh.to(f"cuda:{local}", non_blocking=True)
+    xd, _ = hm.hm_solve(ctx, F2, bd)
+    xh = xd.cpu()
+    e2e_s = time.perf_counter() - t0
+    e2e_flops = sum(F2.stats()["flops"][:4])
+    F2.free()
+    A2.free()
+    del xh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(args.workload, 1)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": f"H-LU factorization GFLOP/s (model flops) at {args.workload}",
+            "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms_max / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload],
+                       "l2": "no flush: every step reads and writes 13+ GB of block values (L2 is 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "seconds_per_factorization": statistics.median(step_ms) * 1e-3,
+            "model_gflop_per_factorization": statistics.median(flops) * 1e-9,
+            "solves_per_s": 1e3 / statistics.mean(lat) if lat else None,
+            "solve_latency_ms": {"p50": p50, "p99": p99, "nrhs": 1},
+            "e2e": {"value": e2e_flops / e2e_s * 1e-9, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": int(pts.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
+                    "seconds": e2e_s, "includes": "hm_build (points H2D, trees, ACA) + hm_lu (task graph, "
+                                                  "plan, execution) + hm_solve with host RHS and result"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "clocks": clk.summary(),
+            "dag": {"tasks": st0["dag_nodes"], "edges": st0["dag_edges"], "levels": st0["dag_levels"],
+                    "build_s": st0["dag_seconds"], "plan_s": st0["plan_seconds"],
+                    "launches_per_step": st0["plan_launches"], "truncations": st0["plan_truncations"],
+                    "scratch_gb": st0["scratch_bytes"] * 1e-9},
+            "factor": {"max_rank": fstats["max_rank"], "rank_cap_hits": fstats["rank_cap_hits"],
+                       "flops_by_class_gflop": [round(f * 1e-9, 3) for f in fstats["flops"][:4]]},
+            "wall_s": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -111,6 +111,8 @@ typedef struct {
   int64_t aca_unconverged;      /* ACA runs that hit their rank limit during hm_build    */
   double kind_ms[8];            /* with profiling on: device ms per kernel kind          */
   int64_t kind_launches[8];     /*   getrf trsm gemm copy stack core eval aca            */
+  double kind_flops[8];         /* algorithmic flops executed per kernel kind (last hm_lu) */
+  int64_t launches;             /* kernel launches of the last hm_lu                     */
 } hm_stats;
 
 /* Last error message of the calling thread ("" if none). */

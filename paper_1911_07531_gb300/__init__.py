@@ -70,7 +70,8 @@ class Stats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("flops", ctypes.c_double * 5), ("rank_cap_hits", ctypes.c_int64),
                 ("singular_pivots", ctypes.c_int64), ("aca_unconverged", ctypes.c_int64),
-                ("kind_ms", ctypes.c_double * 8), ("kind_launches", ctypes.c_int64 * 8)]
+                ("kind_ms", ctypes.c_double * 8), ("kind_launches", ctypes.c_int64 * 8),
+                ("kind_flops", ctypes.c_double * 8), ("launches", ctypes.c_int64)]
 
     def to_dict(self):
         d = {}

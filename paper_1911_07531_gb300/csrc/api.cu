@@ -236,21 +236,23 @@ int read_ranks(hm_ctx* c, const Buf& ranks, int nr, int64_t* maxr, int64_t* sumr
   return HM_OK;
 }
 
+constexpr int NCOUNT = NFC + NKIND;
+
 struct Counters {
-  Buf b;   // NFC unsigned long long + 4 ints
+  Buf b;   // NCOUNT unsigned long long + 4 ints
   unsigned long long* flops() { return (unsigned long long*)b.p; }
-  int* status() { return (int*)((char*)b.p + NFC * sizeof(unsigned long long)); }
+  int* status() { return (int*)((char*)b.p + NCOUNT * sizeof(unsigned long long)); }
 };
 
 int counters_init(hm_ctx* c, Counters& k) {
-  if (!dalloc(c, k.b, NFC * sizeof(unsigned long long) + 4 * sizeof(int)))
+  if (!dalloc(c, k.b, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int)))
     return fail(HM_ENOMEM, "allocator returned NULL (counters)");
-  CU(cudaMemsetAsync(k.b.p, 0, NFC * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
+  CU(cudaMemsetAsync(k.b.p, 0, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
   return HM_OK;
 }
 
 int counters_read(hm_ctx* c, Counters& k, unsigned long long* fl, int* st) {
-  CU(cudaMemcpyAsync(fl, k.b.p, NFC * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(fl, k.b.p, NCOUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaMemcpyAsync(st, k.status(), 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return HM_OK;
@@ -407,7 +409,7 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
     B.flops = k.flops();
     B.status = k.status();
     rc = run_plan(c, dp, B, A->h, nullptr);
-    unsigned long long fl[NFC];
+    unsigned long long fl[NCOUNT];
     int st[4];
     if (rc == HM_OK) rc = counters_read(c, k, fl, st);
     cudaEventRecord(e1, s);
@@ -521,7 +523,7 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   cudaEventDestroy(e1);
   if (rc) return cleanup(rc);
   if (se) return cleanup(fail(HM_ECUDA, std::string("hm_lu: ") + cudaGetErrorString(se)));
-  unsigned long long fl[NFC];
+  unsigned long long fl[NCOUNT];
   int st[4];
   if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
   fill_matrix_stats(A, &F->st);
@@ -533,7 +535,9 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   for (int q = 0; q < NKIND; ++q) {
     F->st.kind_ms[q] = prof.ms[q];
     F->st.kind_launches[q] = prof.launches[q];
+    F->st.kind_flops[q] = (double)fl[NFC + q];
   }
+  F->st.launches = (int64_t)P.launches.size();
   if ((rc = read_ranks(c, F->ranks, A->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
   dfree(c, sd);
   dfree(c, si);
@@ -786,7 +790,7 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   const int64_t oGz = off; off += al((int64_t)Kc * Kc);
   const int64_t oTw = off; off += al((int64_t)Kc * capk);
   const int64_t oTz = off; off += al((int64_t)Kc * capk);
-  const int64_t oWk = off; off += al(4 * (int64_t)Kc * Kc);
+  const int64_t oWk = off; off += al(2 * (int64_t)Kc * Kc);
   Buf sd, si, ops, ent;
   Counters k;
   auto done = [&](int r) {

@@ -157,8 +157,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
           }
         }
     }
-  if (tid == 0 && op.fclass < FC_NONE)
-    atomicAdd(&B.flops[op.fclass], (unsigned long long)(2.0 * m * n * (double)(k > 0 ? k : 0)));
+  if (tid == 0) {
+    const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)(k > 0 ? k : 0));
+    if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
+    atomicAdd(&B.flops[NFC + K_GEMM], f);
+  }
 }
 
 // ------------------------------------------------------------------------------ TRSM
@@ -265,7 +268,10 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
     }
     __syncthreads();
   }
-  if (tid == 0) atomicAdd(&B.flops[FC_TRSM], (unsigned long long)nv * b * b);
+  if (tid == 0) {
+    atomicAdd(&B.flops[FC_TRSM], (unsigned long long)nv * b * b);
+    atomicAdd(&B.flops[NFC + K_TRSM], (unsigned long long)nv * b * b);
+  }
 }
 
 // ------------------------------------------------------------------------------ GETRF
@@ -322,7 +328,10 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
     __syncthreads();
   }
   for (int e = tid; e < b * b; e += 256) A[e] = S[e % b][e / b];
-  if (tid == 0) atomicAdd(&B.flops[FC_GETRF], (unsigned long long)(2.0 * b * b * b / 3.0));
+  if (tid == 0) {
+    atomicAdd(&B.flops[FC_GETRF], (unsigned long long)(2.0 * b * b * b / 3.0));
+    atomicAdd(&B.flops[NFC + K_GETRF], (unsigned long long)(2.0 * b * b * b / 3.0));
+  }
 }
 
 // ------------------------------------------------------------------------------ COPY
@@ -489,13 +498,13 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     if (tid == 0) *rk = 0;
     return;
   }
-  const double* Gw = dptr(B, op.Gw);
-  const double* Gz = dptr(B, op.Gz);
+  double* Gw = dptr(B, op.Gw);
+  double* Gz = dptr(B, op.Gz);
   double* work = dptr(B, op.work);
-  double* R = work;                            // K x K (ld Kc): equilibrated Gram -> Cholesky
-  double* Bm = work + (int64_t)Kc * Kc;        // K x r
-  double* T1 = work + 2 * (int64_t)Kc * Kc;    // K x r
-  double* M = work + 3 * (int64_t)Kc * Kc;     // r x r (global fallback for Jacobi)
+  double* R = Gw;                              // K x K (ld Kc): equilibrated Gram -> Cholesky, in place
+  double* Bm = work;                           // K x r
+  double* T1 = work + (int64_t)Kc * Kc;        // K x r
+  double* M = Gz;                              // r x r (global fallback for Jacobi; Gz is dead by then)
   // 1. equilibrate the Gram matrix of the stacked left factor
   for (int i = tid; i < K; i += nt) {
     double g = Gw[i + (int64_t)i * Kc];
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
   __syncthreads();
   for (int e = tid; e < K * K; e += nt) {
     int i = e % K, j = e / K;
-    R[i + (int64_t)j * Kc] = Gw[i + (int64_t)j * Kc] / (d[i] * d[j]);
+    R[i + (int64_t)j * Kc] = R[i + (int64_t)j * Kc] / (d[i] * d[j]);
   }
   __syncthreads();
   // 2. pivoted Cholesky G = Pi R^T R Pi^T (upper R in pivoted order, stored in place);
@@ -700,6 +709,8 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     };
     double f = qr(m, Kd) + qr(n, Kd) + 23.0 * Kd * Kd * Kd + 2.0 * (m + n) * Kd * kk;
     atomicAdd(&B.flops[FC_TRUNC], (unsigned long long)f);
+    // the core's own share of the model: product of the triangular factors + SVD of K x K
+    atomicAdd(&B.flops[NFC + K_CORE], (unsigned long long)(23.0 * Kd * Kd * Kd));
   }
 }
 

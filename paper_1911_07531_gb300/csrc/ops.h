@@ -27,7 +27,8 @@ inline uint64_t mkref(int space, int64_t off) { return ((uint64_t)(space + 1) <<
 struct Bases {
   double* d[NDSPACE];
   int* i[NISPACE];
-  unsigned long long* flops;   // per-kernel-class model flop counters
+  unsigned long long* flops;   // [0, NFC): model flops per class; [NFC, NFC+NKIND): algorithmic
+                               // flops executed by each kernel kind
   int* status;                 // [0] singular pivot count, [1] rank-cap hits, [2] aca non-converged
 };
 
@@ -100,7 +101,7 @@ struct TruncOp {
   uint64_t Wst, Zst;   // m x Kcap and n x Kcap stacks
   uint64_t Gw, Gz;     // Kcap x Kcap Gram matrices (ld Kcap)
   uint64_t Tw, Tz;     // Kcap x cap coefficient matrices (ld Kcap)
-  uint64_t work;       // 4 * Kcap * Kcap doubles
+  uint64_t work;       // 2 * Kcap * Kcap doubles (Gw and Gz are reused by the core)
   uint64_t Kd;         // int ref: stacked rank
   double eps;
 };

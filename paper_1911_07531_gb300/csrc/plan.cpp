@@ -499,14 +499,29 @@ struct Ctx {
     apply_pieces(Cn, pieces);
   }
 
-  // rounded additions of all pieces that reached low-rank leaves in this wave
-  void emit_truncations(int ph0, double eps, bool target_rank_zero = false) {
-    for (const TargetEntries& T : w.targets) {
+  // rounded additions of all pieces that reached low-rank leaves in this wave. A target whose
+  // pieces exceed KMAX_STACK columns is updated in rounds (chunk r+1 after chunk r). The
+  // truncations of one round run in batches whose scratch fits `budget`; every batch reuses
+  // the same scratch region (they are sequential phases), so a wave's scratch is its product
+  // temporaries plus one batch.
+  void emit_truncations(int ph0, double eps, bool target_rank_zero = false, int64_t budget = (int64_t)1 << 29) {
+    const int64_t base = w.sd;
+    plan.scratch_products_max = std::max(plan.scratch_products_max, base);
+    // chunking of every target
+    struct Chunk {
+      int target;
+      size_t e0, e1;
+      int Kc;
+      bool zero_self;
+    };
+    std::vector<std::vector<Chunk>> rounds;
+    for (size_t ti = 0; ti < w.targets.size(); ++ti) {
+      const TargetEntries& T = w.targets[ti];
       const LeafStore& L = lay.leaf[T.leaf];
-      const int selfmax = target_rank_zero ? 0 : L.cap;
       size_t e0 = 0;
       int round = 0;
       while (e0 < T.e.size()) {
+        const int selfmax = (target_rank_zero && round == 0) ? 0 : L.cap;
         int sum = selfmax;
         size_t e1 = e0;
         while (e1 < T.e.size() && (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
@@ -514,8 +529,27 @@ struct Ctx {
           ++e1;
         }
         if (sum > KMAX_STACK) throw std::runtime_error("planner: piece rank exceeds the stack limit");
-        const int Kc = (sum + 1) / 2 * 2;
-        const int ph = ph0 + 4 * round;
+        if ((int)rounds.size() <= round) rounds.resize(round + 1);
+        rounds[round].push_back({(int)ti, e0, e1, std::max(2, (sum + 1) / 2 * 2), selfmax == 0});
+        e0 = e1;
+        ++round;
+      }
+    }
+    int batch = 0;
+    int64_t peak = 0;
+    for (const auto& rd : rounds) {
+      w.sd = base;
+      bool opened = false;
+      for (const Chunk& ch : rd) {
+        const LeafStore& L = lay.leaf[w.targets[ch.target].leaf];
+        const int Kc = ch.Kc;
+        const int64_t need = (int64_t)(L.m + L.n) * Kc + 4 * (int64_t)Kc * Kc + 2 * (int64_t)Kc * L.cap + 8 * ALIGN;
+        if (opened && w.sd + need - base > budget) {
+          ++batch;
+          w.sd = base;
+        }
+        opened = true;
+        const int ph = ph0 + 4 * batch;
         w.need(ph + 3);
         TruncOp op;
         std::memset(&op, 0, sizeof(op));
@@ -532,11 +566,13 @@ struct Ctx {
         op.Gz = sref(w.alloc_d((int64_t)Kc * Kc));
         op.Tw = sref(w.alloc_d((int64_t)Kc * L.cap));
         op.Tz = sref(w.alloc_d((int64_t)Kc * L.cap));
-        op.work = sref(w.alloc_d(4 * (int64_t)Kc * Kc));
+        op.work = sref(w.alloc_d(2 * (int64_t)Kc * Kc));
         op.Kd = mkref(IS_S, w.alloc_i(1));
         op.eps = eps;
+        peak = std::max(peak, w.sd);
         std::vector<StackEntry> es;
-        for (size_t q = e0; q < e1; ++q) es.push_back(T.e[q].first);
+        const TargetEntries& T = w.targets[ch.target];
+        for (size_t q = ch.e0; q < ch.e1; ++q) es.push_back(T.e[q].first);
         w.stack[ph].push_back(op);
         w.stack_entries[ph].push_back(es);
         const Dim Kd{0, op.Kd};
@@ -555,11 +591,11 @@ struct Ctx {
         gemm(ph + 3, op.Wst, 1, L.m, op.Tw, 1, Kc, op.U, 1, L.m, {L.m, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
         gemm(ph + 3, op.Zst, 1, L.n, op.Tz, 1, Kc, op.V, 1, L.n, {L.n, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
         plan.ntrunc++;
-        e0 = e1;
-        ++round;
-        target_rank_zero = false;
       }
+      if (opened) ++batch;
     }
+    w.sd = std::max(base, peak);
+    plan.scratch_trunc_max = std::max(plan.scratch_trunc_max, w.sd - base);
   }
 
   // append the wave's phases to the plan in execution order

@@ -51,6 +51,8 @@ struct Plan {
   int nphases = 0;
   int ntasks = 0;
   int64_t ntrunc = 0;
+  int64_t scratch_products_max = 0;   // largest product / solve scratch of one wave (doubles)
+  int64_t scratch_trunc_max = 0;      // largest truncation scratch of one wave (doubles)
 };
 
 // Memory spaces the planner addresses (factor vs. matrix storage).
