@@ -153,7 +153,7 @@ def main():
     ap.add_argument("--workload", default="cube131072", choices=sorted(W.WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--solves", type=int, default=30)
+    ap.add_argument("--solves", type=int, default=10)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

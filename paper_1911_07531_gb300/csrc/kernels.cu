@@ -85,79 +85,118 @@ __device__ __forceinline__ int block_argmax(double v, int idx, double* redv, int
 }
 
 // ------------------------------------------------------------------------------ GEMM
-constexpr int GT = 64;   // output tile edge
-constexpr int GK = 16;   // reduction slice
+// One CTA (256 threads) per micro-op. The output is covered by TM x TN tiles; S groups of
+// threads split the reduction of each tile and are summed in shared memory at the end. The
+// tile shape is chosen per micro-op from its (dynamic) sizes so that few DFMAs are spent on
+// zero padding: the micro-ops are mostly thin (a rank-sized side of 10-60) or have a small
+// output with a long reduction (Gram matrices, V^T X).
+constexpr int GK = 16;                 // reduction slice
+constexpr int GEMM_SMEM_DOUBLES = 5248;
 
-__global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
-  const GemmOp op = ops[blockIdx.x];
-  const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = dimv(B, op.k, op.kd);
-  if (m <= 0 || n <= 0) return;
-  if (k <= 0 && !(op.flags & GF_OVERWRITE)) return;
-  const double* __restrict__ A = dptr(B, op.A);
-  const double* __restrict__ Bm = dptr(B, op.B);
-  double* C = dptr(B, op.C);
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+template <int TM, int TN, int RM, int RN, int S>
+__device__ __forceinline__ void gemm_tiles(const GemmOp& op, int m, int n, int k, const double* __restrict__ A,
+                                           const double* __restrict__ Bm, double* C, double* sm) {
+  constexpr int TX = TN / RN, TY = TM / RM, G = TX * TY;
+  static_assert(G * S == 256, "256 threads");
+  static_assert(S * GK * (TM + 1) + S * GK * (TN + 1) + (S > 1 ? TM * TN : 0) <= GEMM_SMEM_DOUBLES, "smem");
+  double* As = sm;                                  // [S][GK][TM+1]
+  double* Bs = sm + S * GK * (TM + 1);              // [S][GK][TN+1]
+  double* red = Bs + S * GK * (TN + 1);             // [TM*TN] when S > 1
+  const int tid = threadIdx.x, g = tid / G, t = tid % G, tx = t % TX, ty = t / TX;
   const bool a_i_fast = op.a_rs <= op.a_cs;
   const bool b_j_fast = op.b_cs <= op.b_rs;
   const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
-  for (int i0 = 0; i0 < m; i0 += GT)
-    for (int j0 = 0; j0 < n; j0 += GT) {
-      double acc[4][4];
+  for (int i0 = 0; i0 < m; i0 += TM)
+    for (int j0 = 0; j0 < n; j0 += TN) {
+      double acc[RM][RN];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int p = 0; p < RM; ++p)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-      for (int l0 = 0; l0 < k; l0 += GK) {
-        for (int e = tid; e < GK * GT; e += 256) {
+        for (int q = 0; q < RN; ++q) acc[p][q] = 0.0;
+      for (int L0 = 0; L0 < k; L0 += S * GK) {
+        // every group stages its own slice l0 = L0 + g*GK
+        for (int e = tid; e < S * GK * TM; e += 256) {
+          int gg = e / (GK * TM), r = e % (GK * TM);
           int i, l;
-          if (a_i_fast) { i = e % GT; l = e / GT; } else { l = e % GK; i = e / GK; }
-          int gi = i0 + i, gl = l0 + l;
+          if (a_i_fast) { i = r % TM; l = r / TM; } else { l = r % GK; i = r / GK; }
+          int gi = i0 + i, gl = L0 + gg * GK + l;
           double v = 0.0;
           if (gi < m && gl < k) {
             if (unitlower) v = gi > gl ? A[gi * op.a_rs + gl * op.a_cs] : (gi == gl ? 1.0 : 0.0);
             else if (upper) v = gl >= gi ? A[gi * op.a_rs + gl * op.a_cs] : 0.0;
             else v = A[gi * op.a_rs + gl * op.a_cs];
           }
-          As[l][i] = v;
+          As[(gg * GK + l) * (TM + 1) + i] = v;
         }
-        for (int e = tid; e < GK * GT; e += 256) {
+        for (int e = tid; e < S * GK * TN; e += 256) {
+          int gg = e / (GK * TN), r = e % (GK * TN);
           int j, l;
-          if (b_j_fast) { j = e % GT; l = e / GT; } else { l = e % GK; j = e / GK; }
-          int gj = j0 + j, gl = l0 + l;
-          Bs[l][j] = (gj < n && gl < k) ? Bm[gl * op.b_rs + gj * op.b_cs] : 0.0;
+          if (b_j_fast) { j = r % TN; l = r / TN; } else { l = r % GK; j = r / GK; }
+          int gj = j0 + j, gl = L0 + gg * GK + l;
+          Bs[(gg * GK + l) * (TN + 1) + j] = (gj < n && gl < k) ? Bm[gl * op.b_rs + gj * op.b_cs] : 0.0;
         }
         __syncthreads();
-#pragma unroll
+        const double* Ag = As + g * GK * (TM + 1);
+        const double* Bg = Bs + g * GK * (TN + 1);
+#pragma unroll 4
         for (int l = 0; l < GK; ++l) {
-          double a[4], b[4];
+          double a[RM], b[RN];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) a[q] = As[l][ty + 16 * q];
+          for (int p = 0; p < RM; ++p) a[p] = Ag[l * (TM + 1) + ty + TY * p];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = Bs[l][tx + 16 * q];
+          for (int q = 0; q < RN; ++q) b[q] = Bg[l * (TN + 1) + tx + TX * q];
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+          for (int p = 0; p < RM; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+            for (int q = 0; q < RN; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
         }
         __syncthreads();
       }
+      if (S > 1) {
+        for (int e = tid; e < TM * TN; e += 256) red[e] = 0.0;
+        __syncthreads();
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < RM; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int i = i0 + ty + 16 * p, j = j0 + tx + 16 * q;
-          if (i < m && j < n) {
-            double* c = C + (int64_t)i * op.c_rs + (int64_t)j * op.c_cs;
-            double v = op.alpha * acc[p][q];
-            if (op.flags & GF_ATOMIC) atomicAdd(c, v);
-            else if (op.flags & GF_OVERWRITE) *c = v;
-            else *c += v;
+          for (int q = 0; q < RN; ++q) atomicAdd(&red[(ty + TY * p) * TN + tx + TX * q], acc[p][q]);
+        __syncthreads();
+      }
+      if (S == 1 || g == 0) {
+#pragma unroll
+        for (int p = 0; p < RM; ++p)
+#pragma unroll
+          for (int q = 0; q < RN; ++q) {
+            const int il = ty + TY * p, jl = tx + TX * q;
+            const int i = i0 + il, j = j0 + jl;
+            if (i < m && j < n) {
+              double* c = C + (int64_t)i * op.c_rs + (int64_t)j * op.c_cs;
+              const double v = op.alpha * (S > 1 ? red[il * TN + jl] : acc[p][q]);
+              if (op.flags & GF_ATOMIC) atomicAdd(c, v);
+              else if (op.flags & GF_OVERWRITE) *c = v;
+              else *c += v;
+            }
           }
-        }
+      }
+      if (S > 1) __syncthreads();
     }
-  if (tid == 0) {
+}
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
+  const GemmOp op = ops[blockIdx.x];
+  const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = dimv(B, op.k, op.kd);
+  if (m <= 0 || n <= 0) return;
+  if (k <= 0 && !(op.flags & GF_OVERWRITE)) return;
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const double* A = dptr(B, op.A);
+  const double* Bm = dptr(B, op.B);
+  double* C = dptr(B, op.C);
+  if (m <= 16 && n <= 16) gemm_tiles<16, 16, 2, 2, 4>(op, m, n, k, A, Bm, C, sm);
+  else if (m <= 32 && n <= 32) gemm_tiles<32, 32, 4, 4, 4>(op, m, n, k, A, Bm, C, sm);
+  else if (n <= 16) gemm_tiles<256, 16, 16, 1, 1>(op, m, n, k, A, Bm, C, sm);
+  else if (n <= 32) gemm_tiles<128, 32, 8, 2, 1>(op, m, n, k, A, Bm, C, sm);
+  else if (m <= 32) gemm_tiles<32, 128, 2, 8, 1>(op, m, n, k, A, Bm, C, sm);
+  else gemm_tiles<64, 64, 4, 4, 1>(op, m, n, k, A, Bm, C, sm);
+  if (threadIdx.x == 0) {
     const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)(k > 0 ? k : 0));
     if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
     atomicAdd(&B.flops[NFC + K_GEMM], f);
@@ -173,12 +212,16 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
   double(*T)[65] = reinterpret_cast<double(*)[65]>(trsm_smem);
   double(*X)[65] = reinterpret_cast<double(*)[65]>(trsm_smem + 64 * 65);
   __shared__ int piv[64];
+  __shared__ double dinv[64];
   const int tid = threadIdx.x;
   const double* Tg = dptr(B, op.T);
   double* Xg = dptr(B, op.X);
   for (int e = tid; e < b * b; e += 256) T[e % b][e / b] = Tg[e];
   if (op.piv)
     for (int e = tid; e < b; e += 256) piv[e] = iptr(B, op.piv)[e];
+  __syncthreads();
+  if (op.mode == TM_UT || op.mode == TM_U)
+    for (int e = tid; e < b; e += 256) dinv[e] = 1.0 / T[e][e];
   __syncthreads();
   const bool e_fast = op.x_es == 1;
   for (int v0 = 0; v0 < nv; v0 += 64) {
@@ -210,7 +253,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
       }
     } else if (op.mode == TM_UT) {
       for (int j = 0; j < b; ++j) {
-        if (tid < nc) X[j][tid] = X[j][tid] / T[j][j];
+        if (tid < nc) X[j][tid] = X[j][tid] * dinv[j];
         __syncthreads();
         int cnt = (b - 1 - j) * nc;
         for (int e = tid; e < cnt; e += 256) {
@@ -221,7 +264,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
       }
     } else if (op.mode == TM_U) {
       for (int j = b - 1; j >= 0; --j) {
-        if (tid < nc) X[j][tid] = X[j][tid] / T[j][j];
+        if (tid < nc) X[j][tid] = X[j][tid] * dinv[j];
         __syncthreads();
         int cnt = j * nc;
         for (int e = tid; e < cnt; e += 256) {
@@ -317,7 +360,8 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
     if (d == 0.0) {
       if (tid == 0) atomicAdd(&B.status[0], 1);
     } else {
-      for (int i = j + 1 + tid; i < b; i += 256) S[i][j] = S[i][j] / d;
+      const double dinv = 1.0 / d;
+      for (int i = j + 1 + tid; i < b; i += 256) S[i][j] = S[i][j] * dinv;
     }
     __syncthreads();
     const int r = b - 1 - j;
@@ -418,16 +462,21 @@ __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
 }
 
 // ------------------------------------------------------------------------------ CORE
-// Cyclic parallel Jacobi for a symmetric K x K matrix (K even): A <- J^T A J until the
-// off-diagonal part is negligible relative to the diagonal, V <- V J.  The rotation of
-// each pair is the classical one that annihilates A_pq (Golub & Van Loan, "Matrix
-// Computations", symmetric Schur decomposition); the K/2 disjoint pairs of one round of a
-// round-robin tournament are rotated together.
+// Cyclic parallel Jacobi for a symmetric K x K matrix (K even): A <- J^T A J until no
+// off-diagonal entry is significant, V <- V J.  The rotation of each pair is the classical
+// one that annihilates A_pq (Golub & Van Loan, "Matrix Computations", symmetric Schur
+// decomposition); the K/2 disjoint pairs of one round of a round-robin tournament are rotated
+// together.  FP64 division and square root are long FMA sequences on this GPU, so the angle
+// t = tan(theta) is computed in FP32 from exactly formed FP64 differences (its relative
+// error only slows convergence from quadratic to a factor 1e-7 per sweep), and
+// c = 1/sqrt(1 + t^2), s = t c are then made orthogonal to FP64 accuracy by two Newton steps.
+// An entry is significant if A_pq^2 > u^2 |A_pp A_qq| and |A_pq| > abs_tol (the absolute
+// floor keeps noise-level eigenvalues from being chased to the sweep limit).
 __device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, double* cs,
-                             double* sn, int* pa, int* pb, int* flag) {
+                             double* sn, int* pa, int* pb, int* flag, double abs_tol) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int half = K / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  for (int sweep = 0; sweep < 40; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int r = 0; r < K - 1; ++r) {
@@ -438,16 +487,26 @@ __device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, doub
         int a = min(x, y), b = max(x, y);
         pa[q] = a;
         pb[q] = b;
-        double app = A[a + (int64_t)a * lda], aqq = A[b + (int64_t)b * lda], apq = A[a + (int64_t)b * lda];
+        const double app = A[a + (int64_t)a * lda], aqq = A[b + (int64_t)b * lda], apq = A[a + (int64_t)b * lda];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > 2.2e-16 * sqrt(fabs(app * aqq)) && apq != 0.0) {
-          double tau = (aqq - app) / (2.0 * apq);
-          double t;
-          if (fabs(tau) > 1e150) t = 0.5 / tau;
-          else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-          *flag = 1;
+        const double aa = fabs(apq);
+        if (aa > abs_tol && aa * aa > 4.9e-32 * fabs(app * aqq)) {
+          // scale the two FP64 operands of theta by a power of two into FP32 range
+          const double num = aqq - app, den = 2.0 * apq;
+          int e;
+          frexp(fmax(fabs(num), fabs(den)), &e);
+          const float th = (float)ldexp(num, -e) / (float)ldexp(den, -e);
+          float tf;
+          if (!(fabsf(th) < 1e18f)) tf = 0.0f;
+          else tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+          const double t = (double)tf;
+          const double x2 = fma(t, t, 1.0);
+          double yv = (double)rsqrtf((float)x2);
+          yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
+          yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
+          c = yv;
+          s = t * yv;
+          if (s != 0.0) *flag = 1;
         }
         cs[q] = c;
         sn[q] = s;
@@ -488,7 +547,7 @@ constexpr int JSM = 64;         // Jacobi problems up to this size run in shared
 __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, Bases B) {
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
-  __shared__ double d[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
+  __shared__ double d[KMAX], dinv[KMAX], rdinv[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
   __shared__ int perm[KMAX], pa[KMAX / 2], pb[KMAX / 2], order[KMAX], s_int[4];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int K = *iptr(B, op.Kd);
@@ -509,12 +568,13 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
   for (int i = tid; i < K; i += nt) {
     double g = Gw[i + (int64_t)i * Kc];
     d[i] = g > 0.0 ? sqrt(g) : 1.0;
+    dinv[i] = 1.0 / d[i];
     perm[i] = i;
   }
   __syncthreads();
   for (int e = tid; e < K * K; e += nt) {
     int i = e % K, j = e / K;
-    R[i + (int64_t)j * Kc] = R[i + (int64_t)j * Kc] / (d[i] * d[j]);
+    R[i + (int64_t)j * Kc] = R[i + (int64_t)j * Kc] * (dinv[i] * dinv[j]);
   }
   __syncthreads();
   // 2. pivoted Cholesky G = Pi R^T R Pi^T (upper R in pivoted order, stored in place);
@@ -551,10 +611,11 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     // R is kept in original index space: row pj of the factor is stored in column pj
     const int pj = perm[j];
     const double rjj = sqrt(piv);
+    const double rinv = 1.0 / rjj;
     // column j of R^T in pivoted order: l_i = G(pi_i, pj) / rjj for i > j
     for (int i = j + 1 + tid; i < K; i += nt) {
       int pi = perm[i];
-      R[pi + (int64_t)pj * Kc] = R[pi + (int64_t)pj * Kc] / rjj;
+      R[pi + (int64_t)pj * Kc] = R[pi + (int64_t)pj * Kc] * rinv;
     }
     if (tid == 0) R[pj + (int64_t)pj * Kc] = rjj;
     __syncthreads();
@@ -643,8 +704,15 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     Yj[p + (int64_t)q * ldj] = (p == q) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // 5. eigen-decomposition of M = Y S Y^T (S = sigma^2 of the stacked product)
-  jacobi_eigen(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1]);
+  // 5. eigen-decomposition of M = Y S Y^T (S = sigma^2 of the stacked product); entries
+  //    below 1e-17 trace(M) are noise of the Gram formation and are not rotated away
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int q = 0; q < r; ++q) tr += fabs(Mj[q + (int64_t)q * ldj]);
+    red[1] = tr;
+  }
+  __syncthreads();
+  jacobi_eigen(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * red[1]);
   __syncthreads();
   for (int q = tid; q < r; q += nt) lam[q] = Mj[q + (int64_t)q * ldj];
   __syncthreads();
@@ -673,13 +741,19 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
   // 7. coefficient matrices: Tz = Bm Y_k S_k^{-1/2}, Tw = D^{-1} Pi_r Rf11^{-1} Y_k S_k^{1/2}
   double* Tw = dptr(B, op.Tw);
   double* Tz = dptr(B, op.Tz);
+  __syncthreads();
+  if (tid < kk) {
+    const double sg = sqrt(lam[order[tid]]);
+    cs[tid] = sg;          // sigma of the c-th kept direction
+    sn[tid] = 1.0 / sg;
+  }
+  __syncthreads();
   for (int e = tid; e < K * kk; e += nt) {
     int i = e % K, c = e / K;
     int q = order[c];
-    double sig = sqrt(lam[q]);
     double s = 0.0;
     for (int p = 0; p < r; ++p) s = fma(Bm[i + (int64_t)p * Kc], Yj[p + (int64_t)q * ldj], s);
-    Tz[i + (int64_t)c * Kc] = s / sig;
+    Tz[i + (int64_t)c * Kc] = s * sn[c];
   }
   // back substitution Rf11 x = Y_k S^{1/2} (Rf11 upper r x r in pivoted order); x lives in
   // rows perm[0..r) of Tw, the other rows of Tw are zero.
@@ -688,16 +762,24 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     Tw[i + (int64_t)c * Kc] = 0.0;
   }
   __syncthreads();
+  // reciprocals of the Cholesky diagonal
+  for (int l = tid; l < r; l += nt) rdinv[l] = 1.0 / R[perm[l] + (int64_t)perm[l] * Kc];
+  __syncthreads();
   for (int c = tid; c < kk; c += nt) {
     int q = order[c];
-    double sig = sqrt(lam[q]);
+    double sig = cs[c];
     for (int l = r - 1; l >= 0; --l) {
       double s = Yj[l + (int64_t)q * ldj] * sig;
       for (int p = l + 1; p < r; ++p)
-        s -= R[perm[p] + (int64_t)perm[l] * Kc] * Tw[perm[p] + (int64_t)c * Kc];
-      Tw[perm[l] + (int64_t)c * Kc] = s / R[perm[l] + (int64_t)perm[l] * Kc];
+        s = fma(-R[perm[p] + (int64_t)perm[l] * Kc], Tw[perm[p] + (int64_t)c * Kc], s);
+      Tw[perm[l] + (int64_t)c * Kc] = s * rdinv[l];
     }
-    for (int l = 0; l < r; ++l) Tw[perm[l] + (int64_t)c * Kc] /= d[perm[l]];
+  }
+  __syncthreads();
+  // undo the equilibration: rows of Tw scale by 1/d_i
+  for (int e = tid; e < K * kk; e += nt) {
+    int i = e % K, c = e / K;
+    Tw[i + (int64_t)c * Kc] *= dinv[i];
   }
   __syncthreads();
   if (tid == 0) {
