@@ -163,6 +163,26 @@ int hm_factor_stats(const hm_factor* F, hm_stats* out);
 int hm_truncate(hm_ctx* ctx, int64_t m, int64_t n, int K, const double* W, int64_t ldw, const double* Z,
                 int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V, int64_t ldv, int* k_out);
 
+/* Same rounded truncation as hm_truncate, for callers that must not allocate device memory
+ * (a serving loop whose device buffers are all sized at start-up, or a plugin living in
+ * another framework's memory pool with no allocator to hand to hm_ctx_create). The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. Its scratch is a
+ *     file-scope device array of 16 MiB (2^21 doubles) that every GPU loading the library holds
+ *     until the process exits. Sizes beyond it are rejected with HM_EINVAL; m + n <= 8192
+ *     with K <= 128 always fits.
+ *   - Runs on the current device and the given stream (NULL = legacy default stream); the
+ *     caller passes W, Z (inputs) and U, V (outputs, at least min(cap, m, n) columns) as
+ *     device buffers; *k_out (host) receives the rank. Synchronizes the stream.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents (the entry point
+ *     clears what must start at zero): calls that overlap on the GPU (other streams, other
+ *     host threads) race and must be serialized by the caller. */
+int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int K, const double* W, int64_t ldw,
+                        const double* Z, int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V,
+                        int64_t ldv, int* k_out);
+
 /* ---- host-only structure (no GPU needed): cluster tree, block tree, task graph -------- */
 typedef struct {
   int64_t n, nclusters, nleaves, ntasks, nedges, nlevels;

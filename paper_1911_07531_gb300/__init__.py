@@ -23,7 +23,7 @@ from .build import LIB, build as _build_lib
 
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
-    "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate",
+    "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
     "hm_structure_build", "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
 ]
@@ -131,6 +131,7 @@ def load_library():
         "hm_matrix_stats": ([P, ctypes.POINTER(Stats)], I),
         "hm_factor_stats": ([P, ctypes.POINTER(Stats)], I),
         "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
+        "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
         "hm_structure_export": ([P, P, P, P, P, P, P], I),
@@ -322,6 +323,31 @@ def hm_truncate(ctx, W, Z, eps, cap=64):
     k = ctypes.c_int(0)
     _check(load_library().hm_truncate(ctx.handle, m, n, K, Wf.data_ptr(), m, Zf.data_ptr(), n, float(eps), int(cap),
                                       U.data_ptr(), m, V.data_ptr(), n, ctypes.byref(k)))
+    return U[:, :k.value], V[:, :k.value]
+
+
+def hm_truncate_noalloc(W, Z, eps, cap=64, stream=None):
+    """hm_truncate without any device allocation inside the library (static scratch).
+
+    For callers that cannot allocate device memory on their call path; the outputs U, V are
+    allocated here by the caller side (PyTorch) before the call, the library itself allocates
+    nothing. Runs on W's device and the given (or current) torch stream."""
+    import torch
+    m, K = W.shape
+    n = Z.shape[0]
+    if Z.shape[1] != K:
+        raise ValueError("W and Z need the same number of columns")
+    Wf = W.t().contiguous().t() if K > 1 else W.contiguous()
+    Zf = Z.t().contiguous().t() if K > 1 else Z.contiguous()
+    kc = min(cap, m, n)
+    U = torch.empty((kc, m), dtype=torch.float64, device=W.device).t()
+    V = torch.empty((kc, n), dtype=torch.float64, device=W.device).t()
+    st = stream if stream is not None else torch.cuda.current_stream(W.device)
+    k = ctypes.c_int(0)
+    with torch.cuda.device(W.device):
+        _check(load_library().hm_truncate_noalloc(ctypes.c_void_p(st.cuda_stream), m, n, K, Wf.data_ptr(), m,
+                                                  Zf.data_ptr(), n, float(eps), int(cap), U.data_ptr(), m,
+                                                  V.data_ptr(), n, ctypes.byref(k)))
     return U[:, :k.value], V[:, :k.value]
 
 

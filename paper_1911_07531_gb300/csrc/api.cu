@@ -1009,3 +1009,11 @@ int hm_structure_export(const hm_structure* S, int64_t* perm, int32_t* clusters,
 void hm_structure_free(hm_structure* S) { delete S; }
 
 }  // extern "C"
+
+namespace hm {
+// Last-error setter for entry points defined in other translation units (noalloc.cu).
+int set_last_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace hm
