@@ -36,9 +36,11 @@ KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 WORKLOAD_TEXT = {
     "cube131072": "n=131072 uniform on the unit-cube surface, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
     "sphere32768": "n=32768 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
+    "sphere8192": "n=8192 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
     "sphere2048": "n=2048 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-4, rank cap 64, FP64",
 }
 ORACLE_SAMPLE = {"cube131072": ("cube", 2048, 1e-6), "sphere32768": ("sphere", 2048, 1e-6),
+                 "sphere8192": ("sphere", 2048, 1e-6),
                  "sphere2048": ("sphere", 2048, 1e-4)}
 
 

@@ -93,6 +93,8 @@ def gaussian_rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
 WORKLOADS = {
     "sphere2048": dict(geometry="sphere", n=2048, seed=11, rhs_seed=12, leaf=64, eta=2.0,
                        eps=1e-4, rank_cap=64),
+    "sphere8192": dict(geometry="sphere", n=8192, seed=21, rhs_seed=22, leaf=64, eta=2.0,
+                       eps=1e-6, rank_cap=64),
     "sphere32768": dict(geometry="sphere", n=32768, seed=21, rhs_seed=22, leaf=64, eta=2.0,
                         eps=1e-6, rank_cap=64),
     "cube131072": dict(geometry="cube", n=131072, seed=31, rhs_seed=32, leaf=64, eta=2.0,
