@@ -77,6 +77,9 @@ struct DevPlan {
   bool uploaded = false;
   double eps = -1.0;
   double plan_seconds = 0.0;
+  // replay state of solve / matvec plans: persistent scratch and the captured CUDA graph
+  Buf sd, si, cnt;
+  cudaGraphExec_t exec = nullptr;
 };
 
 size_t op_size(int kind) {
@@ -119,6 +122,11 @@ int upload(hm_ctx* c, DevPlan& dp) {
 void free_plan(hm_ctx* c, DevPlan& dp) {
   for (int k = 0; k < NKIND; ++k) dfree(c, dp.ops[k]);
   dfree(c, dp.entries);
+  dfree(c, dp.sd);
+  dfree(c, dp.si);
+  dfree(c, dp.cnt);
+  if (dp.exec) cudaGraphExecDestroy(dp.exec);
+  dp.exec = nullptr;
   dp.uploaded = false;
 }
 
@@ -127,7 +135,9 @@ struct Profile {
   int64_t launches[NKIND] = {0};
 };
 
-int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof) {
+int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cudaStream_t stream_override = nullptr,
+             bool use_override = false) {
+  const cudaStream_t stream = use_override ? stream_override : stream;
   std::vector<cudaEvent_t> ev;
   std::vector<int> evkind;
   for (const Launch& L : dp.host.launches) {
@@ -138,17 +148,17 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof) {
       cudaEvent_t a, b;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, stream);
       ev.push_back(a);
       ev.push_back(b);
       evkind.push_back(L.kind);
     }
-    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, c->stream);
+    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, stream);
     if (e != cudaSuccess) return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-    if (prof) cudaEventRecord(ev.back(), c->stream);
+    if (prof) cudaEventRecord(ev.back(), stream);
   }
   if (prof) {
-    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaStreamSynchronize(stream));
     for (size_t q = 0; q < evkind.size(); ++q) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
@@ -564,42 +574,54 @@ void hm_factor_free(hm_factor* F) {
 
 namespace {
 
-// run a solve / matvec plan on the SP_X work buffer; `nv` goes to scratch int 0
+// run a solve / matvec plan on the SP_X work buffer; `nv` goes to scratch int 0. The plan's
+// scratch is allocated once and the whole launch sequence is captured once into a CUDA graph
+// (on a private stream) and then replayed on the context stream: a solve is thousands of
+// small dependent launches, and graph replay removes their host launch cost.
 int run_aux(hm_ctx* c, hm_matrix* A, hm_factor* F, DevPlan& dp, Buf& work, int nv) {
-  Buf sd, si;
-  Counters k;
-  auto done = [&](int r) {
-    dfree(c, sd);
-    dfree(c, si);
-    dfree(c, k.b);
-    return r;
-  };
-  if (!dalloc(c, sd, std::max<int64_t>(1, dp.host.scratch_doubles) * 8) ||
-      !dalloc(c, si, std::max<int64_t>(8, dp.host.scratch_ints) * 4))
-    return done(fail(HM_ENOMEM, "allocator returned NULL (scratch)"));
-  int rc = counters_init(c, k);
-  if (rc) return done(rc);
-  if (launch_set_int((int*)si.p, nv, c->stream)) return done(fail(HM_ECUDA, "set-int kernel failed"));
-  Bases B = make_bases();
-  B.d[SP_S] = (double*)sd.p;
-  B.d[SP_X] = (double*)work.p;
-  B.d[SP_A] = (double*)A->vals.p;
-  B.d[SP_P] = (double*)A->pts.p;
-  B.i[IS_S] = (int*)si.p;
-  B.i[IS_ARANK] = (int*)A->ranks.p;
-  if (F) {
-    B.d[SP_F] = (double*)F->vals.p;
-    B.i[IS_RANK] = (int*)F->ranks.p;
-    B.i[IS_PIV] = (int*)F->piv.p;
+  if (!dp.sd.p) {
+    if (!dalloc(c, dp.sd, std::max<int64_t>(1, dp.host.scratch_doubles) * 8) ||
+        !dalloc(c, dp.si, std::max<int64_t>(8, dp.host.scratch_ints) * 4) ||
+        !dalloc(c, dp.cnt, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int)))
+      return fail(HM_ENOMEM, "allocator returned NULL (scratch)");
+    CU(cudaMemsetAsync(dp.cnt.p, 0, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
   }
-  B.flops = k.flops();
-  B.status = k.status();
-  rc = run_plan(c, dp, B, A->h, nullptr);
-  if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e) rc = fail(HM_ECUDA, std::string("plan execution: ") + cudaGetErrorString(e));
+  if (launch_set_int((int*)dp.si.p, nv, c->stream)) return fail(HM_ECUDA, "set-int kernel failed");
+  if (!dp.exec) {
+    Bases B = make_bases();
+    B.d[SP_S] = (double*)dp.sd.p;
+    B.d[SP_X] = (double*)work.p;
+    B.d[SP_A] = (double*)A->vals.p;
+    B.d[SP_P] = (double*)A->pts.p;
+    B.i[IS_S] = (int*)dp.si.p;
+    B.i[IS_ARANK] = (int*)A->ranks.p;
+    if (F) {
+      B.d[SP_F] = (double*)F->vals.p;
+      B.i[IS_RANK] = (int*)F->ranks.p;
+      B.i[IS_PIV] = (int*)F->piv.p;
+    }
+    B.flops = (unsigned long long*)dp.cnt.p;
+    B.status = (int*)((char*)dp.cnt.p + NCOUNT * sizeof(unsigned long long));
+    prepare_kernels();
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = HM_OK;
+    if (!e) rc = run_plan(c, dp, B, A->h, nullptr, cs, true);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (!e) e = e2;
+    if (!e && rc == HM_OK) e = cudaGraphInstantiate(&dp.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e) {
+      dp.exec = nullptr;
+      return fail(HM_ECUDA, std::string("plan capture: ") + cudaGetErrorString(e));
+    }
   }
-  return done(rc);
+  CU(cudaGraphLaunch(dp.exec, c->stream));
+  return HM_OK;
 }
 
 int plain_solve(hm_ctx* c, hm_factor* F, const double* b, double* x, int64_t nrhs, int64_t ld) {

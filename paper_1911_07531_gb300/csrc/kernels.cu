@@ -472,11 +472,13 @@ __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
 // c = 1/sqrt(1 + t^2), s = t c are then made orthogonal to FP64 accuracy by two Newton steps.
 // An entry is significant if A_pq^2 > u^2 |A_pp A_qq| and |A_pq| > abs_tol (the absolute
 // floor keeps noise-level eigenvalues from being chased to the sweep limit).
-__device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, double* cs,
-                             double* sn, int* pa, int* pb, int* flag, double abs_tol) {
+template <typename T>
+__device__ void jacobi_eigen(T* A, int lda, T* V, int ldv, int K, T* cs, T* sn, int* pa, int* pb, int* flag,
+                             T abs_tol, int max_sweeps) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int half = K / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  const T rel2 = sizeof(T) == 8 ? (T)4.9e-32 : (T)1.5e-14;   // (unit roundoff)^2
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int r = 0; r < K - 1; ++r) {
@@ -487,26 +489,37 @@ __device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, doub
         int a = min(x, y), b = max(x, y);
         pa[q] = a;
         pb[q] = b;
-        const double app = A[a + (int64_t)a * lda], aqq = A[b + (int64_t)b * lda], apq = A[a + (int64_t)b * lda];
-        double c = 1.0, s = 0.0;
-        const double aa = fabs(apq);
-        if (aa > abs_tol && aa * aa > 4.9e-32 * fabs(app * aqq)) {
-          // scale the two FP64 operands of theta by a power of two into FP32 range
-          const double num = aqq - app, den = 2.0 * apq;
-          int e;
-          frexp(fmax(fabs(num), fabs(den)), &e);
-          const float th = (float)ldexp(num, -e) / (float)ldexp(den, -e);
-          float tf;
-          if (!(fabsf(th) < 1e18f)) tf = 0.0f;
-          else tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
-          const double t = (double)tf;
-          const double x2 = fma(t, t, 1.0);
-          double yv = (double)rsqrtf((float)x2);
-          yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
-          yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
-          c = yv;
-          s = t * yv;
-          if (s != 0.0) *flag = 1;
+        const T app = A[a + (int64_t)a * lda], aqq = A[b + (int64_t)b * lda], apq = A[a + (int64_t)b * lda];
+        T c = 1, s = 0;
+        const T aa = apq < 0 ? -apq : apq;
+        if (aa > abs_tol && aa * aa > rel2 * (app * aqq < 0 ? -app * aqq : app * aqq)) {
+          if (sizeof(T) == 8) {
+            // FP32 angle from exactly formed FP64 operands scaled into FP32 range, then an
+            // exactly orthogonal FP64 pair (c, s) by two Newton steps for 1/sqrt(1 + t^2)
+            const double num = (double)aqq - (double)app, den = 2.0 * (double)apq;
+            int e;
+            frexp(fmax(fabs(num), fabs(den)), &e);
+            const float th = (float)ldexp(num, -e) / (float)ldexp(den, -e);
+            float tf;
+            if (!(fabsf(th) < 1e18f)) tf = 0.0f;
+            else tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+            const double t = (double)tf;
+            const double x2 = fma(t, t, 1.0);
+            double yv = (double)rsqrtf((float)x2);
+            yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
+            yv = yv * fma(-0.5 * x2, yv * yv, 1.5);
+            c = (T)yv;
+            s = (T)(t * yv);
+          } else {
+            const float th = ((float)aqq - (float)app) / (2.0f * (float)apq);
+            float tf;
+            if (!(fabsf(th) < 1e18f)) tf = 0.0f;
+            else tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+            const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+            c = (T)cf;
+            s = (T)(tf * cf);
+          }
+          if (s != 0) *flag = 1;
         }
         cs[q] = c;
         sn[q] = s;
@@ -514,23 +527,23 @@ __device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, doub
       __syncthreads();
       for (int e = tid; e < half * K; e += nt) {   // rows a, b of A
         int q = e / K, j = e % K;
-        double c = cs[q], s = sn[q];
-        if (s == 0.0) continue;
+        T c = cs[q], s = sn[q];
+        if (s == 0) continue;
         int a = pa[q], b = pb[q];
-        double xa = A[a + (int64_t)j * lda], xb = A[b + (int64_t)j * lda];
+        T xa = A[a + (int64_t)j * lda], xb = A[b + (int64_t)j * lda];
         A[a + (int64_t)j * lda] = c * xa - s * xb;
         A[b + (int64_t)j * lda] = s * xa + c * xb;
       }
       __syncthreads();
       for (int e = tid; e < half * K; e += nt) {   // columns a, b of A and V
         int q = e / K, j = e % K;
-        double c = cs[q], s = sn[q];
-        if (s == 0.0) continue;
+        T c = cs[q], s = sn[q];
+        if (s == 0) continue;
         int a = pa[q], b = pb[q];
-        double xa = A[j + (int64_t)a * lda], xb = A[j + (int64_t)b * lda];
+        T xa = A[j + (int64_t)a * lda], xb = A[j + (int64_t)b * lda];
         A[j + (int64_t)a * lda] = c * xa - s * xb;
         A[j + (int64_t)b * lda] = s * xa + c * xb;
-        double va = V[j + (int64_t)a * ldv], vb = V[j + (int64_t)b * ldv];
+        T va = V[j + (int64_t)a * ldv], vb = V[j + (int64_t)b * ldv];
         V[j + (int64_t)a * ldv] = c * va - s * vb;
         V[j + (int64_t)b * ldv] = s * va + c * vb;
       }
@@ -541,10 +554,25 @@ __device__ void jacobi_eigen(double* A, int lda, double* V, int ldv, int K, doub
   }
 }
 
+// C (n x n, ldc) = op(A) B for n x n operands (op(A) = A or A^T), one output element per
+// thread iteration; used for the small products of the eigen-solver polish.
+__device__ void small_mm(double* C, int ldc, const double* A, int lda, bool transA, const double* B, int ldb,
+                         int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    double s = 0.0;
+    if (transA)
+      for (int l = 0; l < n; ++l) s = fma(A[l + (int64_t)i * lda], B[l + (int64_t)j * ldb], s);
+    else
+      for (int l = 0; l < n; ++l) s = fma(A[i + (int64_t)l * lda], B[l + (int64_t)j * ldb], s);
+    C[i + (int64_t)j * ldc] = s;
+  }
+}
+
 constexpr int KMAX = 256;       // largest stacked rank of one rounded addition
 constexpr int JSM = 64;         // Jacobi problems up to this size run in shared memory
 
-__global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, Bases B) {
+__global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, Bases B) {
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
   __shared__ double d[KMAX], dinv[KMAX], rdinv[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
@@ -712,7 +740,60 @@ __global__ void __launch_bounds__(256) k_core(const TruncOp* __restrict__ ops, B
     red[1] = tr;
   }
   __syncthreads();
-  jacobi_eigen(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * red[1]);
+  const double tr = red[1];
+  if (rp <= JSM && tr > 0.0) {
+    // Mixed precision: sweeps in FP32 on M / trace(M) (FP32 runs ~64x faster than FP64 on
+    // this GPU), then in FP64: orthogonalise the FP32 eigenvectors by one Newton-Schulz step
+    // Y <- Y (3 I - Y^T Y) / 2, form M1 = Y^T M Y (nearly diagonal) and finish with FP64
+    // sweeps that accumulate onto Y. The eigenvalues come from the FP64 sweeps, so they keep
+    // full accuracy; the FP32 stage only supplies a starting basis.
+    double* Mg = T1;                     // global copy of M (ld Kc)
+    double* G = Gz;                      // global temporary (ld Kc); Gz is dead here
+    float* Mf = reinterpret_cast<float*>(Mj);            // two FP32 matrices inside Mj's buffer
+    float* Yf = Mf + JSM * (JSM + 1);
+    const int ldf = JSM + 1;
+    __shared__ float csf[KMAX / 2], snf[KMAX / 2];
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Mg[p + (int64_t)q * Kc] = Mj[p + q * ldj];
+    }
+    __syncthreads();
+    const double itr = 1.0 / tr;
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Mf[p + q * ldf] = (float)(Mg[p + (int64_t)q * Kc] * itr);
+      Yf[p + q * ldf] = (p == q) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    jacobi_eigen<float>(Mf, ldf, Yf, ldf, rp, csf, snf, pa, pb, &s_int[1], 1e-12f, 12);
+    __syncthreads();
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Yj[p + q * ldj] = (double)Yf[p + q * ldf];
+    }
+    __syncthreads();
+    small_mm(Mj, ldj, Yj, ldj, true, Yj, ldj, rp);            // P = Y^T Y
+    __syncthreads();
+    small_mm(G, Kc, Yj, ldj, false, Mj, ldj, rp);             // Y P
+    __syncthreads();
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Yj[p + q * ldj] = 1.5 * Yj[p + q * ldj] - 0.5 * G[p + (int64_t)q * Kc];
+    }
+    __syncthreads();
+    small_mm(Mj, ldj, Mg, Kc, false, Yj, ldj, rp);            // T = M Y
+    __syncthreads();
+    small_mm(G, Kc, Yj, ldj, true, Mj, ldj, rp);              // M1 = Y^T T
+    __syncthreads();
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Mj[p + q * ldj] = 0.5 * (G[p + (int64_t)q * Kc] + G[q + (int64_t)p * Kc]);
+    }
+    __syncthreads();
+    jacobi_eigen<double>(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * tr, 40);
+  } else {
+    jacobi_eigen<double>(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * tr, 40);
+  }
   __syncthreads();
   for (int q = tid; q < r; q += nt) lam[q] = Mj[q + (int64_t)q * ldj];
   __syncthreads();
@@ -1033,6 +1114,8 @@ static void set_attributes() {
   g_attr_set = true;
 }
 
+void prepare_kernels() { set_attributes(); }
+
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
                         double h, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
@@ -1043,7 +1126,7 @@ cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* 
     case K_GEMM: k_gemm<<<count, 256, 0, s>>>((const GemmOp*)ops, B); break;
     case K_COPY: k_copy<<<count, 256, 0, s>>>((const CopyOp*)ops, B); break;
     case K_STACK: k_stack<<<count, 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
-    case K_CORE: k_core<<<count, 256, CORE_SMEM, s>>>((const TruncOp*)ops, B); break;
+    case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, B); break;
     case K_EVAL: k_eval<<<count, 256, 0, s>>>((const EvalOp*)ops, B, h); break;
     case K_ACA: k_aca<<<count, 256, 0, s>>>((const AcaOp*)ops, B, h); break;
     default: return cudaErrorInvalidValue;

@@ -7,6 +7,8 @@
 
 namespace hm {
 
+// sets the kernels' shared-memory attributes (call before capturing launches into a graph)
+void prepare_kernels();
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
                         double h, cudaStream_t s);
 cudaError_t launch_nn2(const double* P, int n, double* out, cudaStream_t s);

@@ -29,7 +29,7 @@ namespace {
 
 constexpr int KMAX_STACK = 256;     // largest stacked rank of one rounded addition
 constexpr int GEMM_MCHUNK = 512;    // row chunk of a GEMM micro-op
-constexpr int GEMM_KCHUNK = 2048;   // reduction chunk of an accumulating GEMM micro-op
+constexpr int GEMM_KCHUNK = 512;    // reduction chunk of an accumulating GEMM micro-op
 constexpr int TRSM_VCHUNK = 256;    // vectors of one triangular-solve micro-op
 constexpr int64_t ALIGN = 32;       // doubles (256 bytes)
 
@@ -225,12 +225,14 @@ struct Ctx {
       } else {
         const int64_t T = w.alloc_d((int64_t)L.cap * nvmax);
         const Dim rk{0, rref(L)};
-        copy(ph, CM_ZERO, 0, 0, 0, sref(T), 1, L.cap, rk, nv);
-        // T = V^T X (or U^T X when transposed), reduction split across CTAs
+        // T = V^T X (or U^T X when transposed); a long reduction is split across CTAs and
+        // accumulated atomically into a zeroed T, a short one is written directly
         const int64_t first = trans ? L.off : L.voff;
         const int ld1 = trans ? L.m : L.n;
+        const bool split = ld1 > GEMM_KCHUNK;
+        if (split) copy(ph, CM_ZERO, 0, 0, 0, sref(T), 1, L.cap, rk, nv);
         gemm(ph + 1, dref(first), ld1, 1, Xi.ref, Xi.es, Xi.vs, sref(T), 1, L.cap, rk, nv, {ld1, 0}, 1.0,
-             GF_ATOMIC, FC_GEMM);
+             split ? GF_ATOMIC : GF_OVERWRITE, FC_GEMM);
         const int64_t second = trans ? L.voff : L.off;
         const int ld2 = trans ? L.n : L.m;
         gemm(ph + 2, dref(second), 1, ld2, sref(T), 1, L.cap, Yo.ref, Yo.es, Yo.vs, {ld2, 0}, nv, rk, alpha,
@@ -576,13 +578,13 @@ struct Ctx {
         w.stack[ph].push_back(op);
         w.stack_entries[ph].push_back(es);
         const Dim Kd{0, op.Kd};
-        for (int i0 = 0; i0 < L.m; i0 += 4096) {
-          int mi = std::min(4096, L.m - i0);
+        for (int i0 = 0; i0 < L.m; i0 += GEMM_KCHUNK) {
+          int mi = std::min(GEMM_KCHUNK, L.m - i0);
           gemm(ph + 1, op.Wst + (uint64_t)i0, L.m, 1, op.Wst + (uint64_t)i0, 1, L.m, op.Gw, 1, Kc, Kd, Kd,
                {mi, 0}, 1.0, GF_ATOMIC, FC_NONE);
         }
-        for (int i0 = 0; i0 < L.n; i0 += 4096) {
-          int ni = std::min(4096, L.n - i0);
+        for (int i0 = 0; i0 < L.n; i0 += GEMM_KCHUNK) {
+          int ni = std::min(GEMM_KCHUNK, L.n - i0);
           gemm(ph + 1, op.Zst + (uint64_t)i0, L.n, 1, op.Zst + (uint64_t)i0, 1, L.n, op.Gz, 1, Kc, Kd, Kd,
                {ni, 0}, 1.0, GF_ATOMIC, FC_NONE);
         }
