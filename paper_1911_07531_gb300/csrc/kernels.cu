@@ -84,6 +84,34 @@ __device__ __forceinline__ int block_argmax(double v, int idx, double* redv, int
   return bi;
 }
 
+// FP64 reciprocal and reciprocal square root by Newton-Raphson iteration from FP32 seeds
+// (x = m 2^e with m in [0.5, 2); two Newton steps take the ~1e-7 seed to full precision).
+// FP64 division and square root are long dependent instruction sequences on this GPU; these
+// serve the serial paths (pivots of LU and Cholesky), where their latency is exposed.
+__device__ __forceinline__ double nr_rcp(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  double y = (double)(1.0f / (float)m);
+  double r = fma(-m, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-m, y, 1.0);
+  y = fma(y, r, y);
+  return ldexp(y, -e);
+}
+
+__device__ __forceinline__ double nr_rsqrt(double x) {
+  int e;
+  double m = frexp(x, &e);
+  if (e & 1) {
+    m *= 2.0;
+    e -= 1;
+  }
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  return ldexp(y, -e / 2);
+}
+
 // ------------------------------------------------------------------------------ GEMM
 // One CTA (256 threads) per micro-op. The output is covered by TM x TN tiles; S groups of
 // threads split the reduction of each tile and are summed in shared memory at the end. The
@@ -221,7 +249,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
     for (int e = tid; e < b; e += 256) piv[e] = iptr(B, op.piv)[e];
   __syncthreads();
   if (op.mode == TM_UT || op.mode == TM_U)
-    for (int e = tid; e < b; e += 256) dinv[e] = 1.0 / T[e][e];
+    for (int e = tid; e < b; e += 256) dinv[e] = nr_rcp(T[e][e]);
   __syncthreads();
   const bool e_fast = op.x_es == 1;
   for (int v0 = 0; v0 < nv; v0 += 64) {
@@ -360,7 +388,7 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
     if (d == 0.0) {
       if (tid == 0) atomicAdd(&B.status[0], 1);
     } else {
-      const double dinv = 1.0 / d;
+      const double dinv = nr_rcp(d);
       for (int i = j + 1 + tid; i < b; i += 256) S[i][j] = S[i][j] * dinv;
     }
     __syncthreads();
@@ -554,29 +582,253 @@ __device__ void jacobi_eigen(T* A, int lda, T* V, int ldv, int K, T* cs, T* sn, 
   }
 }
 
-// C (n x n, ldc) = op(A) B for n x n operands (op(A) = A or A^T), one output element per
-// thread iteration; used for the small products of the eigen-solver polish.
-__device__ void small_mm(double* C, int ldc, const double* A, int lda, bool transA, const double* B, int ldb,
-                         int n) {
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    double s = 0.0;
-    if (transA)
-      for (int l = 0; l < n; ++l) s = fma(A[l + (int64_t)i * lda], B[l + (int64_t)j * ldb], s);
-    else
-      for (int l = 0; l < n; ++l) s = fma(A[i + (int64_t)l * lda], B[l + (int64_t)j * ldb], s);
-    C[i + (int64_t)j * ldc] = s;
-  }
-}
+#ifdef HM_CORE_TIMING
+__device__ long long g_core_stamp[16];
+#define CORE_STAMP(i)                                  \
+  do {                                                 \
+    __syncthreads();                                   \
+    if (threadIdx.x == 0) g_core_stamp[i] = clock64(); \
+  } while (0)
+#else
+#define CORE_STAMP(i) \
+  do {                \
+  } while (0)
+#endif
 
 constexpr int KMAX = 256;       // largest stacked rank of one rounded addition
 constexpr int JSM = 64;         // Jacobi problems up to this size run in shared memory
+
+// Reciprocal of x in [1e-30, 1e30] to full FP64 accuracy with three dependent FP64 operations:
+// r0 = 1/x correctly rounded in FP32, e = 1 - x r0 (|e| < 2^-22), 1/x = r0 (1 + e + e^2 + ...);
+// the truncated series leaves r0 e^3 ~ 2^-66 r0. GB300 spends ~64 cycles on each dependent FP64
+// operation, so this is for latency-critical serial sections.
+__device__ __forceinline__ double fast_rcp(double x) {
+  const double r0 = (double)__frcp_rn((float)x);
+  const double e = fma(-x, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
+}
+
+// Total order of doubles as signed 64-bit integers (negative values have their magnitude bits
+// flipped): comparisons on the integer pipe instead of ~64-cycle FP64 compares.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+
+// Pivoted Cholesky (outer-product form, diagonal pivoting) of the symmetric positive
+// semi-definite n x n matrix A (ld lda; only the lower triangle is read and written), in place
+// with physical symmetric interchanges: on return P^T A P = L L^T with L lower trapezoidal, its
+// column q (rows q..n-1) in column q of A for q < rank, and perm[q] the original index of
+// pivoted position q (perm must hold 0..n-1 on entry). Stops when the largest remaining
+// diagonal entry is <= tol (tol >= 0); returns the rank. The pivots must lie in [1e-30, 1e30]
+// (callers scale A to unit diagonal or unit trace).
+// One step: warp 0 picks the pivot (an integer max over the bit patterns of the positive
+// diagonal entries, low mantissa bits replaced by the index so that ties go to the lowest
+// index), interchanges, and forms 1/pivot; then the other warps update their columns of the
+// trailing lower triangle with the unscaled pivot column, A_ik -= a_ij (a_kj / a_jj). The
+// columns are scaled by 1/sqrt(pivot) once at the end, all in parallel, so that a step's
+// serial FP64 chain is three operations long. Two block barriers per step.
+// s_flag: one shared int, s_val: one shared double (block-wide broadcast slots).
+#ifdef HM_CORE_TIMING
+__device__ long long g_chol_phase[4];
+#define CHOL_T(v) long long v = clock64()
+#define CHOL_ACC(i, a, b) \
+  if (threadIdx.x == 0) g_chol_phase[i] += (b) - (a)
+#else
+#define CHOL_T(v)
+#define CHOL_ACC(i, a, b)
+#endif
+__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, int* s_flag,
+                                double* s_val) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const long long tol_key = __double_as_longlong(fmax(tol, 0.0));
+  int j = 0;
+  for (; j < n; ++j) {
+    CHOL_T(t0);
+    if (warp == 0) {
+      long long best = -1;
+      for (int i = j + lane; i < n; i += 32) {
+        const long long b = __double_as_longlong(A[i + (int64_t)i * lda]);
+        const long long key = b > 0 ? ((b & ~511LL) | (511 - i)) : -1LL;
+        best = key > best ? key : best;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        best = ob > best ? ob : best;
+      }
+      const int p = best < 0 ? -1 : 511 - (int)(best & 511);
+      const double piv = p < 0 ? 0.0 : A[p + (int64_t)p * lda];
+      const bool go = p >= 0 && __double_as_longlong(piv) > tol_key;
+      if (go && p != j) {
+        // interchange positions j and p: rows of the finished columns, the two diagonal
+        // entries, and the pairs of the trailing lower triangle that trade places
+        for (int k = lane; k < n; k += 32) {
+          double *x, *y;
+          if (k < j) {
+            x = A + j + (int64_t)k * lda;
+            y = A + p + (int64_t)k * lda;
+          } else if (k == j) {
+            x = A + j + (int64_t)j * lda;
+            y = A + p + (int64_t)p * lda;
+          } else if (k < p) {
+            x = A + k + (int64_t)j * lda;
+            y = A + p + (int64_t)k * lda;
+          } else if (k > p) {
+            x = A + k + (int64_t)j * lda;
+            y = A + k + (int64_t)p * lda;
+          } else {
+            continue;
+          }
+          const double t = *x;
+          *x = *y;
+          *y = t;
+        }
+        if (lane == 0) {
+          const int t = perm[j];
+          perm[j] = perm[p];
+          perm[p] = t;
+        }
+      }
+      if (lane == 0) {
+        *s_flag = go ? 1 : 0;
+        if (go) *s_val = fast_rcp(piv);
+      }
+    }
+    __syncthreads();
+    CHOL_T(t1);
+    CHOL_ACC(0, t0, t1);
+    if (!*s_flag) break;
+    const int w0 = nw > 1 ? 1 : 0;    // warp 0 sits out the update when there are others
+    if (warp >= w0) {
+      const double ipiv = *s_val;
+      for (int jj = j + 1 + warp - w0; jj < n; jj += nw - w0) {
+        const double t = A[jj + (int64_t)j * lda] * ipiv;
+        for (int ii = jj + lane; ii < n; ii += 32)
+          A[ii + (int64_t)jj * lda] = fma(-A[ii + (int64_t)j * lda], t, A[ii + (int64_t)jj * lda]);
+      }
+    }
+    __syncthreads();
+    CHOL_T(t2);
+    CHOL_ACC(2, t1, t2);
+  }
+  // scale the columns: L(:, q) = a(:, q) / sqrt(pivot_q)
+  for (int q = warp; q < j; q += nw) {
+    const double piv = A[q + (int64_t)q * lda];
+    const double rinv = nr_rsqrt(piv);
+    for (int i = q + 1 + lane; i < n; i += 32) A[i + (int64_t)q * lda] *= rinv;
+    __syncwarp();
+    if (lane == 0) A[q + (int64_t)q * lda] = piv * rinv;
+  }
+  __syncthreads();
+  return j;
+}
+
+// One-sided (Hestenes) Jacobi in FP32 on the columns of G (rows x cols, cols even, ld ldg):
+// column pairs are rotated until orthogonal, and the rotations are accumulated into V (cols x cols, ld ldv); "orthogonal" means |g_a . g_b| below the FP32
+// rounding level of the dot products. Applied to a Cholesky factor of a graded
+// positive definite matrix it yields singular values with high relative accuracy (Demmel and
+// Veselic, "Jacobi's method is more accurate than QR", 1992). One warp handles one pair at a
+// time (dot products by warp shuffles), so a round needs a single block barrier.
+__device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
+                                    int max_sweeps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int half = cols / 2;
+  // orthogonality target at the FP32 rounding level of dot products of length `rows`
+  const float tol = fmaxf(1e-6f, 6e-8f * (float)rows);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int r = 0; r < cols - 1; ++r) {
+#ifdef HM_CORE_TIMING
+      long long tj0 = clock64(), tj1 = tj0, tj2 = tj0;
+#endif
+      for (int q = warp; q < half; q += nw) {
+        // round-robin pairing: position 0 fixed, positions 1..cols-1 rotate by r
+        int x = q - 1 + r, y = cols - 2 - q + r;
+        x = x >= cols - 1 ? x - (cols - 1) : x;
+        y = y >= cols - 1 ? y - (cols - 1) : y;
+        x = q == 0 ? 0 : 1 + x;
+        y = 1 + y;
+        const int a = min(x, y), b = max(x, y);
+        float* ga = G + a * ldg;
+        float* gb = G + b * ldg;
+        float al = 0.f, be = 0.f, ga_b = 0.f;
+#ifdef HM_CORE_TIMING
+        const long long tja = clock64();
+#endif
+        for (int l = lane; l < rows; l += 32) {
+          const float u = ga[l], v = gb[l];
+          al = fmaf(u, u, al);
+          be = fmaf(v, v, be);
+          ga_b = fmaf(u, v, ga_b);
+        }
+#ifdef HM_CORE_TIMING
+        const long long tjb = clock64();
+        if (threadIdx.x == 0) {
+          g_core_stamp[13] += tja - tj0;
+          g_core_stamp[14] += tjb - tja;
+        }
+#endif
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga_b += __shfl_xor_sync(0xffffffffu, ga_b, o);
+        }
+#ifdef HM_CORE_TIMING
+        tj1 = clock64();
+#endif
+        if (al > 0.f && be > 0.f && fabsf(ga_b) > tol * sqrtf(al) * sqrtf(be)) {
+          const float th = (be - al) / (2.0f * ga_b);
+          float t;
+          if (!(fabsf(th) < 1e18f)) t = 0.0f;
+          else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+          const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+          if (s != 0.f) {
+            for (int l = lane; l < rows; l += 32) {
+              const float u = ga[l], v = gb[l];
+              ga[l] = c * u - s * v;
+              gb[l] = s * u + c * v;
+            }
+            if (V) {
+              float* va = V + a * ldv;
+              float* vb = V + b * ldv;
+              for (int l = lane; l < cols; l += 32) {
+                const float u = va[l], v = vb[l];
+                va[l] = c * u - s * v;
+                vb[l] = s * u + c * v;
+              }
+            }
+            if (lane == 0) *flag = 1;
+          }
+        }
+#ifdef HM_CORE_TIMING
+        tj2 = clock64();
+#endif
+      }
+      __syncthreads();
+#ifdef HM_CORE_TIMING
+      if (threadIdx.x == 0) {
+        const long long tj3 = clock64();
+        g_core_stamp[10] += tj1 - tj0;
+        g_core_stamp[11] += tj2 - tj1;
+        g_core_stamp[12] += tj3 - tj2;
+      }
+#endif
+    }
+    if (*flag == 0) break;
+    __syncthreads();
+  }
+#ifdef HM_CORE_TIMING
+  if (threadIdx.x == 0) g_core_stamp[15] = sweep;
+#endif
+}
 
 __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, Bases B) {
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
   __shared__ double d[KMAX], dinv[KMAX], rdinv[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
-  __shared__ int perm[KMAX], pa[KMAX / 2], pb[KMAX / 2], order[KMAX], s_int[4];
+  __shared__ int perm[KMAX], perm2[KMAX], pa[KMAX / 2], pb[KMAX / 2], order[KMAX], s_int[4];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int K = *iptr(B, op.Kd);
   int* rk = iptr(B, op.rank);
@@ -588,93 +840,57 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   double* Gw = dptr(B, op.Gw);
   double* Gz = dptr(B, op.Gz);
   double* work = dptr(B, op.work);
-  double* R = Gw;                              // K x K (ld Kc): equilibrated Gram -> Cholesky, in place
+  double* R = Gw;                              // K x K (ld Kc): the Cholesky factor of the equilibrated G_W
   double* Bm = work;                           // K x r
-  double* T1 = work + (int64_t)Kc * Kc;        // K x r
-  double* M = Gz;                              // r x r (global fallback for Jacobi; Gz is dead by then)
-  // 1. equilibrate the Gram matrix of the stacked left factor
+  double* T1 = work + (int64_t)Kc * Kc;        // K x r, later a temporary
+  CORE_STAMP(0);
+  // 1. equilibrate the Gram matrix of the stacked left factor: G' = D^-1 G_W D^-1
   for (int i = tid; i < K; i += nt) {
-    double g = Gw[i + (int64_t)i * Kc];
-    d[i] = g > 0.0 ? sqrt(g) : 1.0;
-    dinv[i] = 1.0 / d[i];
+    const double g = Gw[i + (int64_t)i * Kc];
+    const double gi = g > 0.0 ? nr_rsqrt(g) : 1.0;
+    d[i] = g > 0.0 ? g * gi : 1.0;
+    dinv[i] = gi;
     perm[i] = i;
   }
   __syncthreads();
+  double* Rc = R;                              // factorise in shared memory when K fits
+  int ldr = Kc;
+  if (K <= JSM) {
+    Rc = smem;
+    ldr = JSM + 1;
+  }
   for (int e = tid; e < K * K; e += nt) {
     int i = e % K, j = e / K;
-    R[i + (int64_t)j * Kc] = R[i + (int64_t)j * Kc] * (dinv[i] * dinv[j]);
+    Rc[i + (int64_t)j * ldr] = R[i + (int64_t)j * Kc] * (dinv[i] * dinv[j]);
   }
   __syncthreads();
-  // 2. pivoted Cholesky G = Pi R^T R Pi^T (upper R in pivoted order, stored in place);
-  //    stop when the largest remaining diagonal is below the noise level of the Gram.
-  const double tolc = 4.0 * K * 2.2e-16;
-  int r = 0;
-  for (int j = 0; j < K; ++j) {
-    if (tid < 32) {
-      double bv = -1.0;
-      int bi = -1;
-      for (int i = j + tid; i < K; i += 32) {
-        double v = R[perm[i] + (int64_t)perm[i] * Kc];
-        if (v > bv) { bv = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
-      }
-      if (tid == 0) {
-        s_int[0] = bi;
-        red[0] = bv;
-      }
+  CORE_STAMP(1);
+  // 2. pivoted Cholesky G' = Pi Rf^T Rf Pi^T; the tolerance is the noise level of a Gram
+  //    matrix. Rf is kept transposed in pivoted order: Rf(q, l) = R[l + q * Kc] for l >= q.
+  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, &s_int[2], &red[2]);
+  if (Rc != R) {
+    for (int e = tid; e < K * K; e += nt) {
+      int i = e % K, j = e / K;
+      R[i + (int64_t)j * Kc] = Rc[i + (int64_t)j * ldr];
     }
     __syncthreads();
-    const double piv = red[0];
-    if (!(piv > tolc)) break;
-    if (tid == 0) {
-      int t = perm[j];
-      perm[j] = perm[s_int[0]];
-      perm[s_int[0]] = t;
-    }
-    __syncthreads();
-    // R is kept in original index space: row pj of the factor is stored in column pj
-    const int pj = perm[j];
-    const double rjj = sqrt(piv);
-    const double rinv = 1.0 / rjj;
-    // column j of R^T in pivoted order: l_i = G(pi_i, pj) / rjj for i > j
-    for (int i = j + 1 + tid; i < K; i += nt) {
-      int pi = perm[i];
-      R[pi + (int64_t)pj * Kc] = R[pi + (int64_t)pj * Kc] * rinv;
-    }
-    if (tid == 0) R[pj + (int64_t)pj * Kc] = rjj;
-    __syncthreads();
-    const int rem = K - 1 - j;
-    for (int e = tid; e < rem * rem; e += nt) {
-      int ii = j + 1 + e % rem, jj = j + 1 + e / rem;
-      if (jj < ii) continue;   // update the lower triangle (pi_ii, pi_jj), ii <= jj, symmetric use
-      int pi = perm[ii], pk = perm[jj];
-      double v = R[pi + (int64_t)pk * Kc] - R[pi + (int64_t)pj * Kc] * R[pk + (int64_t)pj * Kc];
-      R[pi + (int64_t)pk * Kc] = v;
-      R[pk + (int64_t)pi * Kc] = v;
-    }
-    __syncthreads();
-    ++r;
   }
-  // factor entries: Rf(q, l) for q < r, l >= q in pivoted positions = R[perm[l] + perm[q]*Kc]
-  // (diagonal: R[perm[q] + perm[q]*Kc]).
   if (r == 0) {
     if (tid == 0) *rk = 0;
     return;
   }
+  CORE_STAMP(2);
   // 3. Bm = D Pi Rf^T  (K x r): Bm(perm[l], q) = d[perm[l]] * Rf(q, l) for l >= q
   for (int e = tid; e < K * r; e += nt) {
     int l = e % K, q = e / K;
     int pl = perm[l];
     double v = 0.0;
-    if (l >= q) v = d[pl] * R[pl + (int64_t)perm[q] * Kc];
+    if (l >= q) v = d[pl] * R[l + (int64_t)q * Kc];
     Bm[pl + (int64_t)q * Kc] = v;
   }
   __syncthreads();
-  // 4. M = Bm^T Gz Bm  (r x r)
+  // 4. M = Bm^T G_Z Bm  (r x r): the Gram matrix of Z Bm, whose eigen-decomposition gives the
+  //    singular values (squared) and right factors of W Z^T
   for (int e = tid; e < K * r; e += nt) {
     int i = e % K, q = e / K;
     double s = 0.0;
@@ -682,7 +898,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     T1[i + (int64_t)q * Kc] = s;
   }
   __syncthreads();
-  const int rp = r + (r & 1);                  // even size for the round-robin ordering
+  const int rp = r + (r & 1);                  // even size (Jacobi pairs), zero padding
   double* Mj;
   double* Yj;
   int ldj;
@@ -691,178 +907,229 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     Yj = smem + JSM * (JSM + 1);
     ldj = JSM + 1;
   } else {
-    Mj = M;
-    Yj = T1 + 0;   // T1 is free again after M is formed; reuse below
+    Mj = Gz;       // Gz is dead once T1 = G_Z Bm is formed
+    Yj = T1;       // reused after M is formed (the global path keeps M in Gz)
     ldj = Kc;
   }
-  // M into registers-then-store to allow Yj to alias T1 in the global fallback
   for (int e = tid; e < rp * rp; e += nt) {
     int p = e % rp, q = e / rp;
     double s = 0.0;
-    if (p < r && q < r) {
+    if (p < r && q < r)
       for (int i = 0; i < K; ++i) s = fma(Bm[i + (int64_t)p * Kc], T1[i + (int64_t)q * Kc], s);
-    }
-    if (rp > JSM) M[p + (int64_t)q * Kc] = s;
-    else Mj[p + q * ldj] = s;
-  }
-  __syncthreads();
-  if (rp > JSM) {
-    // symmetrise in place
-    for (int e = tid; e < rp * rp; e += nt) {
-      int p = e % rp, q = e / rp;
-      if (p < q) {
-        double v = 0.5 * (M[p + (int64_t)q * Kc] + M[q + (int64_t)p * Kc]);
-        M[p + (int64_t)q * Kc] = v;
-        M[q + (int64_t)p * Kc] = v;
-      }
-    }
-  } else {
-    for (int e = tid; e < rp * rp; e += nt) {
-      int p = e % rp, q = e / rp;
-      if (p < q) {
-        double v = 0.5 * (Mj[p + q * ldj] + Mj[q + p * ldj]);
-        Mj[p + q * ldj] = v;
-        Mj[q + p * ldj] = v;
-      }
-    }
+    Mj[p + (int64_t)q * ldj] = s;
   }
   __syncthreads();
   for (int e = tid; e < rp * rp; e += nt) {
     int p = e % rp, q = e / rp;
-    Yj[p + (int64_t)q * ldj] = (p == q) ? 1.0 : 0.0;
+    if (p < q) {
+      double v = 0.5 * (Mj[p + (int64_t)q * ldj] + Mj[q + (int64_t)p * ldj]);
+      Mj[p + (int64_t)q * ldj] = v;
+      Mj[q + (int64_t)p * ldj] = v;
+    }
   }
   __syncthreads();
-  // 5. eigen-decomposition of M = Y S Y^T (S = sigma^2 of the stacked product); entries
-  //    below 1e-17 trace(M) are noise of the Gram formation and are not rotated away
-  if (tid == 0) {
+  if (tid < 32) {
     double tr = 0.0;
-    for (int q = 0; q < r; ++q) tr += fabs(Mj[q + (int64_t)q * ldj]);
-    red[1] = tr;
+    for (int q = tid; q < r; q += 32) tr += fabs(Mj[q + (int64_t)q * ldj]);
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (tid == 0) red[1] = tr;
   }
   __syncthreads();
   const double tr = red[1];
-  if (rp <= JSM && tr > 0.0) {
-    // Mixed precision: sweeps in FP32 on M / trace(M) (FP32 runs ~64x faster than FP64 on
-    // this GPU), then in FP64: orthogonalise the FP32 eigenvectors by one Newton-Schulz step
-    // Y <- Y (3 I - Y^T Y) / 2, form M1 = Y^T M Y (nearly diagonal) and finish with FP64
-    // sweeps that accumulate onto Y. The eigenvalues come from the FP64 sweeps, so they keep
-    // full accuracy; the FP32 stage only supplies a starting basis.
-    double* Mg = T1;                     // global copy of M (ld Kc)
-    double* G = Gz;                      // global temporary (ld Kc); Gz is dead here
-    float* Mf = reinterpret_cast<float*>(Mj);            // two FP32 matrices inside Mj's buffer
-    float* Yf = Mf + JSM * (JSM + 1);
+  CORE_STAMP(3);
+  // 5. eigen-decomposition M = X diag(lam) X^T
+  const bool dv = rp <= JSM && tr > 0.0;       // Drmac-Veselic path (FP32 vectors)
+  if (dv) {
+    // (a) FP64 pivoted Cholesky M / tr = P R2^T R2 P^T (in place in Mj);
+    // (b) FP32 one-sided Jacobi on the columns of R2^T (below), whose column norms squared give
+    //     the eigenvalues lam_i / tr with high relative accuracy, so FP32 resolves the graded
+    //     spectrum down to the rank threshold, and whose normalised columns give X;
+    // (c) after the rank is chosen, the kept columns are made orthonormal in FP64 (step 6b).
+    const double itr = nr_rcp(tr);
+    for (int e = tid; e < rp * rp; e += nt) {
+      const int p = e % rp, q = e / rp;
+      Mj[p + q * ldj] *= itr;                          // unit trace for the factorisation
+    }
+    for (int i = tid; i < rp; i += nt) perm2[i] = i;
+    __syncthreads();
+    // the tolerance is one rounding unit of the trace: the Schur complement left behind perturbs
+    // the eigenvalues by at most rp u tr, the rounding level of M itself
+    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, &s_int[2], &red[2]);
+    // Drmac-Veselic preconditioning: one-sided Jacobi on the columns of C = R2^T (the rows of the
+    // pivoted Cholesky factor are graded and nearly orthogonal, so it converges in a few
+    // sweeps): C Q = [s_1 u_1, ...] with C C^T = R2^T R2 = P^T M P, i.e. the columns of C Q are
+    // the eigenvectors of P^T M P scaled by sqrt(eigenvalue); Q itself is not needed.
+    const int rcp = rc + (rc & 1);
+    float* Gf = reinterpret_cast<float*>(Yj);          // rp x rcp, ld JSM + 1 (floats)
     const int ldf = JSM + 1;
-    __shared__ float csf[KMAX / 2], snf[KMAX / 2];
-    for (int e = tid; e < rp * rp; e += nt) {
-      const int p = e % rp, q = e / rp;
-      Mg[p + (int64_t)q * Kc] = Mj[p + q * ldj];
+    for (int e = tid; e < rp * rcp; e += nt) {
+      const int l = e % rp, q = e / rp;    // row l = pivoted position, column q = row q of R2
+                                           // (R2(q, l) = Mj[l + q * ldj] for l >= q)
+      float v = 0.0f;
+      if (q < rc && l >= q) v = (float)Mj[l + (int64_t)q * ldj];
+      Gf[l + q * ldf] = v;
     }
     __syncthreads();
-    const double itr = 1.0 / tr;
-    for (int e = tid; e < rp * rp; e += nt) {
-      const int p = e % rp, q = e / rp;
-      Mf[p + q * ldf] = (float)(Mg[p + (int64_t)q * Kc] * itr);
-      Yf[p + q * ldf] = (p == q) ? 1.0f : 0.0f;
+    CORE_STAMP(8);
+    onesided_jacobi_f32(Gf, ldf, rp, rcp, nullptr, 0, &s_int[1], 15);
+    CORE_STAMP(9);
+    for (int q = tid; q < rp; q += nt) {
+      float s2 = 0.0f;
+      if (q < rc)
+        for (int l = 0; l < rp; ++l) s2 = fmaf(Gf[l + q * ldf], Gf[l + q * ldf], s2);
+      lam[q] = (double)s2 * tr;
+      rdinv[q] = s2 > 0.0f ? (double)rsqrtf(s2) : 0.0;   // 1 / |column| (FP32 accuracy suffices:
+                                                         // step 6b fixes the norms)
     }
     __syncthreads();
-    jacobi_eigen<float>(Mf, ldf, Yf, ldf, rp, csf, snf, pa, pb, &s_int[1], 1e-12f, 12);
-    __syncthreads();
+    // X[perm2[l]][q] = C Q[l][q] / |column q|, staged through T1 (global): X overwrites Gf
     for (int e = tid; e < rp * rp; e += nt) {
-      const int p = e % rp, q = e / rp;
-      Yj[p + q * ldj] = (double)Yf[p + q * ldf];
+      const int l = e % rp, q = e / rp;
+      T1[perm2[l] + (int64_t)q * Kc] = q < rc ? (double)Gf[l + q * ldf] * rdinv[q] : 0.0;
     }
-    __syncthreads();
-    small_mm(Mj, ldj, Yj, ldj, true, Yj, ldj, rp);            // P = Y^T Y
-    __syncthreads();
-    small_mm(G, Kc, Yj, ldj, false, Mj, ldj, rp);             // Y P
-    __syncthreads();
-    for (int e = tid; e < rp * rp; e += nt) {
-      const int p = e % rp, q = e / rp;
-      Yj[p + q * ldj] = 1.5 * Yj[p + q * ldj] - 0.5 * G[p + (int64_t)q * Kc];
-    }
-    __syncthreads();
-    small_mm(Mj, ldj, Mg, Kc, false, Yj, ldj, rp);            // T = M Y
-    __syncthreads();
-    small_mm(G, Kc, Yj, ldj, true, Mj, ldj, rp);              // M1 = Y^T T
     __syncthreads();
     for (int e = tid; e < rp * rp; e += nt) {
       const int p = e % rp, q = e / rp;
-      Mj[p + q * ldj] = 0.5 * (G[p + (int64_t)q * Kc] + G[q + (int64_t)p * Kc]);
+      Yj[p + q * ldj] = T1[p + (int64_t)q * Kc];
     }
     __syncthreads();
-    jacobi_eigen<double>(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * tr, 40);
   } else {
-    jacobi_eigen<double>(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], 1e-17 * tr, 40);
+    for (int e = tid; e < rp * rp; e += nt) {
+      int p = e % rp, q = e / rp;
+      Yj[p + (int64_t)q * ldj] = (p == q) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_eigen<double>(Mj, ldj, Yj, ldj, rp, cs, sn, pa, pb, &s_int[1], K * 2.2e-16 * tr, 40);
+    __syncthreads();
+    for (int q = tid; q < rp; q += nt) lam[q] = Mj[q + (int64_t)q * ldj];
   }
   __syncthreads();
-  for (int q = tid; q < r; q += nt) lam[q] = Mj[q + (int64_t)q * ldj];
-  __syncthreads();
+  CORE_STAMP(5);
   // 6. order the eigenvalues (descending, ties by index) and choose the rank; the order
   //    array is first the identity so that it stays a valid index list even with NaNs
-  for (int q = tid; q < r; q += nt) order[q] = q;
+  for (int q = tid; q < rp; q += nt) order[q] = q;
   __syncthreads();
-  for (int q = tid; q < r; q += nt) {
+  for (int q = tid; q < rp; q += nt) {
     int pos = 0;
-    double v = lam[q];
-    for (int p = 0; p < r; ++p)
-      if (lam[p] > v || (lam[p] == v && p < q)) ++pos;
+    const long long v = order_key(lam[q]);
+    for (int p = 0; p < rp; ++p) {
+      const long long w = order_key(lam[p]);
+      if (w > v || (w == v && p < q)) ++pos;
+    }
     order[pos] = q;
   }
   __syncthreads();
   const double smax = lam[order[0]];
-  const double thr = op.eps * op.eps * smax;
-  int kk = 0;
-  if (smax > 0.0)
-    for (int p = 0; p < r; ++p)
-      if (lam[order[p]] > thr) ++kk;
+  const long long thr = order_key(op.eps * op.eps * smax);
+  int kk = __syncthreads_count(smax > 0.0 && tid < r && order_key(lam[order[tid]]) > thr);
   if (kk > op.cap) {
     if (tid == 0) atomicAdd(&B.status[1], 1);
     kk = op.cap;
   }
-  // 7. coefficient matrices: Tz = Bm Y_k S_k^{-1/2}, Tw = D^{-1} Pi_r Rf11^{-1} Y_k S_k^{1/2}
+  if (dv && kk > 0) {
+    // 6b. ordered orthogonalisation of the kept FP32 vectors X_k = X[:, order[0..kk)] in FP64:
+    //     with F = X_k^T X_k - I, X_k <- X_k (I - U1), U1 = strict upper part of F + diag(F)/2,
+    //     the first-order term of Cholesky QR, so that column c mixes only with columns of
+    //     larger eigenvalue and never takes in a discarded direction (a symmetric
+    //     orthogonalisation would leak the FP32 non-orthogonality of the small vectors into the
+    //     large ones, ~1e-6 sigma_1); then one Newton-Schulz step X_k <- X_k (3I - X_k^T X_k)/2
+    //     on the remaining O(F^2) error. Mj (the Cholesky factor of M) is dead here.
+    double* Fm = Mj;
+    for (int e = tid; e < kk * kk; e += nt) {
+      const int a = e % kk, b = e / kk;
+      double sf = 0.0;
+      if (a <= b) {
+        const double* xa = Yj + order[a] * ldj;
+        const double* xb = Yj + order[b] * ldj;
+        for (int l = 0; l < rp; ++l) sf = fma(xa[l], xb[l], sf);
+        if (a == b) sf = 0.5 * (sf - 1.0);
+      }
+      Fm[a + b * ldj] = sf;
+    }
+    __syncthreads();
+    for (int e = tid; e < rp * kk; e += nt) {
+      const int l = e % rp, c = e / rp;
+      double sf = 0.0;
+      for (int a = 0; a <= c; ++a) sf = fma(Yj[l + order[a] * ldj], Fm[a + c * ldj], sf);
+      T1[l + (int64_t)c * Kc] = sf;
+    }
+    __syncthreads();
+    for (int e = tid; e < rp * kk; e += nt) {
+      const int l = e % rp, c = e / rp;
+      Yj[l + order[c] * ldj] -= T1[l + (int64_t)c * Kc];
+    }
+    __syncthreads();
+    for (int e = tid; e < kk * kk; e += nt) {
+      const int a = e % kk, b = e / kk;
+      const double* xa = Yj + order[a] * ldj;
+      const double* xb = Yj + order[b] * ldj;
+      double sf = 0.0;
+      for (int l = 0; l < rp; ++l) sf = fma(xa[l], xb[l], sf);
+      Fm[a + b * ldj] = sf;
+    }
+    __syncthreads();
+    for (int e = tid; e < rp * kk; e += nt) {
+      const int l = e % rp, c = e / rp;
+      double sf = 0.0;
+      for (int a = 0; a < kk; ++a) sf = fma(Yj[l + order[a] * ldj], Fm[a + c * ldj], sf);
+      T1[l + (int64_t)c * Kc] = sf;
+    }
+    __syncthreads();
+    for (int e = tid; e < rp * kk; e += nt) {
+      const int l = e % rp, c = e / rp;
+      double* x = Yj + l + order[c] * ldj;
+      *x = 1.5 * *x - 0.5 * T1[l + (int64_t)c * Kc];
+    }
+    __syncthreads();
+  }
+  CORE_STAMP(6);
+  // 7. coefficient matrices: Tz = Bm X_k S_k^{-1/2}, Tw = D^{-1} Pi_r Rf11^{-1} X_k S_k^{1/2}
   double* Tw = dptr(B, op.Tw);
   double* Tz = dptr(B, op.Tz);
-  __syncthreads();
+  double* Y = Gz;          // K x kk scratch (ld Kc) for the back substitution; Gz is dead here
   if (tid < kk) {
-    const double sg = sqrt(lam[order[tid]]);
-    cs[tid] = sg;          // sigma of the c-th kept direction
-    sn[tid] = 1.0 / sg;
+    const double l = lam[order[tid]];
+    const double is = nr_rsqrt(l);
+    cs[tid] = l * is;      // sigma of the c-th kept direction
+    sn[tid] = is;          // 1 / sigma
   }
+  for (int l = tid; l < r; l += nt) rdinv[l] = nr_rcp(R[l + (int64_t)l * Kc]);
   __syncthreads();
   for (int e = tid; e < K * kk; e += nt) {
-    int i = e % K, c = e / K;
-    int q = order[c];
+    const int i = e % K, c = e / K;
+    const int q = order[c];
     double s = 0.0;
     for (int p = 0; p < r; ++p) s = fma(Bm[i + (int64_t)p * Kc], Yj[p + (int64_t)q * ldj], s);
     Tz[i + (int64_t)c * Kc] = s * sn[c];
-  }
-  // back substitution Rf11 x = Y_k S^{1/2} (Rf11 upper r x r in pivoted order); x lives in
-  // rows perm[0..r) of Tw, the other rows of Tw are zero.
-  for (int e = tid; e < K * kk; e += nt) {
-    int i = e % K, c = e / K;
-    Tw[i + (int64_t)c * Kc] = 0.0;
+    if (i < r) Y[i + (int64_t)c * Kc] = Yj[i + (int64_t)q * ldj] * cs[c];
   }
   __syncthreads();
-  // reciprocals of the Cholesky diagonal
-  for (int l = tid; l < r; l += nt) rdinv[l] = 1.0 / R[perm[l] + (int64_t)perm[l] * Kc];
-  __syncthreads();
-  for (int c = tid; c < kk; c += nt) {
-    int q = order[c];
-    double sig = cs[c];
+  // back substitution Rf11 x = X_k S^{1/2} (Rf11 upper r x r, Rf11(p, l) = R[l + p * Kc]),
+  // column oriented: one warp owns columns c = warp, warp + nw, ... and walks l = r-1 .. 0 with
+  // all of its columns in lockstep; x_l = y_l / Rf11(l, l), then lanes p < l subtract
+  // Rf11(p, l) x_l from y_p.
+  {
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     for (int l = r - 1; l >= 0; --l) {
-      double s = Yj[l + (int64_t)q * ldj] * sig;
-      for (int p = l + 1; p < r; ++p)
-        s = fma(-R[perm[p] + (int64_t)perm[l] * Kc], Tw[perm[p] + (int64_t)c * Kc], s);
-      Tw[perm[l] + (int64_t)c * Kc] = s * rdinv[l];
+      const double rd = rdinv[l];
+      for (int c = warp; c < kk; c += nw) {
+        double* y = Y + (int64_t)c * Kc;
+        const double x = y[l] * rd;
+        for (int p = lane; p < l; p += 32) y[p] = fma(-R[l + (int64_t)p * Kc], x, y[p]);
+        __syncwarp();
+        if (lane == 0) y[l] = x;
+      }
+      __syncwarp();
     }
   }
   __syncthreads();
-  // undo the equilibration: rows of Tw scale by 1/d_i
+  // scatter to the rows perm[0..r) and undo the equilibration (rows of Tw scale by 1/d_i)
   for (int e = tid; e < K * kk; e += nt) {
-    int i = e % K, c = e / K;
-    Tw[i + (int64_t)c * Kc] *= dinv[i];
+    const int l = e % K, c = e / K;
+    const int i = perm[l];
+    Tw[i + (int64_t)c * Kc] = l < r ? Y[l + (int64_t)c * Kc] * dinv[i] : 0.0;
   }
-  __syncthreads();
+  CORE_STAMP(7);
   if (tid == 0) {
     *rk = kk;
     double Kd = K;
