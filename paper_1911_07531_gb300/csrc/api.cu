@@ -137,7 +137,7 @@ struct Profile {
 
 int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cudaStream_t stream_override = nullptr,
              bool use_override = false) {
-  const cudaStream_t stream = use_override ? stream_override : stream;
+  const cudaStream_t stream = use_override ? stream_override : c->stream;
   std::vector<cudaEvent_t> ev;
   std::vector<int> evkind;
   for (const Launch& L : dp.host.launches) {
@@ -153,7 +153,7 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
       ev.push_back(b);
       evkind.push_back(L.kind);
     }
-    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, stream);
+    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, stream, L.gy, L.gz);
     if (e != cudaSuccess) return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     if (prof) cudaEventRecord(ev.back(), stream);
   }
@@ -913,10 +913,13 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   B.status = k.status();
   const TruncOp* dt = (const TruncOp*)ops.p;
   const GemmOp* dg = (const GemmOp*)((char*)ops.p + sizeof(t));
+  int gy0, gz0, gy1, gz1;
+  gemm_grid(g, 2, gy0, gz0);
+  gemm_grid(g + 2, 2, gy1, gz1);
   cudaError_t ce = launch_kind(K_STACK, dt, 1, (const StackEntry*)ent.p, B, 0.0, s);
-  if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
   if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);
-  if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s, gy1, gz1);
   if (ce) return done(fail(HM_ECUDA, std::string("hm_truncate: ") + cudaGetErrorString(ce)));
   int kk = 0;
   CU(cudaMemcpyAsync(&kk, si.p, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -1,10 +1,11 @@
 // Batched FP64 kernels of the H-LU hot path (one CTA per micro-op).
 //
-// GB300 has very little FP64 throughput (about 2 DFMA per clock per SM), so every kernel
-// here is FP64-issue bound once the operands sit in shared memory or L1/L2; the design
-// goal is to keep the DFMA pipe of all 152 SMs busy: 64x64 register-blocked tiles with
-// 16 independent accumulators per thread for the small GEMMs, one CTA per task so that
-// a wave with hundreds of tasks fills the machine, and no host round trip inside a wave.
+// GB300 has very little FP64 throughput (about 2 DFMA per clock per SM, ~64 cycles of latency
+// per dependent FP64 operation), so every kernel here is FP64-issue bound once the operands sit
+// in shared memory or L1/L2, and serial FP64 chains dominate the small factorisations. The
+// design keeps the DFMA pipes busy without padding (exact-size GEMM tiles, large micro-ops
+// spread over several CTAs), moves decisions and iterations that tolerate it to FP32 or the
+// integer pipe, and keeps a whole wave on the device with no host round trip.
 //
 //   k_getrf  dense leaf LU with partial pivoting (Alg 2, leaf case)
 //   k_trsm   triangular solves / multiplies of a diagonal leaf on many vectors (Alg 3 leaf)
@@ -113,119 +114,142 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
 }
 
 // ------------------------------------------------------------------------------ GEMM
-// One CTA (256 threads) per micro-op. The output is covered by TM x TN tiles; S groups of
-// threads split the reduction of each tile and are summed in shared memory at the end. The
-// tile shape is chosen per micro-op from its (dynamic) sizes so that few DFMAs are spent on
-// zero padding: the micro-ops are mostly thin (a rank-sized side of 10-60) or have a small
-// output with a long reduction (Gram matrices, V^T X).
-constexpr int GK = 16;                 // reduction slice
-constexpr int GEMM_SMEM_DOUBLES = 5248;
+// GEMM micro-ops are thin (a rank-sized side of 10-60) or have a small output with a long
+// reduction (Gram matrices). GB300 executes ~2 FP64 FMAs per clock per SM while shared memory
+// delivers 16 doubles per clock, so the kernel needs no register blocking to keep the FP64 pipe
+// busy, and register tiles of fixed shape would pad a 15 x 15 or 45 x 45 output to 16 x 16 or
+// 64 x 64 (3.4x the useful FMAs on the H-LU plans). Instead the output is cut into exact tiles
+// of at most GE elements (at most GTM rows and columns), each thread owns up to four output
+// elements of a tile, and for tiles of fewer than 128 elements G = 2..8 threads split the
+// reduction of one element (partial sums combined in shared memory). A slice of GKS reduction
+// steps of both operands is staged in shared memory per pass. Tiles of one micro-op are spread
+// over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z,
+// so that a large micro-op does not sit on a single SM.
+constexpr int GE = 1024;      // largest C tile (elements)
+constexpr int GTM = 128;      // largest C tile side
+constexpr int GKS = 32;       // staged reduction slice
+constexpr int GEMM_SMEM = (2 * GKS * (GTM + 1) + 256) * (int)sizeof(double);
 
-template <int TM, int TN, int RM, int RN, int S>
-__device__ __forceinline__ void gemm_tiles(const GemmOp& op, int m, int n, int k, const double* __restrict__ A,
-                                           const double* __restrict__ Bm, double* C, double* sm) {
-  constexpr int TX = TN / RN, TY = TM / RM, G = TX * TY;
-  static_assert(G * S == 256, "256 threads");
-  static_assert(S * GK * (TM + 1) + S * GK * (TN + 1) + (S > 1 ? TM * TN : 0) <= GEMM_SMEM_DOUBLES, "smem");
-  double* As = sm;                                  // [S][GK][TM+1]
-  double* Bs = sm + S * GK * (TM + 1);              // [S][GK][TN+1]
-  double* red = Bs + S * GK * (TN + 1);             // [TM*TN] when S > 1
-  const int tid = threadIdx.x, g = tid / G, t = tid % G, tx = t % TX, ty = t / TX;
-  const bool a_i_fast = op.a_rs <= op.a_cs;
-  const bool b_j_fast = op.b_cs <= op.b_rs;
-  const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
-  for (int i0 = 0; i0 < m; i0 += TM)
-    for (int j0 = 0; j0 < n; j0 += TN) {
-      double acc[RM][RN];
-#pragma unroll
-      for (int p = 0; p < RM; ++p)
-#pragma unroll
-        for (int q = 0; q < RN; ++q) acc[p][q] = 0.0;
-      for (int L0 = 0; L0 < k; L0 += S * GK) {
-        // every group stages its own slice l0 = L0 + g*GK
-        for (int e = tid; e < S * GK * TM; e += 256) {
-          int gg = e / (GK * TM), r = e % (GK * TM);
-          int i, l;
-          if (a_i_fast) { i = r % TM; l = r / TM; } else { l = r % GK; i = r / GK; }
-          int gi = i0 + i, gl = L0 + gg * GK + l;
-          double v = 0.0;
-          if (gi < m && gl < k) {
-            if (unitlower) v = gi > gl ? A[gi * op.a_rs + gl * op.a_cs] : (gi == gl ? 1.0 : 0.0);
-            else if (upper) v = gl >= gi ? A[gi * op.a_rs + gl * op.a_cs] : 0.0;
-            else v = A[gi * op.a_rs + gl * op.a_cs];
-          }
-          As[(gg * GK + l) * (TM + 1) + i] = v;
-        }
-        for (int e = tid; e < S * GK * TN; e += 256) {
-          int gg = e / (GK * TN), r = e % (GK * TN);
-          int j, l;
-          if (b_j_fast) { j = r % TN; l = r / TN; } else { l = r % GK; j = r / GK; }
-          int gj = j0 + j, gl = L0 + gg * GK + l;
-          Bs[(gg * GK + l) * (TN + 1) + j] = (gj < n && gl < k) ? Bm[gl * op.b_rs + gj * op.b_cs] : 0.0;
-        }
-        __syncthreads();
-        const double* Ag = As + g * GK * (TM + 1);
-        const double* Bg = Bs + g * GK * (TN + 1);
-#pragma unroll 4
-        for (int l = 0; l < GK; ++l) {
-          double a[RM], b[RN];
-#pragma unroll
-          for (int p = 0; p < RM; ++p) a[p] = Ag[l * (TM + 1) + ty + TY * p];
-#pragma unroll
-          for (int q = 0; q < RN; ++q) b[q] = Bg[l * (TN + 1) + tx + TX * q];
-#pragma unroll
-          for (int p = 0; p < RM; ++p)
-#pragma unroll
-            for (int q = 0; q < RN; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
-        }
-        __syncthreads();
-      }
-      if (S > 1) {
-        for (int e = tid; e < TM * TN; e += 256) red[e] = 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int p = 0; p < RM; ++p)
-#pragma unroll
-          for (int q = 0; q < RN; ++q) atomicAdd(&red[(ty + TY * p) * TN + tx + TX * q], acc[p][q]);
-        __syncthreads();
-      }
-      if (S == 1 || g == 0) {
-#pragma unroll
-        for (int p = 0; p < RM; ++p)
-#pragma unroll
-          for (int q = 0; q < RN; ++q) {
-            const int il = ty + TY * p, jl = tx + TX * q;
-            const int i = i0 + il, j = j0 + jl;
-            if (i < m && j < n) {
-              double* c = C + (int64_t)i * op.c_rs + (int64_t)j * op.c_cs;
-              const double v = op.alpha * (S > 1 ? red[il * TN + jl] : acc[p][q]);
-              if (op.flags & GF_ATOMIC) atomicAdd(c, v);
-              else if (op.flags & GF_OVERWRITE) *c = v;
-              else *c += v;
-            }
-          }
-      }
-      if (S > 1) __syncthreads();
-    }
+__device__ __forceinline__ void gemm_tile_shape(int m, int n, int& mt, int& nt, int& nrt, int& nct) {
+  nct = (n + GTM - 1) / GTM;
+  nt = (n + nct - 1) / nct;
+  const int capm = min(GTM, max(1, GE / nt));
+  nrt = (m + capm - 1) / capm;
+  mt = (m + nrt - 1) / nrt;
 }
 
 __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
   const GemmOp op = ops[blockIdx.x];
-  const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = dimv(B, op.k, op.kd);
+  const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = max(dimv(B, op.k, op.kd), 0);
+  const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
   if (m <= 0 || n <= 0) return;
-  if (k <= 0 && !(op.flags & GF_OVERWRITE)) return;
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  if (k == 0 && !overwrite) return;
+  const int nslices = (k + GKS - 1) / GKS;
+  const int z0 = atomic ? (int)blockIdx.z : 0, zs = atomic ? (int)gridDim.z : 1;
+  if (blockIdx.z > 0 && (!atomic || z0 >= nslices)) return;
+  int mt, nt, nrt, nct;
+  gemm_tile_shape(m, n, mt, nt, nrt, nct);
+  if ((int)blockIdx.y >= nrt * nct) return;
+  extern __shared__ double gsm[];
+  double* As = gsm;                         // [GKS][GTM + 1]
+  double* Bs = gsm + GKS * (GTM + 1);       // [GKS][GTM + 1]
+  double* red = Bs + GKS * (GTM + 1);       // [256]
   const double* A = dptr(B, op.A);
   const double* Bm = dptr(B, op.B);
   double* C = dptr(B, op.C);
-  if (m <= 16 && n <= 16) gemm_tiles<16, 16, 2, 2, 4>(op, m, n, k, A, Bm, C, sm);
-  else if (m <= 32 && n <= 32) gemm_tiles<32, 32, 4, 4, 4>(op, m, n, k, A, Bm, C, sm);
-  else if (n <= 16) gemm_tiles<256, 16, 16, 1, 1>(op, m, n, k, A, Bm, C, sm);
-  else if (n <= 32) gemm_tiles<128, 32, 8, 2, 1>(op, m, n, k, A, Bm, C, sm);
-  else if (m <= 32) gemm_tiles<32, 128, 2, 8, 1>(op, m, n, k, A, Bm, C, sm);
-  else gemm_tiles<64, 64, 4, 4, 1>(op, m, n, k, A, Bm, C, sm);
-  if (threadIdx.x == 0) {
-    const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)(k > 0 ? k : 0));
+  const int tid = threadIdx.x;
+  const bool a_i_fast = op.a_rs <= op.a_cs;
+  const bool b_j_fast = op.b_cs <= op.b_rs;
+  const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
+  for (int tile = blockIdx.y; tile < nrt * nct; tile += gridDim.y) {
+    const int i0 = (tile % nrt) * mt, j0 = (tile / nrt) * nt;
+    const int mi = min(mt, m - i0), nj = min(nt, n - j0);
+    const int ne = mi * nj;
+    int G = 1;
+    while (G < 8 && ne * G * 2 <= 256) G *= 2;
+    const int nslot = ne * G;
+    // slots tid + 256 j (j < 4) of this thread; with G > 1 only slot 0 exists
+    int ii[4], jj[4];
+    int nmy = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int sl = tid + 256 * j;
+      const int e = sl < nslot ? sl % ne : 0;
+      ii[j] = e % mi;
+      jj[j] = e / mi;
+      nmy += sl < nslot ? 1 : 0;
+    }
+    const int grp = tid < nslot ? tid / ne : 0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int sl = z0; sl < nslices; sl += zs) {
+      const int L0 = sl * GKS, ks = min(GKS, k - L0);
+      __syncthreads();
+      for (int e = tid; e < mi * ks; e += 256) {
+        int i, l;
+        if (a_i_fast) {
+          i = e % mi;
+          l = e / mi;
+        } else {
+          l = e % ks;
+          i = e / ks;
+        }
+        const int gi = i0 + i, gl = L0 + l;
+        const double* src = A + (int64_t)gi * op.a_rs + (int64_t)gl * op.a_cs;
+        double v;
+        if (unitlower) v = gi > gl ? *src : (gi == gl ? 1.0 : 0.0);
+        else if (upper) v = gl >= gi ? *src : 0.0;
+        else v = *src;
+        As[l * (GTM + 1) + i] = v;
+      }
+      for (int e = tid; e < ks * nj; e += 256) {
+        int j, l;
+        if (b_j_fast) {
+          j = e % nj;
+          l = e / nj;
+        } else {
+          l = e % ks;
+          j = e / ks;
+        }
+        Bs[l * (GTM + 1) + j] = Bm[(int64_t)(L0 + l) * op.b_rs + (int64_t)(j0 + j) * op.b_cs];
+      }
+      __syncthreads();
+      if (G == 1) {
+        for (int l = 0; l < ks; ++l) {
+          const double* a = As + l * (GTM + 1);
+          const double* b = Bs + l * (GTM + 1);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < nmy) acc[j] = fma(a[ii[j]], b[jj[j]], acc[j]);
+        }
+      } else if (nmy > 0) {
+        const int lo = (grp * ks) / G, hi = ((grp + 1) * ks) / G;
+        for (int l = lo; l < hi; ++l) acc[0] = fma(As[l * (GTM + 1) + ii[0]], Bs[l * (GTM + 1) + jj[0]], acc[0]);
+      }
+    }
+    if (G > 1) {
+      __syncthreads();
+      if (tid < nslot) red[tid] = acc[0];
+      __syncthreads();
+      if (tid < ne) {
+        double t = red[tid];
+        for (int g = 1; g < G; ++g) t += red[tid + g * ne];
+        acc[0] = t;
+      }
+      nmy = tid < ne ? 1 : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j < nmy) {
+        double* c = C + (int64_t)(i0 + ii[j]) * op.c_rs + (int64_t)(j0 + jj[j]) * op.c_cs;
+        const double v = op.alpha * acc[j];
+        if (atomic) atomicAdd(c, v);
+        else if (overwrite) *c = v;
+        else *c += v;
+      }
+    }
+  }
+  if (threadIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+    const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)k);
     if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
     atomicAdd(&B.flops[NFC + K_GEMM], f);
   }
@@ -1377,6 +1401,7 @@ constexpr int CORE_SMEM = 2 * JSM * (JSM + 1) * (int)sizeof(double);
 static void set_attributes() {
   if (g_attr_set) return;
   cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM);
+  cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
   cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, CORE_SMEM);
   g_attr_set = true;
 }
@@ -1384,13 +1409,13 @@ static void set_attributes() {
 void prepare_kernels() { set_attributes(); }
 
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
-                        double h, cudaStream_t s) {
+                        double h, cudaStream_t s, int gy, int gz) {
   if (count <= 0) return cudaSuccess;
   set_attributes();
   switch (kind) {
     case K_GETRF: k_getrf<<<count, 256, 0, s>>>((const GetrfOp*)ops, B); break;
     case K_TRSM: k_trsm<<<count, 256, TRSM_SMEM, s>>>((const TrsmOp*)ops, B); break;
-    case K_GEMM: k_gemm<<<count, 256, 0, s>>>((const GemmOp*)ops, B); break;
+    case K_GEMM: k_gemm<<<dim3(count, gy, gz), 256, GEMM_SMEM, s>>>((const GemmOp*)ops, B); break;
     case K_COPY: k_copy<<<count, 256, 0, s>>>((const CopyOp*)ops, B); break;
     case K_STACK: k_stack<<<count, 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
     case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, B); break;

@@ -9,8 +9,10 @@ namespace hm {
 
 // sets the kernels' shared-memory attributes (call before capturing launches into a graph)
 void prepare_kernels();
+// gy, gz: extra grid dimensions of a GEMM launch (C tiles and reduction slices of one
+// micro-op spread over several CTAs); ignored by the other kinds
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
-                        double h, cudaStream_t s);
+                        double h, cudaStream_t s, int gy = 1, int gz = 1);
 cudaError_t launch_nn2(const double* P, int n, double* out, cudaStream_t s);
 cudaError_t launch_exact_mv(const double* P, int n, double h, const double* x, int64_t ldx, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);

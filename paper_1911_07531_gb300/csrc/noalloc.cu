@@ -17,6 +17,7 @@
 
 #include "../../include/hmgb300.h"
 #include "kernels.h"
+#include "plan.h"
 
 namespace hm {
 // defined in api.cu: sets the thread's last-error message and returns `code`
@@ -179,10 +180,13 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   B.i[IS_S] = ints;
   B.flops = (unsigned long long*)(base + oCnt);
   B.status = (int*)(base + oCnt + NFC + NKIND);
+  int gy0, gz0, gy1, gz1;
+  gemm_grid(g, 2, gy0, gz0);
+  gemm_grid(g + 2, 2, gy1, gz1);
   ce = launch_kind(K_STACK, dt, 1, de, B, 0.0, s);
-  if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
   if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);
-  if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s, gy1, gz1);
   int kk = 0;
   if (!ce) ce = cudaMemcpyAsync(&kk, ints, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (!ce) ce = cudaStreamSynchronize(s);

@@ -25,6 +25,33 @@
 
 namespace hm {
 
+void gemm_grid(const GemmOp* ops, int count, int& gy, int& gz) {
+  // Dynamic sizes (ranks) are not known here; they are taken as 16 for the estimate. A CTA
+  // should get about 32k FMAs (16k cycles of one SM's FP64 pipe); the launch stays within
+  // about four CTAs per SM.
+  constexpr double kTarget = 32768.0, kDyn = 16.0;
+  constexpr int kSms = 152, kMaxSplit = 16, kTile = 1024, kSlice = 32;
+  gy = gz = 1;
+  if (count >= 2 * kSms) return;
+  double wmax = 0.0;
+  int tiles = 1, slices = 1;
+  for (int q = 0; q < count; ++q) {
+    const GemmOp& o = ops[q];
+    const double m = o.m + (o.md ? kDyn : 0.0), n = o.n + (o.nd ? kDyn : 0.0), k = o.k + (o.kd ? kDyn : 0.0);
+    const double w = m * n * k;
+    if (w > wmax) {
+      wmax = w;
+      tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
+      slices = (o.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
+    }
+  }
+  const int want = std::min(kMaxSplit, std::max(1, (int)(wmax / kTarget + 0.5)));
+  const int room = std::max(1, 4 * kSms / count);
+  const int split = std::min(want, room);
+  gy = std::max(1, std::min(split, tiles));
+  gz = std::max(1, std::min(split / gy, slices));
+}
+
 namespace {
 
 constexpr int KMAX_STACK = 256;     // largest stacked rank of one rounded addition
@@ -618,6 +645,8 @@ struct Ctx {
       put(K_TRSM, (int)w.trsm[ph].size(), (int)plan.trsm.size());
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
       put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
+      if (!w.gemm[ph].empty())
+        gemm_grid(w.gemm[ph].data(), (int)w.gemm[ph].size(), plan.launches.back().gy, plan.launches.back().gz);
       plan.gemm.insert(plan.gemm.end(), w.gemm[ph].begin(), w.gemm[ph].end());
       if (!w.stack[ph].empty()) {
         put(K_STACK, (int)w.stack[ph].size(), (int)plan.trunc.size());

@@ -33,7 +33,13 @@ void build_layout(const ClusterTree& ct, const BlockTree& bt, int rank_cap, Layo
 
 struct Launch {
   int kind, begin, count;
+  int gy = 1, gz = 1;   // GEMM launches: CTAs per micro-op along C tiles / reduction slices
 };
+
+// Grid split of a GEMM launch: large micro-ops of a narrow launch get several CTAs (tiles of C
+// along y, reduction slices of accumulating micro-ops along z) so that they do not run on one
+// SM; launches that already fill the GPU stay one CTA per micro-op.
+void gemm_grid(const GemmOp* ops, int count, int& gy, int& gz);
 
 struct Plan {
   std::vector<GetrfOp> getrf;
