@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <stdexcept>
@@ -140,6 +142,13 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
   const cudaStream_t stream = use_override ? stream_override : c->stream;
   std::vector<cudaEvent_t> ev;
   std::vector<int> evkind;
+  // with the launch log on, the kind's FLOP counter is copied after every launch (pinned host
+  // buffer, asynchronous), so that the log carries each launch's FLOPs
+  const char* log_path = prof ? std::getenv("HMGB300_LAUNCH_LOG") : nullptr;
+  unsigned long long* fl_host = nullptr;
+  if (log_path && cudaMallocHost(&fl_host, (dp.host.launches.size() + 1) * sizeof(unsigned long long)) != cudaSuccess)
+    fl_host = nullptr;
+  size_t li = 0;
   for (const Launch& L : dp.host.launches) {
     const int buf = L.kind == K_CORE ? K_STACK : L.kind;
     const char* base = (const char*)dp.ops[buf].p;
@@ -154,11 +163,24 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
       evkind.push_back(L.kind);
     }
     cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, stream, L.gy, L.gz);
-    if (e != cudaSuccess) return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      if (fl_host) cudaFreeHost(fl_host);
+      return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    }
     if (prof) cudaEventRecord(ev.back(), stream);
+    if (fl_host)
+      cudaMemcpyAsync(fl_host + li, B.flops + NFC + L.kind, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                      stream);
+    ++li;
   }
   if (prof) {
     CU(cudaStreamSynchronize(stream));
+    // HMGB300_LAUNCH_LOG=<file>: one CSV line per launch of a profiled run (kind, micro-ops,
+    // grid y/z, ms and, for GEMM launches, the largest static m n k with 'd' marking a
+    // dimension that has a dynamic part)
+    FILE* log = log_path ? std::fopen(log_path, "a") : nullptr;
+    if (log) std::fprintf(log, "kind,count,gy,gz,ms,flops,m,n,k\n");
+    unsigned long long prev[NKIND] = {0};
     for (size_t q = 0; q < evkind.size(); ++q) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
@@ -166,8 +188,32 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
       prof->launches[evkind[q]] += 1;
       cudaEventDestroy(ev[2 * q]);
       cudaEventDestroy(ev[2 * q + 1]);
+      if (log) {
+        const Launch& L = dp.host.launches[q];
+        std::string dims = ",,,";
+        if (L.kind == K_GEMM) {
+          double wmax = -1.0;
+          for (int i = L.begin; i < L.begin + L.count; ++i) {
+            const GemmOp& o = dp.host.gemm[i];
+            const double w = (o.m + (o.md ? 16.0 : 0.0)) * (o.n + (o.nd ? 16.0 : 0.0)) * (o.k + (o.kd ? 16.0 : 0.0));
+            if (w > wmax) {
+              wmax = w;
+              dims = "," + std::to_string(o.m) + (o.md ? "d" : "") + "," + std::to_string(o.n) + (o.nd ? "d" : "") +
+                     "," + std::to_string(o.k) + (o.kd ? "d" : "");
+            }
+          }
+        }
+        unsigned long long f = 0;
+        if (fl_host) {
+          f = fl_host[q] - prev[L.kind];
+          prev[L.kind] = fl_host[q];
+        }
+        std::fprintf(log, "%d,%d,%d,%d,%.4f,%llu%s\n", L.kind, L.count, L.gy, L.gz, ms, f, dims.c_str());
+      }
     }
+    if (log) std::fclose(log);
   }
+  if (fl_host) cudaFreeHost(fl_host);
   return HM_OK;
 }
 
@@ -876,7 +922,7 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
     g[q].md = t.Kd;
     g[q].nd = t.Kd;
     g[q].k = (int)rows[q];
-    g[q].flags = GF_ATOMIC;
+    g[q].flags = GF_ATOMIC | GF_SYM_UPPER;
     g[q].alpha = 1.0;
     g[q].fclass = FC_NONE;
   }

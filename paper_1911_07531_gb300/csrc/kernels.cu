@@ -138,6 +138,27 @@ __device__ __forceinline__ void gemm_tile_shape(int m, int n, int& mt, int& nt, 
   mt = (m + nrt - 1) / nrt;
 }
 
+template <int W>
+__device__ __forceinline__ void gemm_slice(const double* As, const double* Bs, int ks, const int (&ii)[4],
+                                           const int (&jj)[4], double (&acc)[4]) {
+  for (int l = 0; l < ks; ++l) {
+    const double* a = As + l * (GTM + 1);
+    const double* b = Bs + l * (GTM + 1);
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = fma(a[ii[j]], b[jj[j]], acc[j]);
+  }
+}
+
+// Entries (il, jl) of a tile at (i0, j0) with i0 + il <= j0 + jl, counted column by column:
+// column jl holds clamp(jl + c0, 0, mi) of them (c0 = j0 - i0 + 1); sym_prefix(x) is the number
+// in columns 0..x-1.
+__device__ __forceinline__ int sym_tri(int v, int mi) {   // sum_{u=0}^{v-1} clamp(u, 0, mi)
+  return v <= mi + 1 ? v * (v - 1) / 2 : mi * (mi + 1) / 2 + (v - mi - 1) * mi;
+}
+__device__ __forceinline__ int sym_prefix(int x, int c0, int mi) {
+  return sym_tri(max(0, c0 + x), mi) - sym_tri(max(0, c0), mi);
+}
+
 __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
   const GemmOp op = ops[blockIdx.x];
   const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = max(dimv(B, op.k, op.kd), 0);
@@ -161,10 +182,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
   const bool a_i_fast = op.a_rs <= op.a_cs;
   const bool b_j_fast = op.b_cs <= op.b_rs;
   const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
+  const bool sym = op.flags & GF_SYM_UPPER;
   for (int tile = blockIdx.y; tile < nrt * nct; tile += gridDim.y) {
     const int i0 = (tile % nrt) * mt, j0 = (tile / nrt) * nt;
     const int mi = min(mt, m - i0), nj = min(nt, n - j0);
-    const int ne = mi * nj;
+    const int c0 = j0 - i0 + 1;
+    if (sym && c0 + nj - 1 <= 0) continue;        // tile strictly below the diagonal
+    const int ne = sym ? sym_prefix(nj, c0, mi) : mi * nj;
     int G = 1;
     while (G < 8 && ne * G * 2 <= 256) G *= 2;
     const int nslot = ne * G;
@@ -175,11 +199,23 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
     for (int j = 0; j < 4; ++j) {
       const int sl = tid + 256 * j;
       const int e = sl < nslot ? sl % ne : 0;
-      ii[j] = e % mi;
-      jj[j] = e / mi;
+      if (sym) {
+        int lo = 0, hi = nj - 1;                  // last column whose prefix is <= e
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sym_prefix(mid, c0, mi) <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        jj[j] = lo;
+        ii[j] = e - sym_prefix(lo, c0, mi);
+      } else {
+        ii[j] = e % mi;
+        jj[j] = e / mi;
+      }
       nmy += sl < nslot ? 1 : 0;
     }
     const int grp = tid < nslot ? tid / ne : 0;
+    const int wmy = __reduce_max_sync(0xffffffffu, (unsigned)nmy);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int sl = z0; sl < nslices; sl += zs) {
       const int L0 = sl * GKS, ks = min(GKS, k - L0);
@@ -214,12 +250,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
       }
       __syncthreads();
       if (G == 1) {
-        for (int l = 0; l < ks; ++l) {
-          const double* a = As + l * (GTM + 1);
-          const double* b = Bs + l * (GTM + 1);
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (j < nmy) acc[j] = fma(a[ii[j]], b[jj[j]], acc[j]);
+        // the slot count is made warp-uniform so that no DFMA is issued for an empty slot
+        // (a predicated-off DFMA still takes its turn on the FP64 pipe); the extra lanes of
+        // a warp compute on slot 0's indices into accumulators that are never written
+        switch (wmy) {
+          case 4: gemm_slice<4>(As, Bs, ks, ii, jj, acc); break;
+          case 3: gemm_slice<3>(As, Bs, ks, ii, jj, acc); break;
+          case 2: gemm_slice<2>(As, Bs, ks, ii, jj, acc); break;
+          case 1: gemm_slice<1>(As, Bs, ks, ii, jj, acc); break;
+          default: break;
         }
       } else if (nmy > 0) {
         const int lo = (grp * ks) / G, hi = ((grp + 1) * ks) / G;
@@ -864,6 +903,15 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   double* Gw = dptr(B, op.Gw);
   double* Gz = dptr(B, op.Gz);
   double* work = dptr(B, op.work);
+  // the Gram GEMMs wrote the upper triangles only
+  for (int e = tid; e < K * K; e += nt) {
+    const int i = e % K, j = e / K;
+    if (i > j) {
+      Gw[i + (int64_t)j * Kc] = Gw[j + (int64_t)i * Kc];
+      Gz[i + (int64_t)j * Kc] = Gz[j + (int64_t)i * Kc];
+    }
+  }
+  __syncthreads();
   double* R = Gw;                              // K x K (ld Kc): the Cholesky factor of the equilibrated G_W
   double* Bm = work;                           // K x r
   double* T1 = work + (int64_t)Kc * Kc;        // K x r, later a temporary

@@ -139,7 +139,7 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
     g[q].md = t.Kd;
     g[q].nd = t.Kd;
     g[q].k = (int)rows[q];
-    g[q].flags = GF_ATOMIC;
+    g[q].flags = GF_ATOMIC | GF_SYM_UPPER;
     g[q].alpha = 1.0;
     g[q].fclass = FC_NONE;
   }

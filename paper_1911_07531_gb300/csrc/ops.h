@@ -35,7 +35,9 @@ struct Bases {
 // flop accounting classes (model of the truncation counts QR + core + SVD + rebuild)
 enum FlopClass : int { FC_GETRF = 0, FC_TRSM = 1, FC_GEMM = 2, FC_TRUNC = 3, FC_NONE = 4, NFC = 5 };
 
-enum GemmFlags : int { GF_ATOMIC = 1, GF_OVERWRITE = 2, GF_A_UPPER = 4, GF_A_UNITLOWER = 8 };
+// GF_SYM_UPPER: C is symmetric (a Gram matrix A^T A); only the entries i <= j are computed and
+// written, the consumer mirrors them
+enum GemmFlags : int { GF_ATOMIC = 1, GF_OVERWRITE = 2, GF_A_UPPER = 4, GF_A_UNITLOWER = 8, GF_SYM_UPPER = 16 };
 
 // C(i,j) (+)= alpha * sum_l A(i,l) B(l,j),  X(i,j) = X[i*rs + j*cs]
 struct GemmOp {

@@ -608,12 +608,12 @@ struct Ctx {
         for (int i0 = 0; i0 < L.m; i0 += GEMM_KCHUNK) {
           int mi = std::min(GEMM_KCHUNK, L.m - i0);
           gemm(ph + 1, op.Wst + (uint64_t)i0, L.m, 1, op.Wst + (uint64_t)i0, 1, L.m, op.Gw, 1, Kc, Kd, Kd,
-               {mi, 0}, 1.0, GF_ATOMIC, FC_NONE);
+               {mi, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE);
         }
         for (int i0 = 0; i0 < L.n; i0 += GEMM_KCHUNK) {
           int ni = std::min(GEMM_KCHUNK, L.n - i0);
           gemm(ph + 1, op.Zst + (uint64_t)i0, L.n, 1, op.Zst + (uint64_t)i0, 1, L.n, op.Gz, 1, Kc, Kd, Kd,
-               {ni, 0}, 1.0, GF_ATOMIC, FC_NONE);
+               {ni, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE);
         }
         w.core[ph + 2].push_back(op);
         const Dim rk{0, op.rank};
