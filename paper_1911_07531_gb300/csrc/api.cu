@@ -945,6 +945,9 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   }
   if (!dalloc(c, ops, sizeof(t) + sizeof(g)) || !dalloc(c, ent, sizeof(e)))
     return done(fail(HM_ENOMEM, "hm_truncate: allocator returned NULL"));
+  int gy0, gz0, gy1, gz1;
+  gemm_grid(g, 2, gy0, gz0);
+  gemm_grid(g + 2, 2, gy1, gz1);
   cudaStream_t s = c->stream;
   CU(cudaMemcpyAsync(ops.p, &t, sizeof(t), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync((char*)ops.p + sizeof(t), g, sizeof(g), cudaMemcpyHostToDevice, s));
@@ -959,9 +962,6 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   B.status = k.status();
   const TruncOp* dt = (const TruncOp*)ops.p;
   const GemmOp* dg = (const GemmOp*)((char*)ops.p + sizeof(t));
-  int gy0, gz0, gy1, gz1;
-  gemm_grid(g, 2, gy0, gz0);
-  gemm_grid(g + 2, 2, gy1, gz1);
   cudaError_t ce = launch_kind(K_STACK, dt, 1, (const StackEntry*)ent.p, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
   if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);

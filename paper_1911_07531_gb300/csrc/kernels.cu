@@ -123,8 +123,8 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
 // elements of a tile, and for tiles of fewer than 128 elements G = 2..8 threads split the
 // reduction of one element (partial sums combined in shared memory). A slice of GKS reduction
 // steps of both operands is staged in shared memory per pass. Tiles of one micro-op are spread
-// over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z,
-// so that a large micro-op does not sit on a single SM.
+// over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z
+// (per micro-op counts in GemmOp::split), so that a large micro-op does not sit on one SM.
 constexpr int GE = 1024;      // largest C tile (elements)
 constexpr int GTM = 128;      // largest C tile side
 constexpr int GKS = 32;       // staged reduction slice
@@ -166,8 +166,10 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
   if (m <= 0 || n <= 0) return;
   if (k == 0 && !overwrite) return;
   const int nslices = (k + GKS - 1) / GKS;
-  const int z0 = atomic ? (int)blockIdx.z : 0, zs = atomic ? (int)gridDim.z : 1;
-  if (blockIdx.z > 0 && (!atomic || z0 >= nslices)) return;
+  const int sy = max(1, op.split & 0xffff), sz = atomic ? max(1, op.split >> 16) : 1;
+  if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;
+  const int z0 = blockIdx.z, zs = sz;
+  if (z0 > 0 && z0 >= nslices) return;
   int mt, nt, nrt, nct;
   gemm_tile_shape(m, n, mt, nt, nrt, nct);
   if ((int)blockIdx.y >= nrt * nct) return;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
   const bool b_j_fast = op.b_cs <= op.b_rs;
   const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
   const bool sym = op.flags & GF_SYM_UPPER;
-  for (int tile = blockIdx.y; tile < nrt * nct; tile += gridDim.y) {
+  for (int tile = blockIdx.y; tile < nrt * nct; tile += sy) {
     const int i0 = (tile % nrt) * mt, j0 = (tile / nrt) * nt;
     const int mi = min(mt, m - i0), nj = min(nt, n - j0);
     const int c0 = j0 - i0 + 1;
@@ -647,6 +649,7 @@ __device__ void jacobi_eigen(T* A, int lda, T* V, int ldv, int K, T* cs, T* sn, 
 
 #ifdef HM_CORE_TIMING
 __device__ long long g_core_stamp[16];
+__device__ float g_core_gf[64 * 64];
 #define CORE_STAMP(i)                                  \
   do {                                                 \
     __syncthreads();                                   \
@@ -662,11 +665,18 @@ constexpr int KMAX = 256;       // largest stacked rank of one rounded addition
 constexpr int JSM = 64;         // Jacobi problems up to this size run in shared memory
 
 // Reciprocal of x in [1e-30, 1e30] to full FP64 accuracy with three dependent FP64 operations:
-// r0 = 1/x correctly rounded in FP32, e = 1 - x r0 (|e| < 2^-22), 1/x = r0 (1 + e + e^2 + ...);
-// the truncated series leaves r0 e^3 ~ 2^-66 r0. GB300 spends ~64 cycles on each dependent FP64
-// operation, so this is for latency-critical serial sections.
+// r0 = 1/x from the FP32 approximate reciprocal (the FP32 operand and the FP64 seed are formed
+// by integer moves of the exponent and the leading mantissa bits, not by conversion
+// instructions), e = 1 - x r0 (|e| < 2^-21), 1/x = r0 (1 + e + e^2 + ...); the truncated series
+// leaves r0 e^3 ~ 2^-63 r0.
+// GB300 spends ~64 cycles on each dependent FP64 operation, so this is for serial sections.
 __device__ __forceinline__ double fast_rcp(double x) {
-  const double r0 = (double)__frcp_rn((float)x);
+  constexpr long long kBias = (long long)(1023 - 127) << 23;   // exponent rebias, FP32 bit position
+  const long long xb = __double_as_longlong(x);
+  const float xf = __int_as_float((int)((xb >> 29) - kBias));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));   // ~1 ulp; the series absorbs it
+  const double r0 = __longlong_as_double(((long long)__float_as_int(rf) + kBias) << 29);
   const double e = fma(-x, r0, 1.0);
   return fma(r0, fma(e, e, e), r0);
 }
@@ -678,101 +688,112 @@ __device__ __forceinline__ long long order_key(double v) {
   return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
 }
 
+// Pivot key of a diagonal entry at position i (< 256): the high word of a positive double
+// (sign, exponent, 20 mantissa bits) with its low 8 bits replaced by 255 - i, so that an
+// unsigned max picks the largest entry to ~2^-12 relative and the lowest index among near
+// ties; 0 for entries <= 0.
+__device__ __forceinline__ unsigned pivot_key(double v, int i) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 ? (((unsigned)(b >> 32)) & ~255u) | (unsigned)(255 - i) : 0u;
+}
+
 // Pivoted Cholesky (outer-product form, diagonal pivoting) of the symmetric positive
-// semi-definite n x n matrix A (ld lda; only the lower triangle is read and written), in place
-// with physical symmetric interchanges: on return P^T A P = L L^T with L lower trapezoidal, its
-// column q (rows q..n-1) in column q of A for q < rank, and perm[q] the original index of
-// pivoted position q (perm must hold 0..n-1 on entry). Stops when the largest remaining
-// diagonal entry is <= tol (tol >= 0); returns the rank. The pivots must lie in [1e-30, 1e30]
-// (callers scale A to unit diagonal or unit trace).
-// One step: warp 0 picks the pivot (an integer max over the bit patterns of the positive
-// diagonal entries, low mantissa bits replaced by the index so that ties go to the lowest
-// index), interchanges, and forms 1/pivot; then the other warps update their columns of the
-// trailing lower triangle with the unscaled pivot column, A_ik -= a_ij (a_kj / a_jj). The
-// columns are scaled by 1/sqrt(pivot) once at the end, all in parallel, so that a step's
-// serial FP64 chain is three operations long. Two block barriers per step.
-// s_flag: one shared int, s_val: one shared double (block-wide broadcast slots).
-#ifdef HM_CORE_TIMING
-__device__ long long g_chol_phase[4];
-#define CHOL_T(v) long long v = clock64()
-#define CHOL_ACC(i, a, b) \
-  if (threadIdx.x == 0) g_chol_phase[i] += (b) - (a)
-#else
-#define CHOL_T(v)
-#define CHOL_ACC(i, a, b)
-#endif
-__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, int* s_flag,
-                                double* s_val) {
+// semi-definite n x n matrix A (n <= 256, ld lda; only the lower triangle is read and written),
+// in place with physical symmetric interchanges: on return P^T A P = L L^T with L lower
+// trapezoidal, its column q (rows q..n-1) in column q of A for q < rank, and perm[q] the
+// original index of pivoted position q (perm must hold 0..n-1 on entry). Stops when the largest
+// remaining diagonal entry is <= tol (tol >= 0); returns the rank. The pivots must lie in
+// [1e-30, 1e30] (callers scale A to unit diagonal or unit trace).
+// Step j: warp 0 interchanges positions j and p_j (chosen in the previous step); then warps
+// 1.. update the trailing lower triangle with the unscaled pivot column, A_ik -= a_ij (a_kj /
+// a_jj), while warp 0 updates its copy dg of the trailing diagonal with the same operations
+// (bitwise the same values), picks p_{j+1} from it and forms 1/a_{p_{j+1}} -- the pivot search
+// and the reciprocal of the next step overlap this step's update. Columns are scaled by
+// 1/sqrt(pivot) once at the end. dg: n doubles of shared scratch; s_flag: 2 ints, s_val: 2
+// doubles, s_pidx: 2 ints of shared scratch (double-buffered broadcast slots).
+__device__ __forceinline__ void chol_select(const double* dg, int j, int n, double tol, int* s_flag,
+                                            double* s_val, int* s_pidx, int slot) {
+  // warp 0 only
+  const int lane = threadIdx.x & 31;
+  unsigned best = 0;
+  for (int i = j + lane; i < n; i += 32) best = max(best, pivot_key(dg[i], i));
+  best = __reduce_max_sync(0xffffffffu, best);
+  const int p = best ? 255 - (int)(best & 255u) : -1;
+  if (lane == 0) {
+    const double piv = p >= 0 ? dg[p] : 0.0;
+    const bool go = p >= 0 && __double_as_longlong(piv) > __double_as_longlong(fmax(tol, 0.0));
+    s_flag[slot] = go ? 1 : 0;
+    s_pidx[slot] = p;
+    if (go) s_val[slot] = fast_rcp(piv);
+  }
+}
+
+__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, double* dg, int* s_flag,
+                                double* s_val, int* s_pidx) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const long long tol_key = __double_as_longlong(fmax(tol, 0.0));
+  if (warp == 0) {
+    for (int i = lane; i < n; i += 32) dg[i] = A[i + (int64_t)i * lda];
+    __syncwarp();
+    chol_select(dg, 0, n, tol, s_flag, s_val, s_pidx, 0);
+  }
+  __syncthreads();
   int j = 0;
   for (; j < n; ++j) {
-    CHOL_T(t0);
-    if (warp == 0) {
-      long long best = -1;
-      for (int i = j + lane; i < n; i += 32) {
-        const long long b = __double_as_longlong(A[i + (int64_t)i * lda]);
-        const long long key = b > 0 ? ((b & ~511LL) | (511 - i)) : -1LL;
-        best = key > best ? key : best;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-        best = ob > best ? ob : best;
-      }
-      const int p = best < 0 ? -1 : 511 - (int)(best & 511);
-      const double piv = p < 0 ? 0.0 : A[p + (int64_t)p * lda];
-      const bool go = p >= 0 && __double_as_longlong(piv) > tol_key;
-      if (go && p != j) {
-        // interchange positions j and p: rows of the finished columns, the two diagonal
-        // entries, and the pairs of the trailing lower triangle that trade places
-        for (int k = lane; k < n; k += 32) {
-          double *x, *y;
-          if (k < j) {
-            x = A + j + (int64_t)k * lda;
-            y = A + p + (int64_t)k * lda;
-          } else if (k == j) {
-            x = A + j + (int64_t)j * lda;
-            y = A + p + (int64_t)p * lda;
-          } else if (k < p) {
-            x = A + k + (int64_t)j * lda;
-            y = A + p + (int64_t)k * lda;
-          } else if (k > p) {
-            x = A + k + (int64_t)j * lda;
-            y = A + k + (int64_t)p * lda;
-          } else {
-            continue;
-          }
-          const double t = *x;
-          *x = *y;
-          *y = t;
+    const int slot = j & 1;
+    if (!s_flag[slot]) break;
+    const int p = s_pidx[slot];
+    if (warp == 0 && p != j) {
+      // interchange positions j and p: rows of the finished columns, the two diagonal
+      // entries, and the pairs of the trailing lower triangle that trade places
+      for (int k = lane; k < n; k += 32) {
+        double *x, *y;
+        if (k < j) {
+          x = A + j + (int64_t)k * lda;
+          y = A + p + (int64_t)k * lda;
+        } else if (k == j) {
+          x = A + j + (int64_t)j * lda;
+          y = A + p + (int64_t)p * lda;
+        } else if (k < p) {
+          x = A + k + (int64_t)j * lda;
+          y = A + p + (int64_t)k * lda;
+        } else if (k > p) {
+          x = A + k + (int64_t)j * lda;
+          y = A + k + (int64_t)p * lda;
+        } else {
+          continue;
         }
-        if (lane == 0) {
-          const int t = perm[j];
-          perm[j] = perm[p];
-          perm[p] = t;
-        }
+        const double t = *x;
+        *x = *y;
+        *y = t;
       }
       if (lane == 0) {
-        *s_flag = go ? 1 : 0;
-        if (go) *s_val = fast_rcp(piv);
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+        const double d = dg[j];
+        dg[j] = dg[p];
+        dg[p] = d;
       }
     }
     __syncthreads();
-    CHOL_T(t1);
-    CHOL_ACC(0, t0, t1);
-    if (!*s_flag) break;
-    const int w0 = nw > 1 ? 1 : 0;    // warp 0 sits out the update when there are others
-    if (warp >= w0) {
-      const double ipiv = *s_val;
+    const double ipiv = s_val[slot];
+    if (warp > 0 || nw == 1) {
+      const int w0 = nw > 1 ? 1 : 0;
       for (int jj = j + 1 + warp - w0; jj < n; jj += nw - w0) {
         const double t = A[jj + (int64_t)j * lda] * ipiv;
         for (int ii = jj + lane; ii < n; ii += 32)
           A[ii + (int64_t)jj * lda] = fma(-A[ii + (int64_t)j * lda], t, A[ii + (int64_t)jj * lda]);
       }
     }
+    if (warp == 0) {
+      for (int i = j + 1 + lane; i < n; i += 32) {
+        const double a = A[i + (int64_t)j * lda];
+        dg[i] = fma(-a, a * ipiv, dg[i]);
+      }
+      __syncwarp();
+      chol_select(dg, j + 1, n, tol, s_flag, s_val, s_pidx, slot ^ 1);
+    }
     __syncthreads();
-    CHOL_T(t2);
-    CHOL_ACC(2, t1, t2);
   }
   // scale the columns: L(:, q) = a(:, q) / sqrt(pivot_q)
   for (int q = warp; q < j; q += nw) {
@@ -787,14 +808,17 @@ __device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol
 }
 
 // One-sided (Hestenes) Jacobi in FP32 on the columns of G (rows x cols, cols even, ld ldg):
-// column pairs are rotated until orthogonal, and the rotations are accumulated into V (cols x cols, ld ldv); "orthogonal" means |g_a . g_b| below the FP32
-// rounding level of the dot products. Applied to a Cholesky factor of a graded
-// positive definite matrix it yields singular values with high relative accuracy (Demmel and
-// Veselic, "Jacobi's method is more accurate than QR", 1992). One warp handles one pair at a
-// time (dot products by warp shuffles), so a round needs a single block barrier.
+// column pairs are rotated until orthogonal, and the rotations are accumulated into V (cols x
+// cols, ld ldv) when V is given; "orthogonal" means |g_a . g_b| below the FP32 rounding level
+// of the dot products. Applied to a Cholesky factor of a graded positive definite matrix it
+// yields singular values with high relative accuracy (Demmel and Veselic, "Jacobi's method is
+// more accurate than QR", 1992). Round-robin pairing; one half-warp (16 lanes) handles one pair
+// of a round, so a block of 512 threads runs all pairs of a round concurrently for cols <= 64,
+// and a round costs one block barrier.
 __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
                                     int max_sweeps) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
+  const unsigned hmask = 0xffffu << (threadIdx.x & 16);
   const int half = cols / 2;
   // orthogonality target at the FP32 rounding level of dot products of length `rows`
   const float tol = fmaxf(1e-6f, 6e-8f * (float)rows);
@@ -803,10 +827,7 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int r = 0; r < cols - 1; ++r) {
-#ifdef HM_CORE_TIMING
-      long long tj0 = clock64(), tj1 = tj0, tj2 = tj0;
-#endif
-      for (int q = warp; q < half; q += nw) {
+      for (int q = hw; q < half; q += nh) {
         // round-robin pairing: position 0 fixed, positions 1..cols-1 rotate by r
         int x = q - 1 + r, y = cols - 2 - q + r;
         x = x >= cols - 1 ? x - (cols - 1) : x;
@@ -817,30 +838,17 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
         float* ga = G + a * ldg;
         float* gb = G + b * ldg;
         float al = 0.f, be = 0.f, ga_b = 0.f;
-#ifdef HM_CORE_TIMING
-        const long long tja = clock64();
-#endif
-        for (int l = lane; l < rows; l += 32) {
+        for (int l = hl; l < rows; l += 16) {
           const float u = ga[l], v = gb[l];
           al = fmaf(u, u, al);
           be = fmaf(v, v, be);
           ga_b = fmaf(u, v, ga_b);
         }
-#ifdef HM_CORE_TIMING
-        const long long tjb = clock64();
-        if (threadIdx.x == 0) {
-          g_core_stamp[13] += tja - tj0;
-          g_core_stamp[14] += tjb - tja;
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(hmask, al, o);
+          be += __shfl_xor_sync(hmask, be, o);
+          ga_b += __shfl_xor_sync(hmask, ga_b, o);
         }
-#endif
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga_b += __shfl_xor_sync(0xffffffffu, ga_b, o);
-        }
-#ifdef HM_CORE_TIMING
-        tj1 = clock64();
-#endif
         if (al > 0.f && be > 0.f && fabsf(ga_b) > tol * sqrtf(al) * sqrtf(be)) {
           const float th = (be - al) / (2.0f * ga_b);
           float t;
@@ -848,7 +856,7 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
           else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
           const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
           if (s != 0.f) {
-            for (int l = lane; l < rows; l += 32) {
+            for (int l = hl; l < rows; l += 16) {
               const float u = ga[l], v = gb[l];
               ga[l] = c * u - s * v;
               gb[l] = s * u + c * v;
@@ -856,28 +864,17 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
             if (V) {
               float* va = V + a * ldv;
               float* vb = V + b * ldv;
-              for (int l = lane; l < cols; l += 32) {
+              for (int l = hl; l < cols; l += 16) {
                 const float u = va[l], v = vb[l];
                 va[l] = c * u - s * v;
                 vb[l] = s * u + c * v;
               }
             }
-            if (lane == 0) *flag = 1;
+            if (hl == 0) *flag = 1;
           }
         }
-#ifdef HM_CORE_TIMING
-        tj2 = clock64();
-#endif
       }
       __syncthreads();
-#ifdef HM_CORE_TIMING
-      if (threadIdx.x == 0) {
-        const long long tj3 = clock64();
-        g_core_stamp[10] += tj1 - tj0;
-        g_core_stamp[11] += tj2 - tj1;
-        g_core_stamp[12] += tj3 - tj2;
-      }
-#endif
     }
     if (*flag == 0) break;
     __syncthreads();
@@ -939,7 +936,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   CORE_STAMP(1);
   // 2. pivoted Cholesky G' = Pi Rf^T Rf Pi^T; the tolerance is the noise level of a Gram
   //    matrix. Rf is kept transposed in pivoted order: Rf(q, l) = R[l + q * Kc] for l >= q.
-  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, &s_int[2], &red[2]);
+  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, lam, &s_int[2], &red[2], pa);
   if (Rc != R) {
     for (int e = tid; e < K * K; e += nt) {
       int i = e % K, j = e / K;
@@ -952,22 +949,21 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     return;
   }
   CORE_STAMP(2);
-  // 3. Bm = D Pi Rf^T  (K x r): Bm(perm[l], q) = d[perm[l]] * Rf(q, l) for l >= q
+  // 3. Bm = D Pi Rf^T (K x r), kept with its rows in pivoted order: Bm(l, q) = d[perm[l]] Rf(q, l)
+  //    for l >= q and zero above, so that the products below skip the zero triangle
   for (int e = tid; e < K * r; e += nt) {
-    int l = e % K, q = e / K;
-    int pl = perm[l];
-    double v = 0.0;
-    if (l >= q) v = d[pl] * R[l + (int64_t)q * Kc];
-    Bm[pl + (int64_t)q * Kc] = v;
+    const int l = e % K, q = e / K;
+    Bm[l + (int64_t)q * Kc] = l >= q ? d[perm[l]] * R[l + (int64_t)q * Kc] : 0.0;
   }
   __syncthreads();
-  // 4. M = Bm^T G_Z Bm  (r x r): the Gram matrix of Z Bm, whose eigen-decomposition gives the
-  //    singular values (squared) and right factors of W Z^T
+  // 4. M = Bm^T G_Z Bm (r x r): the Gram matrix of Z D Pi Rf^T, whose eigen-decomposition gives
+  //    the singular values (squared) and right factors of W Z^T. T1 = G_Z Pi Bm with rows in
+  //    the original order: T1(i, q) = sum_{l >= q} G_Z(i, perm[l]) Bm(l, q).
   for (int e = tid; e < K * r; e += nt) {
-    int i = e % K, q = e / K;
-    double s = 0.0;
-    for (int l = 0; l < K; ++l) s = fma(Gz[i + (int64_t)l * Kc], Bm[l + (int64_t)q * Kc], s);
-    T1[i + (int64_t)q * Kc] = s;
+    const int i = e % K, q = e / K;
+    double sm4 = 0.0;
+    for (int l = q; l < K; ++l) sm4 = fma(Gz[i + (int64_t)perm[l] * Kc], Bm[l + (int64_t)q * Kc], sm4);
+    T1[i + (int64_t)q * Kc] = sm4;
   }
   __syncthreads();
   const int rp = r + (r & 1);                  // even size (Jacobi pairs), zero padding
@@ -983,21 +979,15 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     Yj = T1;       // reused after M is formed (the global path keeps M in Gz)
     ldj = Kc;
   }
+  // M(p, q) = sum_{l >= p} Bm(l, p) T1(perm[l], q) for p <= q, mirrored (zero padding at rp > r)
   for (int e = tid; e < rp * rp; e += nt) {
-    int p = e % rp, q = e / rp;
-    double s = 0.0;
-    if (p < r && q < r)
-      for (int i = 0; i < K; ++i) s = fma(Bm[i + (int64_t)p * Kc], T1[i + (int64_t)q * Kc], s);
-    Mj[p + (int64_t)q * ldj] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < rp * rp; e += nt) {
-    int p = e % rp, q = e / rp;
-    if (p < q) {
-      double v = 0.5 * (Mj[p + (int64_t)q * ldj] + Mj[q + (int64_t)p * ldj]);
-      Mj[p + (int64_t)q * ldj] = v;
-      Mj[q + (int64_t)p * ldj] = v;
-    }
+    const int p = e % rp, q = e / rp;
+    if (p > q) continue;
+    double sm4 = 0.0;
+    if (q < r)
+      for (int l = p; l < K; ++l) sm4 = fma(Bm[l + (int64_t)p * Kc], T1[perm[l] + (int64_t)q * Kc], sm4);
+    Mj[p + (int64_t)q * ldj] = sm4;
+    Mj[q + (int64_t)p * ldj] = sm4;
   }
   __syncthreads();
   if (tid < 32) {
@@ -1010,7 +1000,9 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   const double tr = red[1];
   CORE_STAMP(3);
   // 5. eigen-decomposition M = X diag(lam) X^T
-  const bool dv = rp <= JSM && tr > 0.0;       // Drmac-Veselic path (FP32 vectors)
+  // Drmac-Veselic path (FP32 vectors) up to rp = 2 JSM: M and X in shared memory for rp <= JSM,
+  // in global scratch (Gz, T1) above, where the FP32 matrix takes all of the dynamic smem
+  const bool dv = rp <= 2 * JSM && tr > 0.0;
   if (dv) {
     // (a) FP64 pivoted Cholesky M / tr = P R2^T R2 P^T (in place in Mj);
     // (b) FP32 one-sided Jacobi on the columns of R2^T (below), whose column norms squared give
@@ -1026,14 +1018,15 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     __syncthreads();
     // the tolerance is one rounding unit of the trace: the Schur complement left behind perturbs
     // the eigenvalues by at most rp u tr, the rounding level of M itself
-    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, &s_int[2], &red[2]);
+    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, lam, &s_int[2], &red[2], pa);
     // Drmac-Veselic preconditioning: one-sided Jacobi on the columns of C = R2^T (the rows of the
     // pivoted Cholesky factor are graded and nearly orthogonal, so it converges in a few
     // sweeps): C Q = [s_1 u_1, ...] with C C^T = R2^T R2 = P^T M P, i.e. the columns of C Q are
     // the eigenvectors of P^T M P scaled by sqrt(eigenvalue); Q itself is not needed.
     const int rcp = rc + (rc & 1);
-    float* Gf = reinterpret_cast<float*>(Yj);          // rp x rcp, ld JSM + 1 (floats)
-    const int ldf = JSM + 1;
+    // rp x rcp floats: in the X region for rp <= JSM, else the whole dynamic smem (ld 2 JSM + 1)
+    float* Gf = rp <= JSM ? reinterpret_cast<float*>(Yj) : reinterpret_cast<float*>(smem);
+    const int ldf = rp <= JSM ? JSM + 1 : 2 * JSM + 1;
     for (int e = tid; e < rp * rcp; e += nt) {
       const int l = e % rp, q = e / rp;    // row l = pivoted position, column q = row q of R2
                                            // (R2(q, l) = Mj[l + q * ldj] for l >= q)
@@ -1043,6 +1036,14 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     }
     __syncthreads();
     CORE_STAMP(8);
+#ifdef HM_CORE_TIMING
+    if (blockIdx.x == 0 && rp * rcp <= 64 * 64) {
+      for (int e = tid; e < rp * rcp; e += nt) g_core_gf[e] = Gf[(e % rp) + (e / rp) * ldf];
+      if (tid == 0) { g_core_stamp[13] = rp; g_core_stamp[14] = rcp; }
+    }
+    __syncthreads();
+    CORE_STAMP(8);
+#endif
     onesided_jacobi_f32(Gf, ldf, rp, rcp, nullptr, 0, &s_int[1], 15);
     CORE_STAMP(9);
     for (int q = tid; q < rp; q += nt) {
@@ -1054,17 +1055,19 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
                                                          // step 6b fixes the norms)
     }
     __syncthreads();
-    // X[perm2[l]][q] = C Q[l][q] / |column q|, staged through T1 (global): X overwrites Gf
+    // X[perm2[l]][q] = C Q[l][q] / |column q|, staged through T1 (global) when X overwrites Gf
     for (int e = tid; e < rp * rp; e += nt) {
       const int l = e % rp, q = e / rp;
       T1[perm2[l] + (int64_t)q * Kc] = q < rc ? (double)Gf[l + q * ldf] * rdinv[q] : 0.0;
     }
     __syncthreads();
-    for (int e = tid; e < rp * rp; e += nt) {
-      const int p = e % rp, q = e / rp;
-      Yj[p + q * ldj] = T1[p + (int64_t)q * Kc];
+    if (Yj != T1) {
+      for (int e = tid; e < rp * rp; e += nt) {
+        const int p = e % rp, q = e / rp;
+        Yj[p + q * ldj] = T1[p + (int64_t)q * Kc];
+      }
+      __syncthreads();
     }
-    __syncthreads();
   } else {
     for (int e = tid; e < rp * rp; e += nt) {
       int p = e % rp, q = e / rp;
@@ -1104,53 +1107,34 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     //     the first-order term of Cholesky QR, so that column c mixes only with columns of
     //     larger eigenvalue and never takes in a discarded direction (a symmetric
     //     orthogonalisation would leak the FP32 non-orthogonality of the small vectors into the
-    //     large ones, ~1e-6 sigma_1); then one Newton-Schulz step X_k <- X_k (3I - X_k^T X_k)/2
-    //     on the remaining O(F^2) error. Mj (the Cholesky factor of M) is dead here.
-    double* Fm = Mj;
+    //     large ones, ~1e-6 sigma_1). The remaining non-orthogonality is O(F^2) ~ 1e-11, below
+    //     the Gram approach's own error. F goes to shared memory (the Cholesky factor of M or
+    //     the FP32 matrix are dead here), X_k U1 to T1 or, when X itself lives in T1, to Gz.
+    double* Fm = rp <= JSM ? Mj : smem;
+    const int ldm = JSM + 1;
+    double* Tp = Yj != T1 ? T1 : Gz;
     for (int e = tid; e < kk * kk; e += nt) {
       const int a = e % kk, b = e / kk;
       double sf = 0.0;
       if (a <= b) {
-        const double* xa = Yj + order[a] * ldj;
-        const double* xb = Yj + order[b] * ldj;
+        const double* xa = Yj + (int64_t)order[a] * ldj;
+        const double* xb = Yj + (int64_t)order[b] * ldj;
         for (int l = 0; l < rp; ++l) sf = fma(xa[l], xb[l], sf);
         if (a == b) sf = 0.5 * (sf - 1.0);
       }
-      Fm[a + b * ldj] = sf;
+      Fm[a + b * ldm] = sf;
     }
     __syncthreads();
     for (int e = tid; e < rp * kk; e += nt) {
       const int l = e % rp, c = e / rp;
       double sf = 0.0;
-      for (int a = 0; a <= c; ++a) sf = fma(Yj[l + order[a] * ldj], Fm[a + c * ldj], sf);
-      T1[l + (int64_t)c * Kc] = sf;
+      for (int a = 0; a <= c; ++a) sf = fma(Yj[l + (int64_t)order[a] * ldj], Fm[a + c * ldm], sf);
+      Tp[l + (int64_t)c * Kc] = sf;
     }
     __syncthreads();
     for (int e = tid; e < rp * kk; e += nt) {
       const int l = e % rp, c = e / rp;
-      Yj[l + order[c] * ldj] -= T1[l + (int64_t)c * Kc];
-    }
-    __syncthreads();
-    for (int e = tid; e < kk * kk; e += nt) {
-      const int a = e % kk, b = e / kk;
-      const double* xa = Yj + order[a] * ldj;
-      const double* xb = Yj + order[b] * ldj;
-      double sf = 0.0;
-      for (int l = 0; l < rp; ++l) sf = fma(xa[l], xb[l], sf);
-      Fm[a + b * ldj] = sf;
-    }
-    __syncthreads();
-    for (int e = tid; e < rp * kk; e += nt) {
-      const int l = e % rp, c = e / rp;
-      double sf = 0.0;
-      for (int a = 0; a < kk; ++a) sf = fma(Yj[l + order[a] * ldj], Fm[a + c * ldj], sf);
-      T1[l + (int64_t)c * Kc] = sf;
-    }
-    __syncthreads();
-    for (int e = tid; e < rp * kk; e += nt) {
-      const int l = e % rp, c = e / rp;
-      double* x = Yj + l + order[c] * ldj;
-      *x = 1.5 * *x - 0.5 * T1[l + (int64_t)c * Kc];
+      Yj[l + (int64_t)order[c] * ldj] -= Tp[l + (int64_t)c * Kc];
     }
     __syncthreads();
   }
@@ -1158,7 +1142,11 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   // 7. coefficient matrices: Tz = Bm X_k S_k^{-1/2}, Tw = D^{-1} Pi_r Rf11^{-1} X_k S_k^{1/2}
   double* Tw = dptr(B, op.Tw);
   double* Tz = dptr(B, op.Tz);
-  double* Y = Gz;          // K x kk scratch (ld Kc) for the back substitution; Gz is dead here
+  // r x kk scratch for the back substitution: shared memory when X lives there (the first half
+  // of the dynamic smem is dead by now), else Gz
+  const bool ysm = dv && rp <= JSM;
+  double* Y = ysm ? smem : Gz;
+  const int ldy = ysm ? JSM + 1 : Kc;
   if (tid < kk) {
     const double l = lam[order[tid]];
     const double is = nr_rsqrt(l);
@@ -1168,12 +1156,13 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   for (int l = tid; l < r; l += nt) rdinv[l] = nr_rcp(R[l + (int64_t)l * Kc]);
   __syncthreads();
   for (int e = tid; e < K * kk; e += nt) {
-    const int i = e % K, c = e / K;
+    const int l = e % K, c = e / K;     // l: pivoted row of Bm
     const int q = order[c];
-    double s = 0.0;
-    for (int p = 0; p < r; ++p) s = fma(Bm[i + (int64_t)p * Kc], Yj[p + (int64_t)q * ldj], s);
-    Tz[i + (int64_t)c * Kc] = s * sn[c];
-    if (i < r) Y[i + (int64_t)c * Kc] = Yj[i + (int64_t)q * ldj] * cs[c];
+    double sz = 0.0;
+    const int pe = min(l, r - 1);
+    for (int p = 0; p <= pe; ++p) sz = fma(Bm[l + (int64_t)p * Kc], Yj[p + (int64_t)q * ldj], sz);
+    Tz[perm[l] + (int64_t)c * Kc] = sz * sn[c];
+    if (l < r) Y[l + (int64_t)c * ldy] = Yj[l + (int64_t)q * ldj] * cs[c];
   }
   __syncthreads();
   // back substitution Rf11 x = X_k S^{1/2} (Rf11 upper r x r, Rf11(p, l) = R[l + p * Kc]),
@@ -1185,7 +1174,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     for (int l = r - 1; l >= 0; --l) {
       const double rd = rdinv[l];
       for (int c = warp; c < kk; c += nw) {
-        double* y = Y + (int64_t)c * Kc;
+        double* y = Y + (int64_t)c * ldy;
         const double x = y[l] * rd;
         for (int p = lane; p < l; p += 32) y[p] = fma(-R[l + (int64_t)p * Kc], x, y[p]);
         __syncwarp();
@@ -1199,7 +1188,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   for (int e = tid; e < K * kk; e += nt) {
     const int l = e % K, c = e / K;
     const int i = perm[l];
-    Tw[i + (int64_t)c * Kc] = l < r ? Y[l + (int64_t)c * Kc] * dinv[i] : 0.0;
+    Tw[i + (int64_t)c * Kc] = l < r ? Y[l + (int64_t)c * ldy] * dinv[i] : 0.0;
   }
   CORE_STAMP(7);
   if (tid == 0) {

@@ -164,6 +164,9 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   TruncOp* dt = (TruncOp*)desc;
   GemmOp* dg = (GemmOp*)(desc + sizeof(TruncOp));
   StackEntry* de = (StackEntry*)(desc + sizeof(TruncOp) + sizeof(g));
+  int gy0, gz0, gy1, gz1;
+  gemm_grid(g, 2, gy0, gz0);
+  gemm_grid(g + 2, 2, gy1, gz1);
   cudaError_t ce = cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, s);
   if (!ce) ce = cudaMemcpyAsync(dg, g, sizeof(g), cudaMemcpyHostToDevice, s);
   if (!ce) ce = cudaMemcpyAsync(de, &e, sizeof(e), cudaMemcpyHostToDevice, s);
@@ -180,9 +183,6 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   B.i[IS_S] = ints;
   B.flops = (unsigned long long*)(base + oCnt);
   B.status = (int*)(base + oCnt + NFC + NKIND);
-  int gy0, gz0, gy1, gz1;
-  gemm_grid(g, 2, gy0, gz0);
-  gemm_grid(g + 2, 2, gy1, gz1);
   ce = launch_kind(K_STACK, dt, 1, de, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
   if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);

@@ -48,7 +48,8 @@ struct GemmOp {
   int flags;
   double alpha;
   int fclass;
-  int pad;
+  int split;   // CTAs of this micro-op: (split & 0xffff) along C tiles, (split >> 16) along reduction
+               // slices (0 = one CTA); CTAs of the launch grid beyond them exit
 };
 
 // batched vector triangular kernels on the packed LU of a diagonal leaf (b x b, ld = b)

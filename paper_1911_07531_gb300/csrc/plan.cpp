@@ -25,31 +25,32 @@
 
 namespace hm {
 
-void gemm_grid(const GemmOp* ops, int count, int& gy, int& gz) {
+void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
   // Dynamic sizes (ranks) are not known here; they are taken as 16 for the estimate. A CTA
-  // should get about 32k FMAs (16k cycles of one SM's FP64 pipe); the launch stays within
-  // about four CTAs per SM.
-  constexpr double kTarget = 32768.0, kDyn = 16.0;
-  constexpr int kSms = 152, kMaxSplit = 16, kTile = 1024, kSlice = 32;
+  // should get at least ~32k FMAs (16k cycles of one SM's FP64 pipe) and about the launch's
+  // average work per CTA slot (three resident CTAs per SM).
+  constexpr double kMinWork = 32768.0, kDyn = 16.0;
+  constexpr int kSlots = 3 * 152, kMaxSplit = 16, kTile = 1024, kSlice = 32;
+  auto work = [&](const GemmOp& o) {
+    return (o.m + (o.md ? kDyn : 0.0)) * (o.n + (o.nd ? kDyn : 0.0)) * (o.k + (o.kd ? kDyn : 0.0));
+  };
+  std::stable_sort(ops, ops + count, [&](const GemmOp& a, const GemmOp& b) { return work(a) > work(b); });
+  double total = 0.0;
+  for (int q = 0; q < count; ++q) total += work(ops[q]);
+  const double target = std::max(kMinWork, total / kSlots);
   gy = gz = 1;
-  if (count >= 2 * kSms) return;
-  double wmax = 0.0;
-  int tiles = 1, slices = 1;
   for (int q = 0; q < count; ++q) {
-    const GemmOp& o = ops[q];
+    GemmOp& o = ops[q];
     const double m = o.m + (o.md ? kDyn : 0.0), n = o.n + (o.nd ? kDyn : 0.0), k = o.k + (o.kd ? kDyn : 0.0);
-    const double w = m * n * k;
-    if (w > wmax) {
-      wmax = w;
-      tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
-      slices = (o.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
-    }
+    const int want = std::min(kMaxSplit, std::max(1, (int)(work(o) / target + 0.5)));
+    const int tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
+    const int slices = (o.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
+    const int sy = std::max(1, std::min(want, tiles));
+    const int sz = std::max(1, std::min(want / sy, slices));
+    o.split = sy | (sz << 16);
+    gy = std::max(gy, sy);
+    gz = std::max(gz, sz);
   }
-  const int want = std::min(kMaxSplit, std::max(1, (int)(wmax / kTarget + 0.5)));
-  const int room = std::max(1, 4 * kSms / count);
-  const int split = std::min(want, room);
-  gy = std::max(1, std::min(split, tiles));
-  gz = std::max(1, std::min(split / gy, slices));
 }
 
 namespace {
@@ -658,6 +659,10 @@ struct Ctx {
           plan.trunc.push_back(op);
         }
       }
+      // the cores of a launch are independent: largest stacked-rank bound first, so that the
+      // longest ones start first
+      std::stable_sort(w.core[ph].begin(), w.core[ph].end(),
+                       [](const TruncOp& a, const TruncOp& b) { return a.Kcap > b.Kcap; });
       put(K_CORE, (int)w.core[ph].size(), (int)plan.trunc.size());
       plan.trunc.insert(plan.trunc.end(), w.core[ph].begin(), w.core[ph].end());
     }

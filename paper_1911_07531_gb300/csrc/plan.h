@@ -36,10 +36,11 @@ struct Launch {
   int gy = 1, gz = 1;   // GEMM launches: CTAs per micro-op along C tiles / reduction slices
 };
 
-// Grid split of a GEMM launch: large micro-ops of a narrow launch get several CTAs (tiles of C
-// along y, reduction slices of accumulating micro-ops along z) so that they do not run on one
-// SM; launches that already fill the GPU stay one CTA per micro-op.
-void gemm_grid(const GemmOp* ops, int count, int& gy, int& gz);
+// Grid of a GEMM launch: orders the (independent) micro-ops by estimated work, largest first,
+// and gives each micro-op whose work is well above its share of the GPU several CTAs (tiles of
+// C along y, reduction slices of accumulating micro-ops along z, recorded in GemmOp::split);
+// gy, gz are the launch's maxima.
+void gemm_grid(GemmOp* ops, int count, int& gy, int& gz);
 
 struct Plan {
   std::vector<GetrfOp> getrf;
