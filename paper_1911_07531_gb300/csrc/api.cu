@@ -945,6 +945,7 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   }
   if (!dalloc(c, ops, sizeof(t) + sizeof(g)) || !dalloc(c, ent, sizeof(e)))
     return done(fail(HM_ENOMEM, "hm_truncate: allocator returned NULL"));
+  for (int q = 0; q < 4; ++q) g[q].split = (int)Kc;   // expected stacked rank, for the grid split
   int gy0, gz0, gy1, gz1;
   gemm_grid(g, 2, gy0, gz0);
   gemm_grid(g + 2, 2, gy1, gz1);

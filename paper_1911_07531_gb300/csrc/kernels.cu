@@ -166,13 +166,16 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
   if (m <= 0 || n <= 0) return;
   if (k == 0 && !overwrite) return;
   const int nslices = (k + GKS - 1) / GKS;
-  const int sy = max(1, op.split & 0xffff), sz = atomic ? max(1, op.split >> 16) : 1;
-  if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;
-  const int z0 = blockIdx.z, zs = sz;
-  if (z0 > 0 && z0 >= nslices) return;
   int mt, nt, nrt, nct;
   gemm_tile_shape(m, n, mt, nt, nrt, nct);
-  if ((int)blockIdx.y >= nrt * nct) return;
+  // split actually used: the planner's bound, lowered to ~32k FMAs per CTA for the real sizes
+  const int symax = max(1, op.split & 0xffff), szmax = atomic ? max(1, op.split >> 16) : 1;
+  const double work = (double)m * n * max(k, 1);
+  const int want = min(symax * szmax, max(1, (int)ceil(work * (1.0 / 32768.0))));
+  const int sy = min(min(want, symax), nrt * nct);
+  const int sz = min(min((want + sy - 1) / sy, szmax), max(nslices, 1));
+  if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;
+  const int z0 = blockIdx.z, zs = sz;
   extern __shared__ double gsm[];
   double* As = gsm;                         // [GKS][GTM + 1]
   double* Bs = gsm + GKS * (GTM + 1);       // [GKS][GTM + 1]

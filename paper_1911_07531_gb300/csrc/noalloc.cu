@@ -164,6 +164,7 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   TruncOp* dt = (TruncOp*)desc;
   GemmOp* dg = (GemmOp*)(desc + sizeof(TruncOp));
   StackEntry* de = (StackEntry*)(desc + sizeof(TruncOp) + sizeof(g));
+  for (int q = 0; q < 4; ++q) g[q].split = (int)Kc;   // expected stacked rank, for the grid split
   int gy0, gz0, gy1, gz1;
   gemm_grid(g, 2, gy0, gz0);
   gemm_grid(g + 2, 2, gy1, gz1);

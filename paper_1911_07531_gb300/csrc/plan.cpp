@@ -19,6 +19,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <stdexcept>
@@ -26,31 +27,47 @@
 namespace hm {
 
 void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
-  // Dynamic sizes (ranks) are not known here; they are taken as 16 for the estimate. A CTA
-  // should get at least ~32k FMAs (16k cycles of one SM's FP64 pipe) and about the launch's
-  // average work per CTA slot (three resident CTAs per SM).
-  constexpr double kMinWork = 32768.0, kDyn = 16.0;
+  // Dynamic sizes (ranks) are not known here: each micro-op carries an expected value in
+  // `split` (0: 16). A CTA should get at least ~32k FMAs (16k cycles of one SM's FP64 pipe) and
+  // about the launch's average work per CTA slot (three resident CTAs per SM). The split stored
+  // is an upper bound; the kernel lowers it from the actual sizes.
+  constexpr double kMinWork = 32768.0;
   constexpr int kSlots = 3 * 152, kMaxSplit = 16, kTile = 1024, kSlice = 32;
-  auto work = [&](const GemmOp& o) {
-    return (o.m + (o.md ? kDyn : 0.0)) * (o.n + (o.nd ? kDyn : 0.0)) * (o.k + (o.kd ? kDyn : 0.0));
+  std::vector<double> w(count);
+  std::vector<int> idx(count);
+  auto dims = [](const GemmOp& o, double& m, double& n, double& k) {
+    const double dyn = o.split > 0 ? (double)o.split : 16.0;
+    m = o.m + (o.md ? dyn : 0.0);
+    n = o.n + (o.nd ? dyn : 0.0);
+    k = o.k + (o.kd ? dyn : 0.0);
   };
-  std::stable_sort(ops, ops + count, [&](const GemmOp& a, const GemmOp& b) { return work(a) > work(b); });
   double total = 0.0;
-  for (int q = 0; q < count; ++q) total += work(ops[q]);
-  const double target = std::max(kMinWork, total / kSlots);
-  gy = gz = 1;
   for (int q = 0; q < count; ++q) {
-    GemmOp& o = ops[q];
-    const double m = o.m + (o.md ? kDyn : 0.0), n = o.n + (o.nd ? kDyn : 0.0), k = o.k + (o.kd ? kDyn : 0.0);
-    const int want = std::min(kMaxSplit, std::max(1, (int)(work(o) / target + 0.5)));
+    double m, n, k;
+    dims(ops[q], m, n, k);
+    w[q] = m * n * k;
+    total += w[q];
+    idx[q] = q;
+  }
+  const double target = std::max(kMinWork, total / kSlots);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
+  std::vector<GemmOp> sorted(count);
+  gy = gz = 1;
+  for (int t = 0; t < count; ++t) {
+    GemmOp o = ops[idx[t]];
+    double m, n, k;
+    dims(o, m, n, k);
+    const int want = std::min(kMaxSplit, std::max(1, (int)std::ceil(w[idx[t]] / target)));
     const int tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
     const int slices = (o.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
     const int sy = std::max(1, std::min(want, tiles));
-    const int sz = std::max(1, std::min(want / sy, slices));
+    const int sz = std::max(1, std::min((want + sy - 1) / sy, slices));
     o.split = sy | (sz << 16);
     gy = std::max(gy, sy);
     gz = std::max(gz, sz);
+    sorted[t] = o;
   }
+  std::copy(sorted.begin(), sorted.end(), ops);
 }
 
 namespace {
@@ -149,8 +166,9 @@ struct Ctx {
   uint64_t sref(int64_t off) const { return mkref(SP_S, off); }
 
   // ---------------------------------------------------------------- micro-op emitters
+  // dhint: expected value of the dynamic sizes (a rank or a stacked rank), for the grid split
   void gemm(int ph, uint64_t A, int64_t ars, int64_t acs, uint64_t B, int64_t brs, int64_t bcs, uint64_t C,
-            int64_t crs, int64_t ccs, Dim m, Dim n, Dim k, double alpha, int flags, int fclass) {
+            int64_t crs, int64_t ccs, Dim m, Dim n, Dim k, double alpha, int flags, int fclass, int dhint = 0) {
     w.need(ph);
     // split static rows (always legal) and, for accumulating outputs, the static reduction
     int mstep = (m.d || m.s <= GEMM_MCHUNK) ? std::max(m.s, 1) : GEMM_MCHUNK;
@@ -180,6 +198,7 @@ struct Ctx {
         g.flags = flags;
         g.alpha = alpha;
         g.fclass = fclass;
+        g.split = dhint;   // host-side hint until gemm_grid sets the split
         w.gemm[ph].push_back(g);
         if (k.d) break;
       }
@@ -609,17 +628,17 @@ struct Ctx {
         for (int i0 = 0; i0 < L.m; i0 += GEMM_KCHUNK) {
           int mi = std::min(GEMM_KCHUNK, L.m - i0);
           gemm(ph + 1, op.Wst + (uint64_t)i0, L.m, 1, op.Wst + (uint64_t)i0, 1, L.m, op.Gw, 1, Kc, Kd, Kd,
-               {mi, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE);
+               {mi, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE, Kc);
         }
         for (int i0 = 0; i0 < L.n; i0 += GEMM_KCHUNK) {
           int ni = std::min(GEMM_KCHUNK, L.n - i0);
           gemm(ph + 1, op.Zst + (uint64_t)i0, L.n, 1, op.Zst + (uint64_t)i0, 1, L.n, op.Gz, 1, Kc, Kd, Kd,
-               {ni, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE);
+               {ni, 0}, 1.0, GF_ATOMIC | GF_SYM_UPPER, FC_NONE, Kc);
         }
         w.core[ph + 2].push_back(op);
         const Dim rk{0, op.rank};
-        gemm(ph + 3, op.Wst, 1, L.m, op.Tw, 1, Kc, op.U, 1, L.m, {L.m, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
-        gemm(ph + 3, op.Zst, 1, L.n, op.Tz, 1, Kc, op.V, 1, L.n, {L.n, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE);
+        gemm(ph + 3, op.Wst, 1, L.m, op.Tw, 1, Kc, op.U, 1, L.m, {L.m, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE, Kc);
+        gemm(ph + 3, op.Zst, 1, L.n, op.Tz, 1, Kc, op.V, 1, L.n, {L.n, 0}, rk, Kd, 1.0, GF_OVERWRITE, FC_NONE, Kc);
         plan.ntrunc++;
       }
       if (opened) ++batch;
