@@ -32,6 +32,12 @@ import numpy as np  # noqa: E402
 import hm_workloads as W  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# DRAM bytes (read + write) per counted FLOP of a launch, from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum) of one H-LU step of the n = 32768 sphere: the largest k_gemm launch
+# (8906 micro-ops: 406.3 MB + 20.2 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 269.1 kB for
+# 9.0379 MFLOP). A launch's traffic is taken as this ratio times its FLOPs.
+PROFILED_BYTES_PER_FLOP = {"gemm": (406.298112e6 + 20.151552e6) / 2231684434.0,
+                           "core": 269056.0 / 9037896.0}
 KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 WORKLOAD_TEXT = {
     "cube131072": "n=131072 uniform on the unit-cube surface, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
@@ -200,6 +206,8 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        # NVTX range around the timed steps: ncu --nvtx --nvtx-include "hlu_timed/" captures them
+        torch.cuda.nvtx.range_push("hlu_timed")
         for _ in range(args.steps):
             s0 = torch.cuda.Event(enable_timing=True)
             s1 = torch.cuda.Event(enable_timing=True)
@@ -214,6 +222,7 @@ def main():
             if last is not None:
                 last.free()
             last = F
+        torch.cuda.nvtx.range_pop()
         e1.record(stream)
         barrier()
         wall = time.perf_counter() - t_wall0
@@ -240,8 +249,13 @@ def main():
     kind_n = dict(zip(KINDS, ps["kind_launches"]))
     dom = max(KINDS, key=lambda k: kind_ms[k])
     achieved = kind_fl[dom] / (kind_ms[dom] * 1e-3) * 1e-9 if kind_ms[dom] > 0 else 0.0
+    traffic = None
+    if dom in PROFILED_BYTES_PER_FLOP and kind_n[dom] > 0:
+        traffic = PROFILED_BYTES_PER_FLOP[dom] * kind_fl[dom] / kind_n[dom]
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "traffic_basis": "bytes per launch: ncu DRAM bytes/FLOP of a captured launch (n = 32768 "
+                                 "sphere) x this kernel's average FLOPs per launch",
                 "peak_basis": "derived FP64 DFMA peak: 152 SM x 2 FMA/clk x 2 x 2.07 GHz",
                 "launches_per_step": kind_n[dom],
                 "share": kind_ms[dom] / max(sum(kind_ms.values()), 1e-9),
