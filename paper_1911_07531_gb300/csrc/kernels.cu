@@ -113,6 +113,40 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
   return ldexp(y, -e / 2);
 }
 
+// Reciprocal of x in [1e-30, 1e30] to full FP64 accuracy with three dependent FP64 operations:
+// r0 = 1/x from the FP32 approximate reciprocal (the FP32 operand and the FP64 seed are formed
+// by integer moves of the exponent and the leading mantissa bits, not by conversion
+// instructions), e = 1 - x r0 (|e| < 2^-21), 1/x = r0 (1 + e + e^2 + ...); the truncated series
+// leaves r0 e^3 ~ 2^-63 r0.
+// GB300 spends ~64 cycles on each dependent FP64 operation, so this is for serial sections.
+__device__ __forceinline__ double fast_rcp(double x) {
+  constexpr long long kBias = (long long)(1023 - 127) << 23;   // exponent rebias, FP32 bit position
+  const long long xb = __double_as_longlong(x);
+  const float xf = __int_as_float((int)((xb >> 29) - kBias));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));   // ~1 ulp; the series absorbs it
+  const double r0 = __longlong_as_double(((long long)__float_as_int(rf) + kBias) << 29);
+  const double e = fma(-x, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
+}
+
+// Total order of doubles as signed 64-bit integers (negative values have their magnitude bits
+// flipped): comparisons on the integer pipe instead of ~64-cycle FP64 compares.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+
+// Pivot key of a diagonal entry at position i (< 256): the high word of a positive double
+// (sign, exponent, 20 mantissa bits) with its low 8 bits replaced by 255 - i, so that an
+// unsigned max picks the largest entry to ~2^-12 relative and the lowest index among near
+// ties; 0 for entries <= 0.
+__device__ __forceinline__ unsigned pivot_key(double v, int i) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 ? (((unsigned)(b >> 32)) & ~255u) | (unsigned)(255 - i) : 0u;
+}
+
+
 // ------------------------------------------------------------------------------ GEMM
 // GEMM micro-ops are thin (a rank-sized side of 10-60) or have a small output with a long
 // reduction (Gram matrices). GB300 executes ~2 FP64 FMAs per clock per SM while shared memory
@@ -125,6 +159,7 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
 // steps of both operands is staged in shared memory per pass. Tiles of one micro-op are spread
 // over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z
 // (per micro-op counts in GemmOp::split), so that a large micro-op does not sit on one SM.
+constexpr int KMAX_ENTRIES = 256;   // largest number of pieces of one rounded addition (planner)
 constexpr int GE = 1024;      // largest C tile (elements)
 constexpr int GTM = 128;      // largest C tile side
 constexpr int GKS = 32;       // staged reduction slice
@@ -300,13 +335,18 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
 }
 
 // ------------------------------------------------------------------------------ TRSM
+// Triangular solves / multiplies of a diagonal leaf's packed LU on many vectors. CTA (op, y)
+// takes the chunks of 32 vectors y, y + Y, ... of the micro-op (CTAs past nv exit); for a chunk
+// of nc vectors, thread t works on vector t % w and rows t / w, t / w + 256 / w, ... with w the
+// next power of two >= nc (no index divisions in the sequential steps).
+constexpr int TRSM_VC = 32;
 __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Bases B) {
   const TrsmOp op = ops[blockIdx.x];
   const int nv = dimv(B, op.nv, op.nvd), b = op.b;
-  if (nv <= 0 || b <= 0) return;
-  extern __shared__ double trsm_smem[];   // T[64][65] then X[64][65]
+  if (nv <= (int)blockIdx.y * TRSM_VC || b <= 0) return;
+  extern __shared__ double trsm_smem[];   // T[64][65] then X[64][33]
   double(*T)[65] = reinterpret_cast<double(*)[65]>(trsm_smem);
-  double(*X)[65] = reinterpret_cast<double(*)[65]>(trsm_smem + 64 * 65);
+  double(*X)[TRSM_VC + 1] = reinterpret_cast<double(*)[TRSM_VC + 1]>(trsm_smem + 64 * 65);
   __shared__ int piv[64];
   __shared__ double dinv[64];
   const int tid = threadIdx.x;
@@ -318,152 +358,210 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
   __syncthreads();
   if (op.mode == TM_UT || op.mode == TM_U)
     for (int e = tid; e < b; e += 256) dinv[e] = nr_rcp(T[e][e]);
-  __syncthreads();
   const bool e_fast = op.x_es == 1;
-  for (int v0 = 0; v0 < nv; v0 += 64) {
-    const int nc = min(64, nv - v0);
-    for (int e = tid; e < b * nc; e += 256) {
-      int ee, v;
-      if (e_fast) { ee = e % b; v = e / b; } else { v = e % nc; ee = e / nc; }
-      X[ee][v] = Xg[(int64_t)ee * op.x_es + (int64_t)(v0 + v) * op.x_vs];
-    }
-    __syncthreads();
-    if (op.mode == TM_L_PIV) {
-      if (tid < nc)
-        for (int i = 0; i < b; ++i) {
-          int p = piv[i];
-          if (p != i) {
-            double t = X[i][tid];
-            X[i][tid] = X[p][tid];
-            X[p][tid] = t;
-          }
-        }
-      __syncthreads();
-      for (int j = 0; j < b - 1; ++j) {
-        int cnt = (b - 1 - j) * nc;
-        for (int e = tid; e < cnt; e += 256) {
-          int i = j + 1 + e / nc, v = e % nc;
-          X[i][v] = fma(-T[i][j], X[j][v], X[i][v]);
-        }
-        __syncthreads();
-      }
-    } else if (op.mode == TM_UT) {
-      for (int j = 0; j < b; ++j) {
-        if (tid < nc) X[j][tid] = X[j][tid] * dinv[j];
-        __syncthreads();
-        int cnt = (b - 1 - j) * nc;
-        for (int e = tid; e < cnt; e += 256) {
-          int i = j + 1 + e / nc, v = e % nc;
-          X[i][v] = fma(-T[j][i], X[j][v], X[i][v]);
-        }
-        __syncthreads();
-      }
-    } else if (op.mode == TM_U) {
-      for (int j = b - 1; j >= 0; --j) {
-        if (tid < nc) X[j][tid] = X[j][tid] * dinv[j];
-        __syncthreads();
-        int cnt = j * nc;
-        for (int e = tid; e < cnt; e += 256) {
-          int i = e / nc, v = e % nc;
-          X[i][v] = fma(-T[i][j], X[j][v], X[i][v]);
-        }
-        __syncthreads();
-      }
+  for (int v0 = blockIdx.y * TRSM_VC; v0 < nv; v0 += gridDim.y * TRSM_VC) {
+  const int nc = min(TRSM_VC, nv - v0);
+  // vector lanes: the next power of two >= nc, the remaining threads spread over the rows
+  int vw = 1;
+  while (vw < nc) vw *= 2;
+  const int v = tid & (vw - 1), g = tid / vw, ng = blockDim.x / vw;
+  for (int e = tid; e < b * nc; e += 256) {
+    int ee, vv;
+    if (e_fast) {
+      ee = e % b;
+      vv = e / b;
     } else {
-      // multiplies: each thread keeps its results in registers until all reads are done
-      double y[16];
-      int cnt = b * nc;
-      int q = 0;
-      for (int e = tid; e < cnt; e += 256, ++q) {
-        int i = e / nc, v = e % nc;
-        double s = 0.0;
-        if (op.mode == TM_MUL_U) {
-          for (int j = i; j < b; ++j) s = fma(T[i][j], X[j][v], s);
-        } else {
-          s = X[i][v];
-          for (int j = 0; j < i; ++j) s = fma(T[i][j], X[j][v], s);
+      vv = e % nc;
+      ee = e / nc;
+    }
+    X[ee][vv] = Xg[(int64_t)ee * op.x_es + (int64_t)(v0 + vv) * op.x_vs];
+  }
+  __syncthreads();
+  const bool act = v < nc;
+  if (op.mode == TM_L_PIV) {
+    if (tid < nc)
+      for (int i = 0; i < b; ++i) {
+        const int p = piv[i];
+        if (p != i) {
+          const double t = X[i][tid];
+          X[i][tid] = X[p][tid];
+          X[p][tid] = t;
         }
-        y[q] = s;
+      }
+    __syncthreads();
+    for (int j = 0; j < b - 1; ++j) {
+      if (act) {
+        const double xj = X[j][v];
+        for (int i = j + 1 + g; i < b; i += ng) X[i][v] = fma(-T[i][j], xj, X[i][v]);
       }
       __syncthreads();
-      q = 0;
-      for (int e = tid; e < cnt; e += 256, ++q) X[e / nc][e % nc] = y[q];
-      __syncthreads();
-      if (op.mode == TM_MUL_PL && tid < nc)
-        for (int i = b - 1; i >= 0; --i) {
-          int p = piv[i];
-          if (p != i) {
-            double t = X[i][tid];
-            X[i][tid] = X[p][tid];
-            X[p][tid] = t;
-          }
-        }
+    }
+  } else if (op.mode == TM_UT || op.mode == TM_U) {
+    // every thread of vector v scales its own copy of x_j; thread group 0 stores it one step
+    // later, after the barrier that ends the step's reads of the unscaled value
+    __syncthreads();
+    const bool up = op.mode == TM_UT;
+    double xprev = 0.0;
+    int jprev = -1;
+    for (int s = 0; s < b; ++s) {
+      const int j = up ? s : b - 1 - s;
+      if (act) {
+        if (g == 0 && jprev >= 0) X[jprev][v] = xprev;
+        const double xj = X[j][v] * dinv[j];
+        if (up)
+          for (int i = j + 1 + g; i < b; i += ng) X[i][v] = fma(-T[j][i], xj, X[i][v]);
+        else
+          for (int i = g; i < j; i += ng) X[i][v] = fma(-T[i][j], xj, X[i][v]);
+        xprev = xj;
+        jprev = j;
+      }
       __syncthreads();
     }
-    for (int e = tid; e < b * nc; e += 256) {
-      int ee, v;
-      if (e_fast) { ee = e % b; v = e / b; } else { v = e % nc; ee = e / nc; }
-      Xg[(int64_t)ee * op.x_es + (int64_t)(v0 + v) * op.x_vs] = X[ee][v];
+    if (act && g == 0 && jprev >= 0) X[jprev][v] = xprev;
+  } else {
+    // multiplies: each thread keeps its results in registers until all reads are done
+    double y[8];   // rows g + q ng, q < 8 (ng >= 8 threads per vector cover b <= 64)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = g + q * ng;
+      double sacc = 0.0;
+      if (act && i < b) {
+        if (op.mode == TM_MUL_U) {
+          for (int j = i; j < b; ++j) sacc = fma(T[i][j], X[j][v], sacc);
+        } else {
+          sacc = X[i][v];
+          for (int j = 0; j < i; ++j) sacc = fma(T[i][j], X[j][v], sacc);
+        }
+      }
+      y[q] = sacc;
     }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = g + q * ng;
+      if (act && i < b) X[i][v] = y[q];
+    }
+    __syncthreads();
+    if (op.mode == TM_MUL_PL && tid < nc)
+      for (int i = b - 1; i >= 0; --i) {
+        const int p = piv[i];
+        if (p != i) {
+          const double t = X[i][tid];
+          X[i][tid] = X[p][tid];
+          X[p][tid] = t;
+        }
+      }
   }
+  __syncthreads();
+  for (int e = tid; e < b * nc; e += 256) {
+    int ee, vv;
+    if (e_fast) {
+      ee = e % b;
+      vv = e / b;
+    } else {
+      vv = e % nc;
+      ee = e / nc;
+    }
+    Xg[(int64_t)ee * op.x_es + (int64_t)(v0 + vv) * op.x_vs] = X[ee][vv];
+  }
+  __syncthreads();
   if (tid == 0) {
-    atomicAdd(&B.flops[FC_TRSM], (unsigned long long)nv * b * b);
-    atomicAdd(&B.flops[NFC + K_TRSM], (unsigned long long)nv * b * b);
+    atomicAdd(&B.flops[FC_TRSM], (unsigned long long)nc * b * b);
+    atomicAdd(&B.flops[NFC + K_TRSM], (unsigned long long)nc * b * b);
+  }
   }
 }
 
 // ------------------------------------------------------------------------------ GETRF
+// Partial-pivoting pivot of column c (rows r..b-1) of S by warp 0: the first row of largest
+// |a| (64-bit compare of the magnitudes' bit patterns, then the lowest row among the maxima),
+// and the reciprocal of the pivot (0 for a zero column, which is counted as singular).
+__device__ __forceinline__ void getrf_select(double (*S)[65], int c, int r, int b, int* piv, int* s_p,
+                                             double* s_dinv, int slot, int* status) {
+  const int lane = threadIdx.x & 31;
+  long long best = -1;
+  int bi = b;
+  for (int i = r + lane; i < b; i += 32) {
+    const long long k = __double_as_longlong(fabs(S[i][c]));
+    if (k > best) {
+      best = k;
+      bi = i;
+    }
+  }
+  long long gmax = best;
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, gmax, o);
+    gmax = ob > gmax ? ob : gmax;
+  }
+  const int p = (int)__reduce_min_sync(0xffffffffu, (unsigned)(best == gmax ? bi : b));
+  if (lane == 0) {
+    const int pp = p < b ? p : r;
+    const double v = S[pp][c];
+    double dinv = 0.0;
+    const long long mag = gmax;                      // bits of |pivot|
+    if (mag <= 0) atomicAdd(&status[0], 1);
+    else if (mag > 0x39b4484bfeebc2a0LL && mag < 0x46293e5939a08ceaLL)   // 1e-30 < |v| < 1e30
+      dinv = copysign(fast_rcp(fabs(v)), v);
+    else
+      dinv = nr_rcp(v);
+    s_p[slot] = pp;
+    s_dinv[slot] = dinv;
+    piv[c] = pp;
+  }
+}
+
+// Dense LU with partial pivoting of a diagonal leaf (b <= 64) in shared memory. Step j: all
+// threads interchange rows j and p_j (columns != j) and scale column j by 1 / pivot; then warp 0
+// updates column j + 1, picks p_{j+1} and forms its reciprocal while warps 1.. apply the rank-one
+// update to columns j + 2.. -- the pivot search of the next step overlaps this step's update.
 __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, Bases B) {
   const GetrfOp op = ops[blockIdx.x];
   const int b = op.b;
   if (b <= 0) return;
   __shared__ double S[64][65];
-  __shared__ int sp;
+  __shared__ int s_p[2];
+  __shared__ double s_dinv[2];
   double* A = dptr(B, op.A);
   int* piv = iptr(B, op.piv);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < b * b; e += 256) S[e % b][e / b] = A[e];
   __syncthreads();
+  if (warp == 0) getrf_select(S, 0, 0, b, piv, s_p, s_dinv, 0, B.status);
+  __syncthreads();
   for (int j = 0; j < b; ++j) {
-    if (tid < 32) {
-      double bv = -1.0;
-      int bi = -1;
-      for (int i = j + tid; i < b; i += 32) {
-        double v = fabs(S[i][j]);
-        if (v > bv) { bv = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
-      }
-      if (tid == 0) {
-        sp = bi;
-        piv[j] = bi;
-      }
-    }
-    __syncthreads();
-    const int p = sp;
-    if (p != j)
-      for (int c = tid; c < b; c += 256) {
-        double t = S[j][c];
+    const int slot = j & 1;
+    const int p = s_p[slot];
+    const double dinv = s_dinv[slot];
+    if (tid < b) {
+      const int c = tid;
+      if (c != j && p != j) {
+        const double t = S[j][c];
         S[j][c] = S[p][c];
         S[p][c] = t;
       }
-    __syncthreads();
-    const double d = S[j][j];
-    if (d == 0.0) {
-      if (tid == 0) atomicAdd(&B.status[0], 1);
-    } else {
-      const double dinv = nr_rcp(d);
-      for (int i = j + 1 + tid; i < b; i += 256) S[i][j] = S[i][j] * dinv;
+    } else if (tid >= 64 && tid < 64 + b) {
+      const int i = tid - 64;
+      if (i == j) {
+        const double a = S[j][j], pv = S[p][j];
+        S[j][j] = pv;
+        if (p != j) S[p][j] = a * dinv;
+      } else if (i > j && i != p) {
+        S[i][j] *= dinv;
+      }
     }
     __syncthreads();
-    const int r = b - 1 - j;
-    for (int e = tid; e < r * r; e += 256) {
-      int i = j + 1 + e % r, c = j + 1 + e / r;
-      S[i][c] = fma(-S[i][j], S[j][c], S[i][c]);
+    if (j + 1 < b) {
+      if (warp == 0) {
+        const double u = S[j][j + 1];
+        for (int i = j + 1 + lane; i < b; i += 32) S[i][j + 1] = fma(-S[i][j], u, S[i][j + 1]);
+        __syncwarp();
+        getrf_select(S, j + 1, j + 1, b, piv, s_p, s_dinv, slot ^ 1, B.status);
+      } else {
+        for (int c = j + 2 + warp - 1; c < b; c += nw - 1) {
+          const double u = S[j][c];
+          for (int i = j + 1 + lane; i < b; i += 32) S[i][c] = fma(-S[i][j], u, S[i][c]);
+        }
+      }
     }
     __syncthreads();
   }
@@ -499,61 +597,84 @@ __global__ void __launch_bounds__(256) k_copy(const CopyOp* __restrict__ ops, Ba
 // ------------------------------------------------------------------------------ STACK
 __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
                                                const StackEntry* __restrict__ ent, Bases B) {
+  // CTA (op, y) copies rows [y m / Y, (y + 1) m / Y) of the stacked left factor and the same
+  // share of the right factor's rows; every CTA derives the column layout itself, CTA y = 0 also
+  // publishes the stacked rank and clears the Gram matrices.
   const TruncOp op = ops[blockIdx.x];
-  const int m = op.m, n = op.n, Kc = op.Kcap;
-  int* rk = iptr(B, op.rank);
-  const int kself = *rk;
-  __shared__ int s_k[1];
-  if (threadIdx.x == 0) {
-    int K = kself;
-    for (int e = 0; e < op.n_entries; ++e) {
-      const StackEntry& se = ent[op.first_entry + e];
-      int ke = dimv(B, se.k, se.kd);
-      if (ke < 0) ke = 0;
-      K += ke;
-    }
-    if (K > Kc) K = Kc;   // the planner sizes Kcap from static maxima; never taken
-    s_k[0] = K;
-    *iptr(B, op.Kd) = K;
+  const int m = op.m, n = op.n, Kc = op.Kcap, tid = threadIdx.x;
+  const int kself = *iptr(B, op.rank);
+  const int ne = min(op.n_entries, KMAX_ENTRIES);
+  __shared__ int s_ke[KMAX_ENTRIES], s_col[KMAX_ENTRIES], s_K;
+  for (int e = tid; e < ne; e += blockDim.x) {
+    const StackEntry& se = ent[op.first_entry + e];
+    s_ke[e] = max(dimv(B, se.k, se.kd), 0);
   }
   __syncthreads();
-  const int K = s_k[0];
+  if (tid == 0) {
+    int K = kself;
+    for (int e = 0; e < ne; ++e) K += s_ke[e];
+    if (K > Kc) K = Kc;   // the planner sizes Kcap from static maxima; never taken
+    int col = min(kself, K);
+    for (int e = 0; e < ne; ++e) {
+      const int ke = max(0, min(s_ke[e], K - col));
+      s_col[e] = col;
+      s_ke[e] = ke;
+      col += ke;
+    }
+    s_K = K;
+    if (blockIdx.y == 0) *iptr(B, op.Kd) = K;
+  }
+  __syncthreads();
+  const int K = s_K;
   double* Wst = dptr(B, op.Wst);
   double* Zst = dptr(B, op.Zst);
-  double* Gw = dptr(B, op.Gw);
-  double* Gz = dptr(B, op.Gz);
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    int i = e % K, j = e / K;
-    Gw[i + (int64_t)j * Kc] = 0.0;
-    Gz[i + (int64_t)j * Kc] = 0.0;
+  if (blockIdx.y == 0) {
+    double* Gw = dptr(B, op.Gw);
+    double* Gz = dptr(B, op.Gz);
+    for (int e = tid; e < K * K; e += blockDim.x) {
+      const int i = e % K, j = e / K;
+      Gw[i + (int64_t)j * Kc] = 0.0;
+      Gz[i + (int64_t)j * Kc] = 0.0;
+    }
   }
+  const int ny = gridDim.y, y = blockIdx.y;
+  const int w0 = (int)((int64_t)m * y / ny), wl = (int)((int64_t)m * (y + 1) / ny) - w0;
+  const int z0 = (int)((int64_t)n * y / ny), zl = (int)((int64_t)n * (y + 1) / ny) - z0;
   const double* U = dptr(B, op.U);
   const double* V = dptr(B, op.V);
-  int col = min(kself, K);
-  for (int64_t e = threadIdx.x; e < (int64_t)m * col; e += blockDim.x) Wst[e] = U[e];
-  for (int64_t e = threadIdx.x; e < (int64_t)n * col; e += blockDim.x) Zst[e] = V[e];
-  for (int q = 0; q < op.n_entries && col < K; ++q) {
-    const StackEntry se = ent[op.first_entry + q];
-    int ke = dimv(B, se.k, se.kd);
-    if (ke > K - col) ke = K - col;
+  const int cself = min(kself, K);
+  if (wl > 0)
+    for (int e = tid; e < wl * cself; e += blockDim.x) {
+      const int i = w0 + e % wl, c = e / wl;
+      Wst[(int64_t)c * m + i] = U[(int64_t)c * m + i];
+    }
+  if (zl > 0)
+    for (int e = tid; e < zl * cself; e += blockDim.x) {
+      const int j = z0 + e % zl, c = e / zl;
+      Zst[(int64_t)c * n + j] = V[(int64_t)c * n + j];
+    }
+  for (int q = 0; q < ne; ++q) {
+    const int ke = s_ke[q], col = s_col[q];
     if (ke <= 0) continue;
+    const StackEntry se = ent[op.first_entry + q];
     const double* W = dptr(B, se.W);
     const double* Z = dptr(B, se.Z);
-    for (int64_t e = threadIdx.x; e < (int64_t)m * ke; e += blockDim.x) {
-      int i = (int)(e % m), c = (int)(e / m);
-      double v = 0.0;
-      if (i >= se.row_off && i < se.row_off + se.nrows)
-        v = se.alpha * W[(int64_t)(i - se.row_off) * se.w_rs + (int64_t)c * se.w_cs];
-      Wst[(int64_t)(col + c) * m + i] = v;
-    }
-    for (int64_t e = threadIdx.x; e < (int64_t)n * ke; e += blockDim.x) {
-      int j = (int)(e % n), c = (int)(e / n);
-      double v = 0.0;
-      if (j >= se.col_off && j < se.col_off + se.ncols)
-        v = Z[(int64_t)(j - se.col_off) * se.z_rs + (int64_t)c * se.z_cs];
-      Zst[(int64_t)(col + c) * n + j] = v;
-    }
-    col += ke;
+    if (wl > 0)
+      for (int e = tid; e < wl * ke; e += blockDim.x) {
+        const int i = w0 + e % wl, c = e / wl;
+        double v = 0.0;
+        if (i >= se.row_off && i < se.row_off + se.nrows)
+          v = se.alpha * W[(int64_t)(i - se.row_off) * se.w_rs + (int64_t)c * se.w_cs];
+        Wst[(int64_t)(col + c) * m + i] = v;
+      }
+    if (zl > 0)
+      for (int e = tid; e < zl * ke; e += blockDim.x) {
+        const int j = z0 + e % zl, c = e / zl;
+        double v = 0.0;
+        if (j >= se.col_off && j < se.col_off + se.ncols)
+          v = Z[(int64_t)(j - se.col_off) * se.z_rs + (int64_t)c * se.z_cs];
+        Zst[(int64_t)(col + c) * n + j] = v;
+      }
   }
 }
 
@@ -666,39 +787,6 @@ __device__ float g_core_gf[64 * 64];
 
 constexpr int KMAX = 256;       // largest stacked rank of one rounded addition
 constexpr int JSM = 64;         // Jacobi problems up to this size run in shared memory
-
-// Reciprocal of x in [1e-30, 1e30] to full FP64 accuracy with three dependent FP64 operations:
-// r0 = 1/x from the FP32 approximate reciprocal (the FP32 operand and the FP64 seed are formed
-// by integer moves of the exponent and the leading mantissa bits, not by conversion
-// instructions), e = 1 - x r0 (|e| < 2^-21), 1/x = r0 (1 + e + e^2 + ...); the truncated series
-// leaves r0 e^3 ~ 2^-63 r0.
-// GB300 spends ~64 cycles on each dependent FP64 operation, so this is for serial sections.
-__device__ __forceinline__ double fast_rcp(double x) {
-  constexpr long long kBias = (long long)(1023 - 127) << 23;   // exponent rebias, FP32 bit position
-  const long long xb = __double_as_longlong(x);
-  const float xf = __int_as_float((int)((xb >> 29) - kBias));
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));   // ~1 ulp; the series absorbs it
-  const double r0 = __longlong_as_double(((long long)__float_as_int(rf) + kBias) << 29);
-  const double e = fma(-x, r0, 1.0);
-  return fma(r0, fma(e, e, e), r0);
-}
-
-// Total order of doubles as signed 64-bit integers (negative values have their magnitude bits
-// flipped): comparisons on the integer pipe instead of ~64-cycle FP64 compares.
-__device__ __forceinline__ long long order_key(double v) {
-  const long long b = __double_as_longlong(v);
-  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
-}
-
-// Pivot key of a diagonal entry at position i (< 256): the high word of a positive double
-// (sign, exponent, 20 mantissa bits) with its low 8 bits replaced by 255 - i, so that an
-// unsigned max picks the largest entry to ~2^-12 relative and the lowest index among near
-// ties; 0 for entries <= 0.
-__device__ __forceinline__ unsigned pivot_key(double v, int i) {
-  const long long b = __double_as_longlong(v);
-  return b > 0 ? (((unsigned)(b >> 32)) & ~255u) | (unsigned)(255 - i) : 0u;
-}
 
 // Pivoted Cholesky (outer-product form, diagonal pivoting) of the symmetric positive
 // semi-definite n x n matrix A (n <= 256, ld lda; only the lower triangle is read and written),
@@ -1435,7 +1523,7 @@ __global__ void k_permute_points(const double* __restrict__ P, const int64_t* __
 
 // ------------------------------------------------------------------------------ launchers
 static bool g_attr_set = false;
-constexpr int TRSM_SMEM = 2 * 64 * 65 * (int)sizeof(double);
+constexpr int TRSM_SMEM = (64 * 65 + 64 * (TRSM_VC + 1)) * (int)sizeof(double);
 constexpr int CORE_SMEM = 2 * JSM * (JSM + 1) * (int)sizeof(double);
 
 static void set_attributes() {
@@ -1454,10 +1542,10 @@ cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* 
   set_attributes();
   switch (kind) {
     case K_GETRF: k_getrf<<<count, 256, 0, s>>>((const GetrfOp*)ops, B); break;
-    case K_TRSM: k_trsm<<<count, 256, TRSM_SMEM, s>>>((const TrsmOp*)ops, B); break;
+    case K_TRSM: k_trsm<<<dim3(count, gy), 256, TRSM_SMEM, s>>>((const TrsmOp*)ops, B); break;
     case K_GEMM: k_gemm<<<dim3(count, gy, gz), 256, GEMM_SMEM, s>>>((const GemmOp*)ops, B); break;
     case K_COPY: k_copy<<<count, 256, 0, s>>>((const CopyOp*)ops, B); break;
-    case K_STACK: k_stack<<<count, 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
+    case K_STACK: k_stack<<<dim3(count, gy), 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
     case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, B); break;
     case K_EVAL: k_eval<<<count, 256, 0, s>>>((const EvalOp*)ops, B, h); break;
     case K_ACA: k_aca<<<count, 256, 0, s>>>((const AcaOp*)ops, B, h); break;

@@ -73,6 +73,7 @@ void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
 namespace {
 
 constexpr int KMAX_STACK = 256;     // largest stacked rank of one rounded addition
+constexpr int KMAX_ENTRIES = 256;   // largest number of pieces of one rounded addition (k_stack)
 constexpr int GEMM_MCHUNK = 512;    // row chunk of a GEMM micro-op
 constexpr int GEMM_KCHUNK = 512;    // reduction chunk of an accumulating GEMM micro-op
 constexpr int TRSM_VCHUNK = 256;    // vectors of one triangular-solve micro-op
@@ -573,7 +574,8 @@ struct Ctx {
         const int selfmax = (target_rank_zero && round == 0) ? 0 : L.cap;
         int sum = selfmax;
         size_t e1 = e0;
-        while (e1 < T.e.size() && (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
+        while (e1 < T.e.size() && e1 - e0 < (size_t)KMAX_ENTRIES &&
+               (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
           sum += T.e[e1].second;
           ++e1;
         }
@@ -663,6 +665,12 @@ struct Ctx {
       put(K_COPY, (int)w.copy[ph].size(), (int)plan.copy.size());
       plan.copy.insert(plan.copy.end(), w.copy[ph].begin(), w.copy[ph].end());
       put(K_TRSM, (int)w.trsm[ph].size(), (int)plan.trsm.size());
+      if (!w.trsm[ph].empty()) {
+        // CTAs per micro-op along its vectors (chunks of 32; a dynamic count is taken as 64)
+        int most = 0;
+        for (const TrsmOp& op : w.trsm[ph]) most = std::max(most, op.nv + (op.nvd ? 64 : 0));
+        plan.launches.back().gy = std::min(16, std::max(1, (most + 31) / 32));
+      }
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
       put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
       if (!w.gemm[ph].empty())
@@ -670,6 +678,10 @@ struct Ctx {
       plan.gemm.insert(plan.gemm.end(), w.gemm[ph].begin(), w.gemm[ph].end());
       if (!w.stack[ph].empty()) {
         put(K_STACK, (int)w.stack[ph].size(), (int)plan.trunc.size());
+        // CTAs per rounded addition along the rows: ~16k copied doubles each, at most 32
+        int64_t most = 0;
+        for (const TruncOp& op : w.stack[ph]) most = std::max(most, (int64_t)(op.m + op.n) * op.Kcap);
+        plan.launches.back().gy = (int)std::min<int64_t>(32, std::max<int64_t>(1, most / 16384));
         for (size_t q = 0; q < w.stack[ph].size(); ++q) {
           TruncOp op = w.stack[ph][q];
           op.first_entry = (int)plan.entries.size();
