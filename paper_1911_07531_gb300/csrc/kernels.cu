@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
   __shared__ double s_dinv[2];
   double* A = dptr(B, op.A);
   int* piv = iptr(B, op.piv);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < b * b; e += 256) S[e % b][e / b] = A[e];
   __syncthreads();
   if (warp == 0) getrf_select(S, 0, 0, b, piv, s_p, s_dinv, 0, B.status);
@@ -557,9 +557,12 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
         __syncwarp();
         getrf_select(S, j + 1, j + 1, b, piv, s_p, s_dinv, slot ^ 1, B.status);
       } else {
-        for (int c = j + 2 + warp - 1; c < b; c += nw - 1) {
-          const double u = S[j][c];
-          for (int i = j + 1 + lane; i < b; i += 32) S[i][c] = fma(-S[i][j], u, S[i][c]);
+        // dense enumeration of the trailing block (rows j+1.., columns j+2..): full FP64 warp
+        // instructions
+        const int m = b - 1 - j;
+        for (int e = tid - 32; e < m * (m - 1); e += blockDim.x - 32) {
+          const int i = j + 1 + e % m, c = j + 2 + e / m;
+          S[i][c] = fma(-S[i][j], S[j][c], S[i][c]);
         }
       }
     }
@@ -772,7 +775,8 @@ __device__ void jacobi_eigen(T* A, int lda, T* V, int ldv, int K, T* cs, T* sn, 
 }
 
 #ifdef HM_CORE_TIMING
-__device__ long long g_core_stamp[16];
+__device__ long long g_core_stamp[24];
+__device__ int g_jac_maxcos[8];
 __device__ float g_core_gf[64 * 64];
 #define CORE_STAMP(i)                                  \
   do {                                                 \
@@ -795,13 +799,14 @@ constexpr int JSM = 64;         // Jacobi problems up to this size run in shared
 // original index of pivoted position q (perm must hold 0..n-1 on entry). Stops when the largest
 // remaining diagonal entry is <= tol (tol >= 0); returns the rank. The pivots must lie in
 // [1e-30, 1e30] (callers scale A to unit diagonal or unit trace).
-// Step j: warp 0 interchanges positions j and p_j (chosen in the previous step); then warps
-// 1.. update the trailing lower triangle with the unscaled pivot column, A_ik -= a_ij (a_kj /
-// a_jj), while warp 0 updates its copy dg of the trailing diagonal with the same operations
-// (bitwise the same values), picks p_{j+1} from it and forms 1/a_{p_{j+1}} -- the pivot search
-// and the reciprocal of the next step overlap this step's update. Columns are scaled by
-// 1/sqrt(pivot) once at the end. dg: n doubles of shared scratch; s_flag: 2 ints, s_val: 2
-// doubles, s_pidx: 2 ints of shared scratch (double-buffered broadcast slots).
+// Step j: warp 0 interchanges positions j and p_j (chosen in the previous step) and forms
+// lv = a_:j / a_jj; then warps 1.. update the trailing lower triangle, A_ik -= a_ij lv_k (one
+// column per warp, rows over the lanes), while warp 0 updates its
+// copy dg of the trailing diagonal with the same operations (bitwise the same values), picks
+// p_{j+1} from it and forms 1/a_{p_{j+1}} -- the pivot search and the reciprocal of the next step
+// overlap this step's update. Columns are scaled by 1/sqrt(pivot) once at the end. dg, lv: n
+// doubles of shared scratch; s_flag: 2 ints, s_val: 2 doubles, s_pidx: 2 ints of shared scratch
+// (double-buffered broadcast slots).
 __device__ __forceinline__ void chol_select(const double* dg, int j, int n, double tol, int* s_flag,
                                             double* s_val, int* s_pidx, int slot) {
   // warp 0 only
@@ -819,8 +824,8 @@ __device__ __forceinline__ void chol_select(const double* dg, int j, int n, doub
   }
 }
 
-__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, double* dg, int* s_flag,
-                                double* s_val, int* s_pidx) {
+__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, double* dg, double* lv,
+                                int* s_flag, double* s_val, int* s_pidx) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (warp == 0) {
     for (int i = lane; i < n; i += 32) dg[i] = A[i + (int64_t)i * lda];
@@ -828,64 +833,96 @@ __device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol
     chol_select(dg, 0, n, tol, s_flag, s_val, s_pidx, 0);
   }
   __syncthreads();
+#ifdef HM_CORE_TIMING
+  __shared__ long long s_ct[4];
+  if (tid == 0) s_ct[0] = s_ct[1] = s_ct[2] = s_ct[3] = 0;
+  long long c0 = clock64(), c1 = c0, c2 = c0;
+#endif
   int j = 0;
   for (; j < n; ++j) {
     const int slot = j & 1;
     if (!s_flag[slot]) break;
+#ifdef HM_CORE_TIMING
+    c0 = clock64();
+#endif
     const int p = s_pidx[slot];
-    if (warp == 0 && p != j) {
-      // interchange positions j and p: rows of the finished columns, the two diagonal
-      // entries, and the pairs of the trailing lower triangle that trade places
-      for (int k = lane; k < n; k += 32) {
-        double *x, *y;
-        if (k < j) {
-          x = A + j + (int64_t)k * lda;
-          y = A + p + (int64_t)k * lda;
-        } else if (k == j) {
-          x = A + j + (int64_t)j * lda;
-          y = A + p + (int64_t)p * lda;
-        } else if (k < p) {
-          x = A + k + (int64_t)j * lda;
-          y = A + p + (int64_t)k * lda;
-        } else if (k > p) {
-          x = A + k + (int64_t)j * lda;
-          y = A + k + (int64_t)p * lda;
-        } else {
-          continue;
+    const double ipiv = s_val[slot];
+    if (warp == 0) {
+      if (p != j) {
+        // interchange positions j and p: rows of the finished columns, the two diagonal
+        // entries, and the pairs of the trailing lower triangle that trade places
+        for (int k = lane; k < n; k += 32) {
+          double *x, *y;
+          if (k < j) {
+            x = A + j + (int64_t)k * lda;
+            y = A + p + (int64_t)k * lda;
+          } else if (k == j) {
+            x = A + j + (int64_t)j * lda;
+            y = A + p + (int64_t)p * lda;
+          } else if (k < p) {
+            x = A + k + (int64_t)j * lda;
+            y = A + p + (int64_t)k * lda;
+          } else if (k > p) {
+            x = A + k + (int64_t)j * lda;
+            y = A + k + (int64_t)p * lda;
+          } else {
+            continue;
+          }
+          const double t = *x;
+          *x = *y;
+          *y = t;
         }
-        const double t = *x;
-        *x = *y;
-        *y = t;
+        if (lane == 0) {
+          const int t = perm[j];
+          perm[j] = perm[p];
+          perm[p] = t;
+          const double d = dg[j];
+          dg[j] = dg[p];
+          dg[p] = d;
+        }
+        __syncwarp();
       }
-      if (lane == 0) {
-        const int t = perm[j];
-        perm[j] = perm[p];
-        perm[p] = t;
-        const double d = dg[j];
-        dg[j] = dg[p];
-        dg[p] = d;
-      }
+      // the pivot column scaled by 1 / pivot, shared by all updates of this step
+      for (int i = j + 1 + lane; i < n; i += 32) lv[i] = A[i + (int64_t)j * lda] * ipiv;
     }
     __syncthreads();
-    const double ipiv = s_val[slot];
-    if (warp > 0 || nw == 1) {
-      const int w0 = nw > 1 ? 1 : 0;
-      for (int jj = j + 1 + warp - w0; jj < n; jj += nw - w0) {
-        const double t = A[jj + (int64_t)j * lda] * ipiv;
+#ifdef HM_CORE_TIMING
+    c1 = clock64();
+#endif
+    if (warp == 0) {
+      for (int i = j + 1 + lane; i < n; i += 32) dg[i] = fma(-A[i + (int64_t)j * lda], lv[i], dg[i]);
+      __syncwarp();
+      chol_select(dg, j + 1, n, tol, s_flag, s_val, s_pidx, slot ^ 1);
+#ifdef HM_CORE_TIMING
+      __syncwarp();
+      c2 = clock64();
+#endif
+    } else {
+      for (int jj = j + 1 + warp - 1; jj < n; jj += nw - 1) {
+        const double t = lv[jj];
         for (int ii = jj + lane; ii < n; ii += 32)
           A[ii + (int64_t)jj * lda] = fma(-A[ii + (int64_t)j * lda], t, A[ii + (int64_t)jj * lda]);
       }
     }
-    if (warp == 0) {
-      for (int i = j + 1 + lane; i < n; i += 32) {
-        const double a = A[i + (int64_t)j * lda];
-        dg[i] = fma(-a, a * ipiv, dg[i]);
-      }
-      __syncwarp();
-      chol_select(dg, j + 1, n, tol, s_flag, s_val, s_pidx, slot ^ 1);
-    }
     __syncthreads();
+#ifdef HM_CORE_TIMING
+    if (tid == 0) {
+      const long long c3 = clock64();
+      s_ct[0] += c1 - c0;
+      s_ct[1] += c2 - c1;
+      s_ct[2] += c3 - c1;
+      s_ct[3] += 1;
+    }
+#endif
   }
+#ifdef HM_CORE_TIMING
+  if (tid == 0) {
+    atomicAdd((unsigned long long*)&g_core_stamp[19], (unsigned long long)s_ct[0]);
+    atomicAdd((unsigned long long*)&g_core_stamp[20], (unsigned long long)s_ct[1]);
+    atomicAdd((unsigned long long*)&g_core_stamp[21], (unsigned long long)s_ct[2]);
+    atomicAdd((unsigned long long*)&g_core_stamp[22], (unsigned long long)s_ct[3]);
+  }
+#endif
   // scale the columns: L(:, q) = a(:, q) / sqrt(pivot_q)
   for (int q = warp; q < j; q += nw) {
     const double piv = A[q + (int64_t)q * lda];
@@ -913,6 +950,9 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
   const int half = cols / 2;
   // orthogonality target at the FP32 rounding level of dot products of length `rows`
   const float tol = fmaxf(1e-6f, 6e-8f * (float)rows);
+  // Jacobi converges quadratically here: a sweep whose largest |cos| stays below sqrt(tol)
+  // leaves the next one below tol, so it ends the iteration (rotations still applied)
+  const float tol_next = sqrtf(tol);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
@@ -940,11 +980,21 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
           be += __shfl_xor_sync(hmask, be, o);
           ga_b += __shfl_xor_sync(hmask, ga_b, o);
         }
-        if (al > 0.f && be > 0.f && fabsf(ga_b) > tol * sqrtf(al) * sqrtf(be)) {
-          const float th = (be - al) / (2.0f * ga_b);
+        // normalised quantities: gn = cos of the pair's angle, dn = (|b|^2 - |a|^2) / (|a| |b|)
+        const float rab = (al > 0.f && be > 0.f) ? rsqrtf(al) * rsqrtf(be) : 0.f;
+        const float gn = ga_b * rab, dn = (be - al) * rab;
+#ifdef HM_CORE_TIMING
+        if (hl == 0 && sweep < 8) atomicMax(&g_jac_maxcos[sweep], __float_as_int(fabsf(gn)));
+#endif
+        if (fabsf(gn) > tol) {
+          // tan 2 theta = 2 g / (|a|^2 - |b|^2); t = tan theta of the smaller root
+          const float th = __fdividef(dn, 2.0f * gn);
           float t;
           if (!(fabsf(th) < 1e18f)) t = 0.0f;
-          else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+          else {
+            const float h = fmaf(th, th, 1.0f);
+            t = copysignf(__fdividef(1.0f, fabsf(th) + h * rsqrtf(h)), th);
+          }
           const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
           if (s != 0.f) {
             for (int l = hl; l < rows; l += 16) {
@@ -961,7 +1011,7 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
                 vb[l] = s * u + c * v;
               }
             }
-            if (hl == 0) *flag = 1;
+            if (hl == 0 && fabsf(gn) > tol_next) *flag = 1;
           }
         }
       }
@@ -973,6 +1023,31 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
 #ifdef HM_CORE_TIMING
   if (threadIdx.x == 0) g_core_stamp[15] = sweep;
 #endif
+}
+
+template <int NQ>
+__device__ __forceinline__ void backsub_warp(double* Y, int ldy, const double* R, int Kc, const double* rdinv, int r,
+                                             int warp, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int l = r - 1; l >= 0; --l) {
+    const double rd = rdinv[l];
+    double x[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) x[q] = Y[l + (int64_t)(warp + nw * q) * ldy] * rd;
+    for (int p = lane; p < l; p += 32) {
+      const double rr = R[l + (int64_t)p * Kc];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        double* y = Y + p + (int64_t)(warp + nw * q) * ldy;
+        *y = fma(-rr, x[q], *y);
+      }
+    }
+    __syncwarp();
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) Y[l + (int64_t)(warp + nw * q) * ldy] = x[q];
+    __syncwarp();
+  }
 }
 
 __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, Bases B) {
@@ -1027,7 +1102,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   CORE_STAMP(1);
   // 2. pivoted Cholesky G' = Pi Rf^T Rf Pi^T; the tolerance is the noise level of a Gram
   //    matrix. Rf is kept transposed in pivoted order: Rf(q, l) = R[l + q * Kc] for l >= q.
-  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, lam, &s_int[2], &red[2], pa);
+  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, lam, rdinv, &s_int[2], &red[2], pa);
   if (Rc != R) {
     for (int e = tid; e < K * K; e += nt) {
       int i = e % K, j = e / K;
@@ -1109,7 +1184,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     __syncthreads();
     // the tolerance is one rounding unit of the trace: the Schur complement left behind perturbs
     // the eigenvalues by at most rp u tr, the rounding level of M itself
-    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, lam, &s_int[2], &red[2], pa);
+    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, lam, rdinv, &s_int[2], &red[2], pa);
     // Drmac-Veselic preconditioning: one-sided Jacobi on the columns of C = R2^T (the rows of the
     // pivoted Cholesky factor are graded and nearly orthogonal, so it converges in a few
     // sweeps): C Q = [s_1 u_1, ...] with C C^T = R2^T R2 = P^T M P, i.e. the columns of C Q are
@@ -1246,6 +1321,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   }
   for (int l = tid; l < r; l += nt) rdinv[l] = nr_rcp(R[l + (int64_t)l * Kc]);
   __syncthreads();
+  CORE_STAMP(16);
   for (int e = tid; e < K * kk; e += nt) {
     const int l = e % K, c = e / K;     // l: pivoted row of Bm
     const int q = order[c];
@@ -1256,25 +1332,25 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     if (l < r) Y[l + (int64_t)c * ldy] = Yj[l + (int64_t)q * ldj] * cs[c];
   }
   __syncthreads();
+  CORE_STAMP(17);
   // back substitution Rf11 x = X_k S^{1/2} (Rf11 upper r x r, Rf11(p, l) = R[l + p * Kc]),
-  // column oriented: one warp owns columns c = warp, warp + nw, ... and walks l = r-1 .. 0 with
-  // all of its columns in lockstep; x_l = y_l / Rf11(l, l), then lanes p < l subtract
-  // Rf11(p, l) x_l from y_p.
+  // column oriented: one warp owns columns c = warp + nw q (q < nq <= 4; kk <= 64 = 4 x 16 warps)
+  // and walks l = r-1 .. 0 with all of them in lockstep: x_l = y_l / Rf11(l, l), then lanes
+  // p < l subtract Rf11(p, l) x_l from y_p. The step is specialised to the warp's exact column
+  // count: predicated-off DFMAs would still take turns on the shared FP64 pipe.
   {
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int l = r - 1; l >= 0; --l) {
-      const double rd = rdinv[l];
-      for (int c = warp; c < kk; c += nw) {
-        double* y = Y + (int64_t)c * ldy;
-        const double x = y[l] * rd;
-        for (int p = lane; p < l; p += 32) y[p] = fma(-R[l + (int64_t)p * Kc], x, y[p]);
-        __syncwarp();
-        if (lane == 0) y[l] = x;
-      }
-      __syncwarp();
+    const int warp = tid >> 5, nw = nt >> 5;
+    const int nq = kk > warp ? (kk - warp + nw - 1) / nw : 0;
+    switch (nq) {
+      case 4: backsub_warp<4>(Y, ldy, R, Kc, rdinv, r, warp, nw); break;
+      case 3: backsub_warp<3>(Y, ldy, R, Kc, rdinv, r, warp, nw); break;
+      case 2: backsub_warp<2>(Y, ldy, R, Kc, rdinv, r, warp, nw); break;
+      case 1: backsub_warp<1>(Y, ldy, R, Kc, rdinv, r, warp, nw); break;
+      default: break;
     }
   }
   __syncthreads();
+  CORE_STAMP(18);
   // scatter to the rows perm[0..r) and undo the equilibration (rows of Tw scale by 1/d_i)
   for (int e = tid; e < K * kk; e += nt) {
     const int l = e % K, c = e / K;
