@@ -793,143 +793,112 @@ constexpr int KMAX = 256;       // largest stacked rank of one rounded addition
 constexpr int JSM = 64;         // Jacobi problems up to this size run in shared memory
 
 // Pivoted Cholesky (outer-product form, diagonal pivoting) of the symmetric positive
-// semi-definite n x n matrix A (n <= 256, ld lda; only the lower triangle is read and written),
-// in place with physical symmetric interchanges: on return P^T A P = L L^T with L lower
-// trapezoidal, its column q (rows q..n-1) in column q of A for q < rank, and perm[q] the
-// original index of pivoted position q (perm must hold 0..n-1 on entry). Stops when the largest
+// semi-definite n x n matrix A (n <= 256, ld lda), with logical pivoting: A keeps its index
+// order and every symmetric entry {i, k} lives at its lower position (max, min); nothing is
+// interchanged. On return perm is the full pivot order (the rank pivots, then the remaining
+// indices), rs[q] = 1/sqrt(pivot q) for q < rank, and the factor of P^T A P = L L^T is
+// L(l, q) = a(perm[l], perm[q]) rs[q] for l >= q (chol_entry below). Stops when the largest
 // remaining diagonal entry is <= tol (tol >= 0); returns the rank. The pivots must lie in
 // [1e-30, 1e30] (callers scale A to unit diagonal or unit trace).
-// Step j: warp 0 interchanges positions j and p_j (chosen in the previous step) and forms
-// lv = a_:j / a_jj; then warps 1.. update the trailing lower triangle, A_ik -= a_ij lv_k (one
-// column per warp, rows over the lanes), while warp 0 updates its
-// copy dg of the trailing diagonal with the same operations (bitwise the same values), picks
-// p_{j+1} from it and forms 1/a_{p_{j+1}} -- the pivot search and the reciprocal of the next step
-// overlap this step's update. Columns are scaled by 1/sqrt(pivot) once at the end. dg, lv: n
-// doubles of shared scratch; s_flag: 2 ints, s_val: 2 doubles, s_pidx: 2 ints of shared scratch
-// (double-buffered broadcast slots).
-__device__ __forceinline__ void chol_select(const double* dg, int j, int n, double tol, int* s_flag,
-                                            double* s_val, int* s_pidx, int slot) {
-  // warp 0 only
-  const int lane = threadIdx.x & 31;
-  unsigned best = 0;
-  for (int i = j + lane; i < n; i += 32) best = max(best, pivot_key(dg[i], i));
-  best = __reduce_max_sync(0xffffffffu, best);
-  const int p = best ? 255 - (int)(best & 255u) : -1;
-  if (lane == 0) {
-    const double piv = p >= 0 ? dg[p] : 0.0;
-    const bool go = p >= 0 && __double_as_longlong(piv) > __double_as_longlong(fmax(tol, 0.0));
-    s_flag[slot] = go ? 1 : 0;
-    s_pidx[slot] = p;
-    if (go) s_val[slot] = fast_rcp(piv);
-  }
+// Step j (pivot p, trailing index list of n - 1 - j entries): warps 1.. update the trailing
+// pairs, a_ik -= a_ip (a_kp / a_pp), one list position per warp for k and lanes over i, while
+// warp 0 updates its copy dg of the trailing diagonal with the same operations (bitwise the same
+// values), picks the next pivot (warp max over 32-bit keys of the bit patterns), forms its
+// reciprocal and writes the next list (this one without the new pivot) into the other buffer.
+// One block barrier per step. dg, rs: n doubles; ul: 2 n ints; s_flag, s_pidx: 2 ints;
+// s_val: 2 doubles (shared scratch; the 2-slot ones are double-buffered broadcast slots).
+__device__ __forceinline__ int64_t chol_at(int i, int k, int lda) {
+  return i >= k ? i + (int64_t)k * lda : k + (int64_t)i * lda;
+}
+__device__ __forceinline__ double chol_entry(const double* A, int lda, const int* perm, const double* rs, int l,
+                                             int q) {
+  return A[chol_at(perm[l], perm[q], lda)] * rs[q];
 }
 
-__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, double* dg, double* lv,
-                                int* s_flag, double* s_val, int* s_pidx) {
+__device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol, double* dg, double* rs,
+                                int* ul, int* s_flag, double* s_val, int* s_pidx) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const long long tol_bits = __double_as_longlong(fmax(tol, 0.0));
   if (warp == 0) {
     for (int i = lane; i < n; i += 32) dg[i] = A[i + (int64_t)i * lda];
     __syncwarp();
-    chol_select(dg, 0, n, tol, s_flag, s_val, s_pidx, 0);
+    unsigned best = 0;
+    for (int i = lane; i < n; i += 32) best = max(best, pivot_key(dg[i], i));
+    best = __reduce_max_sync(0xffffffffu, best);
+    const int p = best ? 255 - (int)(best & 255u) : -1;
+    const bool go = p >= 0 && __double_as_longlong(dg[p]) > tol_bits;
+    if (go)
+      for (int r = lane; r < n - 1; r += 32) ul[r] = r < p ? r : r + 1;
+    if (lane == 0) {
+      s_flag[0] = go ? 1 : 0;
+      s_pidx[0] = p;
+      if (go) {
+        s_val[0] = fast_rcp(dg[p]);
+        perm[0] = p;
+      }
+    }
   }
   __syncthreads();
-#ifdef HM_CORE_TIMING
-  __shared__ long long s_ct[4];
-  if (tid == 0) s_ct[0] = s_ct[1] = s_ct[2] = s_ct[3] = 0;
-  long long c0 = clock64(), c1 = c0, c2 = c0;
-#endif
   int j = 0;
   for (; j < n; ++j) {
     const int slot = j & 1;
     if (!s_flag[slot]) break;
-#ifdef HM_CORE_TIMING
-    c0 = clock64();
-#endif
     const int p = s_pidx[slot];
     const double ipiv = s_val[slot];
+    const int m = n - 1 - j;
+    const int* cur = ul + slot * n;
     if (warp == 0) {
-      if (p != j) {
-        // interchange positions j and p: rows of the finished columns, the two diagonal
-        // entries, and the pairs of the trailing lower triangle that trade places
-        for (int k = lane; k < n; k += 32) {
-          double *x, *y;
-          if (k < j) {
-            x = A + j + (int64_t)k * lda;
-            y = A + p + (int64_t)k * lda;
-          } else if (k == j) {
-            x = A + j + (int64_t)j * lda;
-            y = A + p + (int64_t)p * lda;
-          } else if (k < p) {
-            x = A + k + (int64_t)j * lda;
-            y = A + p + (int64_t)k * lda;
-          } else if (k > p) {
-            x = A + k + (int64_t)j * lda;
-            y = A + k + (int64_t)p * lda;
-          } else {
-            continue;
-          }
-          const double t = *x;
-          *x = *y;
-          *y = t;
-        }
-        if (lane == 0) {
-          const int t = perm[j];
-          perm[j] = perm[p];
-          perm[p] = t;
-          const double d = dg[j];
-          dg[j] = dg[p];
-          dg[p] = d;
-        }
-        __syncwarp();
+      for (int r = lane; r < m; r += 32) {
+        const int i = cur[r];
+        const double a = A[chol_at(i, p, lda)];
+        dg[i] = fma(-a, a * ipiv, dg[i]);
       }
-      // the pivot column scaled by 1 / pivot, shared by all updates of this step
-      for (int i = j + 1 + lane; i < n; i += 32) lv[i] = A[i + (int64_t)j * lda] * ipiv;
-    }
-    __syncthreads();
-#ifdef HM_CORE_TIMING
-    c1 = clock64();
-#endif
-    if (warp == 0) {
-      for (int i = j + 1 + lane; i < n; i += 32) dg[i] = fma(-A[i + (int64_t)j * lda], lv[i], dg[i]);
       __syncwarp();
-      chol_select(dg, j + 1, n, tol, s_flag, s_val, s_pidx, slot ^ 1);
-#ifdef HM_CORE_TIMING
-      __syncwarp();
-      c2 = clock64();
-#endif
+      unsigned best = 0;
+      for (int r = lane; r < m; r += 32) {
+        const int i = cur[r];
+        best = max(best, pivot_key(dg[i], i));
+      }
+      best = __reduce_max_sync(0xffffffffu, best);
+      const int q = best ? 255 - (int)(best & 255u) : -1;
+      const bool go = q >= 0 && __double_as_longlong(dg[q]) > tol_bits;
+      if (go) {
+        int pos = m;
+        for (int r = lane; r < m; r += 32)
+          if (cur[r] == q) pos = r;
+        pos = (int)__reduce_min_sync(0xffffffffu, (unsigned)pos);
+        int* nxt = ul + (slot ^ 1) * n;
+        for (int r = lane; r < m - 1; r += 32) nxt[r] = cur[r < pos ? r : r + 1];
+      }
+      if (lane == 0) {
+        s_flag[slot ^ 1] = go ? 1 : 0;
+        s_pidx[slot ^ 1] = q;
+        if (go) {
+          s_val[slot ^ 1] = fast_rcp(dg[q]);
+          perm[j + 1] = q;
+        }
+      }
     } else {
-      for (int jj = j + 1 + warp - 1; jj < n; jj += nw - 1) {
-        const double t = lv[jj];
-        for (int ii = jj + lane; ii < n; ii += 32)
-          A[ii + (int64_t)jj * lda] = fma(-A[ii + (int64_t)j * lda], t, A[ii + (int64_t)jj * lda]);
+      for (int c = warp - 1; c < m; c += nw - 1) {
+        const int kk = cur[c];
+        const double t = A[chol_at(kk, p, lda)] * ipiv;
+        for (int r = c + lane; r < m; r += 32) {
+          const int ii = cur[r];
+          double* x = A + chol_at(ii, kk, lda);
+          *x = fma(-A[chol_at(ii, p, lda)], t, *x);
+        }
       }
     }
     __syncthreads();
-#ifdef HM_CORE_TIMING
-    if (tid == 0) {
-      const long long c3 = clock64();
-      s_ct[0] += c1 - c0;
-      s_ct[1] += c2 - c1;
-      s_ct[2] += c3 - c1;
-      s_ct[3] += 1;
-    }
-#endif
   }
-#ifdef HM_CORE_TIMING
-  if (tid == 0) {
-    atomicAdd((unsigned long long*)&g_core_stamp[19], (unsigned long long)s_ct[0]);
-    atomicAdd((unsigned long long*)&g_core_stamp[20], (unsigned long long)s_ct[1]);
-    atomicAdd((unsigned long long*)&g_core_stamp[21], (unsigned long long)s_ct[2]);
-    atomicAdd((unsigned long long*)&g_core_stamp[22], (unsigned long long)s_ct[3]);
+  // the remaining indices complete the permutation; reciprocal square roots of the pivots
+  if (j < n) {
+    const int* rest = j >= 1 ? ul + ((j - 1) & 1) * n : nullptr;
+    for (int r = tid; r < n - j; r += blockDim.x) perm[j + r] = rest ? rest[r] : r;
   }
-#endif
-  // scale the columns: L(:, q) = a(:, q) / sqrt(pivot_q)
-  for (int q = warp; q < j; q += nw) {
-    const double piv = A[q + (int64_t)q * lda];
-    const double rinv = nr_rsqrt(piv);
-    for (int i = q + 1 + lane; i < n; i += 32) A[i + (int64_t)q * lda] *= rinv;
-    __syncwarp();
-    if (lane == 0) A[q + (int64_t)q * lda] = piv * rinv;
+  for (int q = tid; q < j; q += blockDim.x) {
+    const int pq = perm[q];
+    rs[q] = nr_rsqrt(A[pq + (int64_t)pq * lda]);
   }
   __syncthreads();
   return j;
@@ -1054,7 +1023,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
   __shared__ double d[KMAX], dinv[KMAX], rdinv[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
-  __shared__ int perm[KMAX], perm2[KMAX], pa[KMAX / 2], pb[KMAX / 2], order[KMAX], s_int[4];
+  __shared__ int perm[KMAX], perm2[KMAX], pa[KMAX / 2], pb[KMAX / 2], order[KMAX], s_int[4], ul[2 * KMAX];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int K = *iptr(B, op.Kd);
   int* rk = iptr(B, op.rank);
@@ -1101,14 +1070,24 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
   __syncthreads();
   CORE_STAMP(1);
   // 2. pivoted Cholesky G' = Pi Rf^T Rf Pi^T; the tolerance is the noise level of a Gram
-  //    matrix. Rf is kept transposed in pivoted order: Rf(q, l) = R[l + q * Kc] for l >= q.
-  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, lam, rdinv, &s_int[2], &red[2], pa);
-  if (Rc != R) {
+  //    matrix. Rf is stored transposed in pivoted order: Rf(q, l) = R[l + q * Kc] for l >= q.
+  const int r = pivoted_cholesky(Rc, ldr, K, perm, 4.0 * K * 2.2e-16, lam, rdinv, ul, &s_int[2], &red[2], pa);
+  // the factor in pivoted layout, R[l + q * Kc] = Rf(q, l) for l >= q (q < r), zero elsewhere;
+  // when Rc is R itself (K > JSM) it is gathered into T1 and copied back
+  {
+    double* Lp = Rc != R ? R : T1;
     for (int e = tid; e < K * K; e += nt) {
-      int i = e % K, j = e / K;
-      R[i + (int64_t)j * Kc] = Rc[i + (int64_t)j * ldr];
+      const int l = e % K, q = e / K;
+      Lp[l + (int64_t)q * Kc] = (q < r && l >= q) ? chol_entry(Rc, ldr, perm, rdinv, l, q) : 0.0;
     }
     __syncthreads();
+    if (Lp == T1) {
+      for (int e = tid; e < K * K; e += nt) {
+        const int l = e % K, q = e / K;
+        R[l + (int64_t)q * Kc] = T1[l + (int64_t)q * Kc];
+      }
+      __syncthreads();
+    }
   }
   if (r == 0) {
     if (tid == 0) *rk = 0;
@@ -1184,7 +1163,7 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     __syncthreads();
     // the tolerance is one rounding unit of the trace: the Schur complement left behind perturbs
     // the eigenvalues by at most rp u tr, the rounding level of M itself
-    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, lam, rdinv, &s_int[2], &red[2], pa);
+    const int rc = pivoted_cholesky(Mj, ldj, rp, perm2, 2.2e-16, lam, rdinv, ul, &s_int[2], &red[2], pa);
     // Drmac-Veselic preconditioning: one-sided Jacobi on the columns of C = R2^T (the rows of the
     // pivoted Cholesky factor are graded and nearly orthogonal, so it converges in a few
     // sweeps): C Q = [s_1 u_1, ...] with C C^T = R2^T R2 = P^T M P, i.e. the columns of C Q are
@@ -1195,9 +1174,8 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
     const int ldf = rp <= JSM ? JSM + 1 : 2 * JSM + 1;
     for (int e = tid; e < rp * rcp; e += nt) {
       const int l = e % rp, q = e / rp;    // row l = pivoted position, column q = row q of R2
-                                           // (R2(q, l) = Mj[l + q * ldj] for l >= q)
       float v = 0.0f;
-      if (q < rc && l >= q) v = (float)Mj[l + (int64_t)q * ldj];
+      if (q < rc && l >= q) v = (float)chol_entry(Mj, ldj, perm2, rdinv, l, q);
       Gf[l + q * ldf] = v;
     }
     __syncthreads();
