@@ -34,10 +34,10 @@ import hm_workloads as W  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # DRAM bytes (read + write) per counted FLOP of a launch, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum) of one H-LU step of the n = 32768 sphere: the largest k_gemm launch
-# (8906 micro-ops: 406.3 MB + 20.2 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 269.1 kB for
+# (8906 micro-ops: 406.3 MB + 20.2 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 285.7 kB for
 # 9.0379 MFLOP). A launch's traffic is taken as this ratio times its FLOPs.
 PROFILED_BYTES_PER_FLOP = {"gemm": (406.298112e6 + 20.151552e6) / 2231684434.0,
-                           "core": 269056.0 / 9037896.0}
+                           "core": 285696.0 / 9037896.0}
 KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 WORKLOAD_TEXT = {
     "cube131072": "n=131072 uniform on the unit-cube surface, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
@@ -304,6 +304,7 @@ def main():
         r0 = torch.cuda.Event(enable_timing=True)
         r1 = torch.cuda.Event(enable_timing=True)
         r2 = torch.cuda.Event(enable_timing=True)
+        hm.hm_lu(ctx, A, eps=1e-4).free()      # first use builds the eps = 1e-4 plan (untimed)
         r0.record(stream)
         F4 = hm.hm_lu(ctx, A, eps=1e-4)
         r1.record(stream)
