@@ -153,6 +153,24 @@ def run_reference(args, rank):
     return 0
 
 
+def replica_points(cfg, rank):
+    """Points of this rank's replica: every rank factors its own instance (seed + rank)."""
+    return W.points_for(cfg["geometry"], cfg["n"], cfg["seed"] + rank)
+
+
+def aggregate_ranks(total_ms, flops, dist, device):
+    """Whole-job figures over the ranks: the slowest rank's time and the sum of every rank's
+    FLOPs (replicas only: no data moves between ranks besides these two numbers)."""
+    if dist is None:
+        return total_ms, flops
+    import torch
+    t = torch.tensor([total_ms, flops], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,7 +200,7 @@ def main():
     hm.build_library()
     cfg = W.WORKLOADS[args.workload]
     n = cfg["n"]
-    pts = W.points_for(cfg["geometry"], n, cfg["seed"] + rank)
+    pts = replica_points(cfg, rank)
     ctx = hm.HMContext(local)
     stream = ctx.stream
 
@@ -228,14 +246,7 @@ def main():
         barrier()
         wall = time.perf_counter() - t_wall0
     total_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([total_ms, sum(flops)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, all_flops = float(mx[0]), float(t[1])
-    else:
-        total_ms_max, all_flops = total_ms, sum(flops)
+    total_ms_max, all_flops = aggregate_ranks(total_ms, sum(flops), dist, "cuda")
     value = all_flops / (total_ms_max * 1e-3) * 1e-9
     fstats = last.stats()
 
