@@ -155,15 +155,28 @@ __device__ __forceinline__ unsigned pivot_key(double v, int i) {
 // 64 x 64 (3.4x the useful FMAs on the H-LU plans). Instead the output is cut into exact tiles
 // of at most GE elements (at most GTM rows and columns), each thread owns up to four output
 // elements of a tile, and for tiles of fewer than 128 elements G = 2..8 threads split the
-// reduction of one element (partial sums combined in shared memory). A slice of GKS reduction
-// steps of both operands is staged in shared memory per pass. Tiles of one micro-op are spread
+// reduction of one element (partial sums combined in shared memory). Slices of GKS reduction
+// steps of both operands are staged in shared memory through two buffers: the next slice is
+// fetched with cp.async while the current one is multiplied. Tiles of one micro-op are spread
 // over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z
 // (per micro-op counts in GemmOp::split), so that a large micro-op does not sit on one SM.
 constexpr int KMAX_ENTRIES = 256;   // largest number of pieces of one rounded addition (planner)
 constexpr int GE = 1024;      // largest C tile (elements)
 constexpr int GTM = 128;      // largest C tile side
-constexpr int GKS = 32;       // staged reduction slice
-constexpr int GEMM_SMEM = (2 * GKS * (GTM + 1) + 256) * (int)sizeof(double);
+constexpr int GKS = 16;       // staged reduction slice (two buffers: the next slice is fetched with
+                              // cp.async while the current one is multiplied)
+constexpr int GBUF = 2 * GKS * (GTM + 1);   // doubles of one buffer (A slice, then B slice)
+constexpr int GEMM_SMEM = (2 * GBUF + 256) * (int)sizeof(double);
+
+// 8-byte asynchronous copy global -> shared (zero-fill when !valid: no bytes are read)
+__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void gemm_tile_shape(int m, int n, int& mt, int& nt, int& nrt, int& nct) {
   nct = (n + GTM - 1) / GTM;
@@ -194,7 +207,7 @@ __device__ __forceinline__ int sym_prefix(int x, int c0, int mi) {
   return sym_tri(max(0, c0 + x), mi) - sym_tri(max(0, c0), mi);
 }
 
-__global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
+__global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
   const GemmOp op = ops[blockIdx.x];
   const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = max(dimv(B, op.k, op.kd), 0);
   const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
@@ -211,10 +224,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
   const int sz = min(min((want + sy - 1) / sy, szmax), max(nslices, 1));
   if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;
   const int z0 = blockIdx.z, zs = sz;
-  extern __shared__ double gsm[];
-  double* As = gsm;                         // [GKS][GTM + 1]
-  double* Bs = gsm + GKS * (GTM + 1);       // [GKS][GTM + 1]
-  double* red = Bs + GKS * (GTM + 1);       // [256]
+  extern __shared__ double gsm[];             // buffer b: A slice [GKS][GTM + 1], B slice [GKS][GTM + 1]
+  double* red = gsm + 2 * GBUF;               // [256]
   const double* A = dptr(B, op.A);
   const double* Bm = dptr(B, op.B);
   double* C = dptr(B, op.C);
@@ -257,9 +268,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
     const int grp = tid < nslot ? tid / ne : 0;
     const int wmy = __reduce_max_sync(0xffffffffu, (unsigned)nmy);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int sl = z0; sl < nslices; sl += zs) {
+    // stage slice `sl` of A (mi x ks) and B (ks x nj) into buffer `buf` with asynchronous copies
+    auto stage = [&](int sl, int buf) {
+      double* Asb = gsm + buf * GBUF;
+      double* Bsb = Asb + GKS * (GTM + 1);
       const int L0 = sl * GKS, ks = min(GKS, k - L0);
-      __syncthreads();
       for (int e = tid; e < mi * ks; e += 256) {
         int i, l;
         if (a_i_fast) {
@@ -271,11 +284,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
         }
         const int gi = i0 + i, gl = L0 + l;
         const double* src = A + (int64_t)gi * op.a_rs + (int64_t)gl * op.a_cs;
-        double v;
-        if (unitlower) v = gi > gl ? *src : (gi == gl ? 1.0 : 0.0);
-        else if (upper) v = gl >= gi ? *src : 0.0;
-        else v = *src;
-        As[l * (GTM + 1) + i] = v;
+        double* dst = Asb + l * (GTM + 1) + i;
+        if (unitlower && gi == gl) *dst = 1.0;
+        else cp_async8(dst, src, unitlower ? gi > gl : (upper ? gl >= gi : true));
       }
       for (int e = tid; e < ks * nj; e += 256) {
         int j, l;
@@ -286,9 +297,23 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
           l = e % ks;
           j = e / ks;
         }
-        Bs[l * (GTM + 1) + j] = Bm[(int64_t)(L0 + l) * op.b_rs + (int64_t)(j0 + j) * op.b_cs];
+        cp_async8(Bsb + l * (GTM + 1) + j, Bm + (int64_t)(L0 + l) * op.b_rs + (int64_t)(j0 + j) * op.b_cs, true);
+      }
+      cp_async_commit();
+    };
+    int buf = 0;
+    if (z0 < nslices) stage(z0, 0);
+    for (int sl = z0; sl < nslices; sl += zs) {
+      const int ks = min(GKS, k - sl * GKS);
+      if (sl + zs < nslices) {
+        stage(sl + zs, buf ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
       __syncthreads();
+      const double* As = gsm + buf * GBUF;
+      const double* Bs = As + GKS * (GTM + 1);
       if (G == 1) {
         // the slot count is made warp-uniform so that no DFMA is issued for an empty slot
         // (a predicated-off DFMA still takes its turn on the FP64 pipe); the extra lanes of
@@ -304,6 +329,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, Ba
         const int lo = (grp * ks) / G, hi = ((grp + 1) * ks) / G;
         for (int l = lo; l < hi; ++l) acc[0] = fma(As[l * (GTM + 1) + ii[0]], Bs[l * (GTM + 1) + jj[0]], acc[0]);
       }
+      __syncthreads();
+      buf ^= 1;
     }
     if (G > 1) {
       __syncthreads();
