@@ -34,9 +34,9 @@ import hm_workloads as W  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # DRAM bytes (read + write) per counted FLOP of a launch, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum) of one H-LU step of the n = 32768 sphere: the largest k_gemm launch
-# (8906 micro-ops: 406.3 MB + 20.2 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 285.7 kB for
+# (8906 micro-ops: 405.4 MB + 20.4 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 285.7 kB for
 # 9.0379 MFLOP). A launch's traffic is taken as this ratio times its FLOPs.
-PROFILED_BYTES_PER_FLOP = {"gemm": (406.298112e6 + 20.151552e6) / 2231684434.0,
+PROFILED_BYTES_PER_FLOP = {"gemm": (405.352192e6 + 20.44544e6) / 2231684434.0,
                            "core": 285696.0 / 9037896.0}
 KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 WORKLOAD_TEXT = {
