@@ -216,10 +216,10 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
   const int nslices = (k + GKS - 1) / GKS;
   int mt, nt, nrt, nct;
   gemm_tile_shape(m, n, mt, nt, nrt, nct);
-  // split actually used: the planner's bound, lowered to ~32k FMAs per CTA for the real sizes
+  // split actually used: the planner's bound, lowered to ~16k FMAs per CTA for the real sizes
   const int symax = max(1, op.split & 0xffff), szmax = atomic ? max(1, op.split >> 16) : 1;
   const double work = (double)m * n * max(k, 1);
-  const int want = min(symax * szmax, max(1, (int)ceil(work * (1.0 / 32768.0))));
+  const int want = min(symax * szmax, max(1, (int)ceil(work * (1.0 / 16384.0))));
   const int sy = min(min(want, symax), nrt * nct);
   const int sz = min(min((want + sy - 1) / sy, szmax), max(nslices, 1));
   if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;

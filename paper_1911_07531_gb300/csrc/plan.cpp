@@ -28,11 +28,11 @@ namespace hm {
 
 void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
   // Dynamic sizes (ranks) are not known here: each micro-op carries an expected value in
-  // `split` (0: 16). A CTA should get at least ~32k FMAs (16k cycles of one SM's FP64 pipe) and
+  // `split` (0: 16). A CTA should get at least ~16k FMAs (8k cycles of one SM's FP64 pipe) and
   // about the launch's average work per CTA slot (three resident CTAs per SM). The split stored
   // is an upper bound; the kernel lowers it from the actual sizes.
-  constexpr double kMinWork = 32768.0;
-  constexpr int kSlots = 3 * 152, kMaxSplit = 16, kTile = 1024, kSlice = 32;
+  constexpr double kMinWork = 16384.0;
+  constexpr int kSlots = 3 * 152, kMaxSplit = 32, kTile = 1024, kSlice = 16;
   std::vector<double> w(count);
   std::vector<int> idx(count);
   auto dims = [](const GemmOp& o, double& m, double& n, double& k) {
