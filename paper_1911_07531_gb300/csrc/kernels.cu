@@ -1021,6 +1021,8 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
 #endif
 }
 
+// Back substitution Rf11 x = y for the NQ columns y_c (c = warp + nw q) of Y owned by one warp,
+// in lockstep (see k_core step 7); Rf11(p, l) = R[l + p * Kc], rdinv[l] = 1 / Rf11(l, l).
 template <int NQ>
 __device__ __forceinline__ void backsub_warp(double* Y, int ldy, const double* R, int Kc, const double* rdinv, int r,
                                              int warp, int nw) {
@@ -1046,6 +1048,19 @@ __device__ __forceinline__ void backsub_warp(double* Y, int ldy, const double* R
   }
 }
 
+// Rounded truncation core, one rounded addition per CTA (§2.3: the sum of low-rank updates of a
+// leaf truncated to precision eps, at most the rank cap). From the Gram matrices G_W = W^T W and
+// G_Z = Z^T Z of the stacked factors W = [U, a_1 W_1, ...], Z = [V, Z_1, ...] (upper triangles,
+// formed by k_gemm) it computes the coefficient matrices of the truncated U = W T_W, V = Z T_Z
+// (rebuilt by k_gemm):
+//   1. equilibrate G_W; pivoted Cholesky G' = Pi Rf^T Rf Pi^T (tolerance 4 K u);
+//   2-4. Bm = D Pi Rf^T and M = Bm^T G_Z Bm (triangular products);
+//   5. eigen-decomposition of M: pivoted Cholesky of M / tr(M) and FP32 one-sided Jacobi on the
+//      factor's transpose (rank <= 128), else FP64 two-sided Jacobi on M;
+//   6. keep sigma_i = sqrt(lam_i) > eps sigma_1 (at most the cap); FP64 orthogonalisation of the
+//      kept vectors in order of decreasing eigenvalue;
+//   7. T_Z = Bm X_k S^{-1/2}, T_W = D^-1 Pi Rf11^-1 X_k S^{1/2} (back substitution).
+// V = Z T_Z has orthonormal columns; U = W T_W carries the singular values.
 __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, Bases B) {
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
