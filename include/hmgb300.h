@@ -159,7 +159,10 @@ int hm_factor_stats(const hm_factor* F, hm_stats* out);
  * relative spectral accuracy eps (keep sigma_i > eps sigma_1) and rank <= cap (<= 64):
  * U (m x k) and V (n x k, orthonormal columns) with U V^T ~ W Z^T. K <= 256. *k_out
  * (host) receives k. This is the kernel the H-LU applies to every low-rank update
- * (the "truncation operation" of §2.3); device scratch comes from the context allocator. */
+ * (the "truncation operation" of §2.3); device scratch comes from the context allocator.
+ * The method works on the Gram matrices W^T W and Z^T Z, so its error floor is about
+ * sqrt(K u) relative to |W| |Z| (~1e-8): eps below that is not resolved, and singular values
+ * within ~1e-6 (relative) of eps sigma_1 may be kept or dropped. */
 int hm_truncate(hm_ctx* ctx, int64_t m, int64_t n, int K, const double* W, int64_t ldw, const double* Z,
                 int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V, int64_t ldv, int* k_out);
 
