@@ -26,15 +26,17 @@
 
 namespace hm {
 
-void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
+void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz) {
   // Dynamic sizes (ranks) are not known here: each micro-op carries an expected value in
   // `split` (0: 16). A CTA should get at least ~16k FMAs (8k cycles of one SM's FP64 pipe) and
   // about the launch's average work per CTA slot (three resident CTAs per SM). The split stored
   // is an upper bound; the kernel lowers it from the actual sizes.
   constexpr double kMinWork = 16384.0;
   constexpr int kSlots = 3 * 152, kMaxSplit = 32, kTile = 1024, kSlice = 16;
-  std::vector<double> w(count);
-  std::vector<int> idx(count);
+  thread_local std::vector<double> w;
+  thread_local std::vector<int> idx;
+  w.resize(count);
+  idx.resize(count);
   auto dims = [](const GemmOp& o, double& m, double& n, double& k) {
     const double dyn = o.split > 0 ? (double)o.split : 16.0;
     m = o.m + (o.md ? dyn : 0.0);
@@ -51,23 +53,26 @@ void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
   }
   const double target = std::max(kMinWork, total / kSlots);
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
-  std::vector<GemmOp> sorted(count);
   gy = gz = 1;
   for (int t = 0; t < count; ++t) {
-    GemmOp o = ops[idx[t]];
+    const GemmOp& src = ops[idx[t]];
     double m, n, k;
-    dims(o, m, n, k);
+    dims(src, m, n, k);
     const int want = std::min(kMaxSplit, std::max(1, (int)std::ceil(w[idx[t]] / target)));
     const int tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
-    const int slices = (o.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
+    const int slices = (src.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
     const int sy = std::max(1, std::min(want, tiles));
     const int sz = std::max(1, std::min((want + sy - 1) / sy, slices));
-    o.split = sy | (sz << 16);
+    out[t] = src;
+    out[t].split = sy | (sz << 16);
     gy = std::max(gy, sy);
     gz = std::max(gz, sz);
-    sorted[t] = o;
   }
-  std::copy(sorted.begin(), sorted.end(), ops);
+}
+
+void gemm_grid(GemmOp* ops, int count, int& gy, int& gz) {
+  std::vector<GemmOp> in(ops, ops + count);
+  gemm_grid_to(in.data(), count, ops, gy, gz);
 }
 
 namespace {
@@ -673,9 +678,12 @@ struct Ctx {
       }
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
       put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
-      if (!w.gemm[ph].empty())
-        gemm_grid(w.gemm[ph].data(), (int)w.gemm[ph].size(), plan.launches.back().gy, plan.launches.back().gz);
-      plan.gemm.insert(plan.gemm.end(), w.gemm[ph].begin(), w.gemm[ph].end());
+      if (!w.gemm[ph].empty()) {
+        const size_t at = plan.gemm.size();
+        plan.gemm.resize(at + w.gemm[ph].size());
+        gemm_grid_to(w.gemm[ph].data(), (int)w.gemm[ph].size(), plan.gemm.data() + at, plan.launches.back().gy,
+                     plan.launches.back().gz);
+      }
       if (!w.stack[ph].empty()) {
         put(K_STACK, (int)w.stack[ph].size(), (int)plan.trunc.size());
         // CTAs per rounded addition along the rows: ~16k copied doubles each, at most 32

@@ -41,6 +41,9 @@ struct Launch {
 // C along y, reduction slices of accumulating micro-ops along z, recorded in GemmOp::split);
 // gy, gz are the launch's maxima.
 void gemm_grid(GemmOp* ops, int count, int& gy, int& gz);
+// The same, writing the ordered micro-ops with their splits to out (count entries, not
+// overlapping ops).
+void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz);
 
 struct Plan {
   std::vector<GetrfOp> getrf;
