@@ -61,16 +61,20 @@ class HLUFactor:
         self.hlu(self.ct.root)
         return self
 
+    def leaf_lu(self, b):
+        """Dense LU with partial pivoting of the diagonal leaf b (Alg 2, leaf case)."""
+        D = self.M[b.key].D
+        lu, piv = sla.lu_factor(D, check_finite=False)
+        if np.any(np.diag(lu) == 0.0):
+            self.singular = True
+        self.M[b.key] = DiagLU(lu, piv)
+        nb = D.shape[0]
+        self.stats.flops += 2.0 * nb ** 3 / 3.0
+
     def hlu(self, t):
         b = self.bt.get(t, t)
         if b.is_leaf:
-            D = self.M[b.key].D
-            lu, piv = sla.lu_factor(D, check_finite=False)
-            if np.any(np.diag(lu) == 0.0):
-                self.singular = True
-            self.M[b.key] = DiagLU(lu, piv)
-            nb = D.shape[0]
-            self.stats.flops += 2.0 * nb ** 3 / 3.0
+            self.leaf_lu(b)
             return
         t0, t1 = t.sons
         self.hlu(t0)
@@ -80,14 +84,18 @@ class HLUFactor:
         self.hlu(t1)
 
     # -- Alg 3: L_tt X_ts = M_ts -----------------------------------------------------------------
+    def leaf_trsl(self, t, b):
+        """L_tt X = M for the leaf block b = (t, s) (Alg 3, leaf case)."""
+        st = self.M[b.key]
+        if isinstance(st, Dense):
+            st.D = self.lsolve(t, st.D)
+        else:
+            st.U = self.lsolve(t, st.U)
+
     def htrsl(self, t, s):
         b = self.bt.get(t, s)
         if b.is_leaf:
-            st = self.M[b.key]
-            if isinstance(st, Dense):
-                st.D = self.lsolve(t, st.D)
-            else:
-                st.U = self.lsolve(t, st.U)
+            self.leaf_trsl(t, b)
             return
         t0, t1 = t.sons
         s0, s1 = s.sons
@@ -99,14 +107,18 @@ class HLUFactor:
         self.htrsl(t1, s1)
 
     # -- upper mirror of Alg 3: X_st U_tt = M_st ---------------------------------------------
+    def leaf_trsu(self, t, b):
+        """X U_tt = M for the leaf block b = (s, t) (upper mirror of Alg 3, leaf case)."""
+        st = self.M[b.key]
+        if isinstance(st, Dense):
+            st.D = np.ascontiguousarray(self.utsolve(t, st.D.T).T)
+        else:
+            st.V = self.utsolve(t, st.V)
+
     def htrsu(self, t, s):
         b = self.bt.get(s, t)
         if b.is_leaf:
-            st = self.M[b.key]
-            if isinstance(st, Dense):
-                st.D = np.ascontiguousarray(self.utsolve(t, st.D.T).T)
-            else:
-                st.V = self.utsolve(t, st.V)
+            self.leaf_trsu(t, b)
             return
         t0, t1 = t.sons
         s0, s1 = s.sons
