@@ -126,3 +126,63 @@ class AccuHLUFactor(HLUFactor):
         # every collected update reached its leaf
         assert not any(self.acc.values()) and not any(self.pending.values())
         return self
+
+
+class AccuTaskRunner(AccuHLUFactor):
+    """Executes the tasks of the accumulator task graph (§3.2, Table 2) one at a time, in any
+    order that respects the graph's edges; used to check that the graph carries every
+    dependency the accumulator H-LU needs.
+
+    Each task does its own part of Alg 4-8. add_upd ('add', t, r, s) forms the product of the
+    leaf-level operands and appends it to U_ts. Accumulators are pulled down the block tree:
+    shift_upd ('shift', t, s) appends the restriction of the parent's accumulator to U_ts, and
+    apply_upd ('apply', t, s) adds U_ts and the restriction of the parent's accumulator to the
+    leaf in one rounded addition. The leaf tasks ('lu', 'trsl', 'trsu') are the leaf cases of
+    Alg 2 and Alg 3 and its mirror.
+    """
+
+    def __init__(self, hm, parent, eps=None, rank_cap=None):
+        super().__init__(hm, eps, rank_cap)
+        self.parent = parent
+
+    def _pulled(self, key):
+        own = list(self.acc.get(key, []))
+        p = self.parent.get(key)
+        if p is None:
+            return own
+        P, C = self.bt.blocks[p], self.bt.blocks[key]
+        ro, co = C.row.lo - P.row.lo, C.col.lo - P.col.lo
+        m, n = C.row.size, C.col.size
+        for (r0, c0, W, Z) in self.acc.get(p, []):
+            ir0, ir1 = max(r0, ro), min(r0 + W.shape[0], ro + m)
+            ic0, ic1 = max(c0, co), min(c0 + Z.shape[0], co + n)
+            if ir0 < ir1 and ic0 < ic1:
+                own.append((ir0 - ro, ic0 - co, W[ir0 - r0:ir1 - r0], Z[ic0 - c0:ic1 - c0]))
+        return own
+
+    def run(self, task):
+        ty, a, b, c = task
+        if ty == "lu":
+            self.leaf_lu(self.blk(a, a))
+        elif ty == "trsl":
+            self.leaf_trsl(self.cl[a], self.blk(a, b))
+        elif ty == "trsu":
+            self.leaf_trsu(self.cl[a], self.blk(b, a))
+        elif ty == "add":
+            acc = self.acc.setdefault((a, c), [])
+            for (r0, c0, W, Z) in self.product(self.blk(a, b), self.blk(b, c)):
+                acc.append((r0, c0, -W, Z))
+        elif ty == "shift":
+            self.acc[(a, b)] = self._pulled((a, b))
+        elif ty == "apply":
+            C = self.blk(a, b)
+            pieces = self._pulled((a, b))
+            if pieces:
+                self.apply_to_leaf(C, 1.0, pieces, C.row.lo, C.col.lo)
+        else:
+            raise ValueError(f"unknown task {task}")
+
+    def run_all(self, order):
+        for t in order:
+            self.run(t)
+        return self

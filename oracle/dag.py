@@ -192,3 +192,83 @@ def levels(nodes, edges):
     if seen != len(nodes):
         raise ValueError("task graph has a cycle")
     return lev
+
+
+# -- §3.2: the task graph of the accumulator-based H-LU (Table 2, Alg 7, Alg 8) --------------------
+ADD, SHIFT, APPLY = "add", "shift", "apply"
+
+
+class AccuTaskGraphBuilder(TaskGraphBuilder):
+    """Tasks of the accumulator-based H-LU with the data dependencies of Table 2.
+
+    Task tuples: ('lu', t, t, -1), ('trsl', t, s, -1) and ('trsu', t, s, -1) as above;
+    ('add', t, r, s) for add_upd(-1, L_tr, U_rs, A_ts) (refined like hmul, Alg 1);
+    ('shift', t, s, -1) for shift_upd of the block (t, s); ('apply', t, s, -1) for apply_upd of
+    the leaf (t, s).  Every accumulator is a matrix of its own: its identifier is
+    ('acc', t, s), so only dependencies on the same block's accumulator can intersect.
+
+    Readings:
+    * the parent accumulator a task reads (Table 2) is the accumulator of the parent block in the
+      block tree, restricted to the task's own block; the root block has none;
+    * shift_upd and apply_upd appear where Alg 7 / Alg 8 call them: a refined hlu / htrsl /
+      htrsu starts with shift_upd of its block, and every sub-task of those types whose block is
+      a leaf is preceded by apply_upd of that leaf in the sub-task list;
+    * add_upd of three structured blocks refines into the eight products of the sons (what
+      shift_upd does with a pending product), so leaf add_upd tasks are formed exactly where
+      hmul has leaf tasks.
+    """
+
+    def __init__(self, ct, bt):
+        super().__init__(ct, bt)
+        self.parent = {}
+        for b in bt.blocks.values():
+            for row in b.sons:
+                for s in row:
+                    self.parent[s.key] = b.key
+
+    @staticmethod
+    def acc(r, c):
+        return (("acc", r, c), r, c)
+
+    def acc_parent(self, r, c):
+        p = self.parent.get((r, c))
+        return [] if p is None else [(("acc",) + p, r, c)]
+
+    def deps(self, task):
+        ty, a, b, c = task
+        if ty == LU:
+            return [(ID_A, a, a)] + self.acc_parent(a, a), [(ID_L, a, a), (ID_U, a, a)]
+        if ty == TRSL:
+            return [(ID_L, a, a), (ID_A, a, b)] + self.acc_parent(a, b), [(ID_U, a, b)]
+        if ty == TRSU:
+            return [(ID_U, a, a), (ID_A, b, a)] + self.acc_parent(b, a), [(ID_L, b, a)]
+        if ty == ADD:
+            return [(ID_L, a, b), (ID_U, b, c)], [(ID_A, a, c), self.acc(a, c)]
+        if ty == SHIFT:
+            return self.acc_parent(a, b) + [self.acc(a, b)], [self.acc(a, b)]
+        # APPLY
+        return self.acc_parent(a, b) + [self.acc(a, b)], [(ID_A, a, b)]
+
+    def _block_of(self, task):
+        ty, a, b, _ = task
+        return (b, a) if ty == TRSU else (a, b)
+
+    def subtasks(self, task):
+        ty, a, b, c = task
+        if ty in (SHIFT, APPLY):
+            return []
+        if ty == ADD:
+            return [(ADD,) + t[1:] for t in super().subtasks((MUL, a, b, c))]
+        sub = super().subtasks(task)
+        if not sub:
+            return []
+        out = [(SHIFT,) + self._block_of(task) + (-1,)]
+        for t in sub:
+            if t[0] == MUL:
+                out.append((ADD,) + t[1:])
+                continue
+            r, s = self._block_of(t)
+            if self._leaf(r, s):
+                out.append((APPLY, r, s, -1))
+            out.append(t)
+        return out

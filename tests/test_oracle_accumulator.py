@@ -92,3 +92,177 @@ def test_planted_misplaced_restriction_is_caught(monkeypatch):
     monkeypatch.setattr(AccuHLUFactor, "shift_upd", swapped_shift)
     f = AccuHLUFactor(hm).factor()
     assert _rel(hm.exact_dense(), f, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
+
+
+# -- the task graph of the accumulator H-LU (§3.2, Table 2) -------------------------------------------
+import heapq
+from collections import defaultdict
+
+from oracle import dag as D
+from oracle.accu import AccuTaskRunner
+
+
+def _graph(hm, builder=D.AccuTaskGraphBuilder):
+    b = builder(hm.ct, hm.bt)
+    nodes, edges = b.compute_dag()
+    return b, nodes, edges
+
+
+def _level_order(nodes, edges, seed):
+    """Waves in level order, shuffled inside each wave (the order the GPU may take)."""
+    lev = D.levels(nodes, edges)
+    rng = np.random.default_rng(seed)
+    return sorted(nodes, key=lambda t: (lev[t], rng.random()))
+
+
+def _eager_order(nodes, edges, seed):
+    """A topological order that runs accumulator tasks as soon as their edges allow."""
+    rng = np.random.default_rng(seed)
+    indeg, out = defaultdict(int), defaultdict(list)
+    for a, b in edges:
+        out[a].append(b)
+        indeg[b] += 1
+    pri = {t: (0 if t[0] in (D.SHIFT, D.APPLY) else 1, rng.random()) for t in nodes}
+    heap = [(pri[t], t) for t in nodes if indeg[t] == 0]
+    heapq.heapify(heap)
+    order = []
+    while heap:
+        _, t = heapq.heappop(heap)
+        order.append(t)
+        for s in out[t]:
+            indeg[s] -= 1
+            if indeg[s] == 0:
+                heapq.heappush(heap, (pri[s], s))
+    assert len(order) == len(nodes)
+    return order
+
+
+def _ancestors(nodes, edges):
+    """Ancestor sets as bit masks over the node index."""
+    idx = {t: i for i, t in enumerate(nodes)}
+    preds = defaultdict(list)
+    for a, b in edges:
+        preds[b].append(a)
+    anc = {}
+    for t in _level_order(nodes, edges, 0):
+        m = 0
+        for p in preds[t]:
+            m |= anc[p] | (1 << idx[p])
+        anc[t] = m
+    return idx, anc
+
+
+@pytest.mark.parametrize("geom,n", [("sphere", 1024), ("cube", 700)])
+def test_accumulator_graph_tasks(geom, n):
+    """The accumulator graph holds the leaf tasks of the standard graph (hmul leaves become
+    add_upd leaves), one shift_upd per inner block and one apply_upd per leaf block."""
+    hm = HMatrix(W.points_for(geom, n, 21), 64, 2.0, 1e-6, 64)
+    _, nodes, edges = _graph(hm)
+    std, _ = D.TaskGraphBuilder(hm.ct, hm.bt).compute_dag()
+    D.levels(nodes, edges)                       # acyclic
+    renamed = sorted((D.ADD,) + t[1:] if t[0] == D.MUL else t for t in std)
+    assert sorted(t for t in nodes if t[0] not in (D.SHIFT, D.APPLY)) == renamed
+    acc = sorted(t for t in nodes if t[0] in (D.SHIFT, D.APPLY))
+    blocks = sorted(((D.APPLY if b.is_leaf else D.SHIFT), b.row.id, b.col.id, -1)
+                    for b in hm.bt.blocks.values())
+    assert acc == blocks
+
+
+def test_accumulator_graph_hierarchy_and_updates():
+    """Updates reach the leaves top-down (the parent's shift_upd precedes the sons' shift_upd /
+    apply_upd), every add_upd into a block precedes the apply_upd of every leaf below it, and
+    the apply_upd of a leaf precedes the task that factorises or solves with it."""
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-6, 64)
+    b, nodes, edges = _graph(hm)
+    idx, anc = _ancestors(nodes, edges)
+    acc_task = {(t[1], t[2]): t for t in nodes if t[0] in (D.SHIFT, D.APPLY)}
+    for child, par in b.parent.items():
+        assert anc[acc_task[child]] >> idx[acc_task[par]] & 1, (par, child)
+    for t in nodes:
+        if t[0] == D.ADD:
+            for leaf in hm.bt.leaves_under(hm.bt.blocks[(t[1], t[3])]):
+                assert anc[acc_task[leaf.key]] >> idx[t] & 1, (t, leaf.key)
+        elif t[0] in (D.LU, D.TRSL, D.TRSU) and len(nodes) > 1:
+            key = (t[2], t[1]) if t[0] == D.TRSU else (t[1], t[2])
+            assert anc[t] >> idx[acc_task[key]] & 1, t
+
+
+@pytest.mark.parametrize("geom,n,eps", [("sphere", 1024, 1e-10), ("cube", 700, 1e-6)])
+def test_accumulator_graph_execution_equals_recursion(geom, n, eps):
+    """Running the graph's tasks one by one, in level order shuffled inside each level and in an
+    order that runs accumulator tasks as early as the edges allow, gives the recursive
+    accumulator H-LU (same truncations, same factors up to the order of the stacked pieces)."""
+    hm = HMatrix(W.points_for(geom, n, 21), 64, 2.0, eps, 64)
+    b, nodes, edges = _graph(hm)
+    A = hm.exact_dense()
+    X = np.random.default_rng(3).standard_normal((hm.n, 4))
+    ref = AccuHLUFactor(hm).factor()
+    for order in (_level_order(nodes, edges, 5), _eager_order(nodes, edges, 6)):
+        run = AccuTaskRunner(hm, b.parent).run_all(order)
+        assert run.stats.truncations == ref.stats.truncations
+        assert np.linalg.norm(run.apply_lu(X) - ref.apply_lu(X)) / np.linalg.norm(A @ X) < 100 * eps
+        assert _rel(A, run, X) <= 10 * eps
+
+
+def test_accumulator_graph_literal_and_sparse_readings_have_equal_levels():
+    """Table 2 lets add_upd write the global block as well as its accumulator; without that output
+    (and with the factorisation and solve tasks reading their own block's accumulator) the graph
+    has fewer edges but the same longest-path level for every task: the extra edges are implied."""
+
+    class Sparse(D.AccuTaskGraphBuilder):
+        def deps(self, task):
+            i, o = super().deps(task)
+            ty, a, _, c = task
+            if ty == D.ADD:
+                o = [self.acc(a, c)]
+            elif ty in (D.LU, D.TRSL, D.TRSU):
+                i = i + [self.acc(*self._block_of(task))]
+            return i, o
+
+    hm = HMatrix(W.fibonacci_sphere(2048, 11), 64, 2.0, 1e-6, 64)
+    _, n1, e1 = _graph(hm)
+    _, n2, e2 = _graph(hm, Sparse)
+    assert sorted(n1) == sorted(n2) and len(e2) < len(e1)
+    l1, l2 = D.levels(n1, e1), D.levels(n2, e2)
+    assert all(l1[t] == l2[t] for t in n1)
+
+
+def test_planted_apply_without_parent_accumulator_is_caught(monkeypatch):
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-10, 64)
+    orig = D.AccuTaskGraphBuilder.deps
+
+    def deps(self, task):
+        i, o = orig(self, task)
+        return ([self.acc(task[1], task[2])] if task[0] == D.APPLY else i), o
+
+    monkeypatch.setattr(D.AccuTaskGraphBuilder, "deps", deps)
+    b, nodes, edges = _graph(hm)
+    run = AccuTaskRunner(hm, b.parent).run_all(_level_order(nodes, edges, 5))
+    assert _rel(hm.exact_dense(), run, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
+
+
+def test_planted_shift_without_parent_accumulator_is_caught(monkeypatch):
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-6, 64)
+    orig = D.AccuTaskGraphBuilder.deps
+
+    def deps(self, task):
+        i, o = orig(self, task)
+        return ([self.acc(task[1], task[2])] if task[0] == D.SHIFT else i), o
+
+    monkeypatch.setattr(D.AccuTaskGraphBuilder, "deps", deps)
+    with pytest.raises(AssertionError):
+        test_accumulator_graph_hierarchy_and_updates()
+
+
+def test_planted_add_without_accumulator_output_is_caught(monkeypatch):
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-10, 64)
+    orig = D.AccuTaskGraphBuilder.deps
+
+    def deps(self, task):
+        i, o = orig(self, task)
+        return i, (o[:1] if task[0] == D.ADD else o)
+
+    monkeypatch.setattr(D.AccuTaskGraphBuilder, "deps", deps)
+    b, nodes, edges = _graph(hm)
+    run = AccuTaskRunner(hm, b.parent).run_all(_eager_order(nodes, edges, 6))
+    assert _rel(hm.exact_dense(), run, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
