@@ -197,12 +197,20 @@ typedef struct {
  * longest-path levels. points: host n x 3. with_plan != 0 also runs the H-LU planner. */
 int hm_structure_build(const double* points_xyz, int64_t n, int leaf_size, double eta, int with_plan,
                        hm_structure** out);
+/* The same trees with the task graph of the accumulator-based H-LU (§3.2, Table 2; Alg 4-8):
+ * a refined hlu / htrsl / htrsu starts with shift_upd of its block, apply_upd of a leaf precedes
+ * the task that factorises or solves with it, add_upd (task type 1) is refined like hmul (Alg 1)
+ * and writes the block and its accumulator; shift_upd and apply_upd read the accumulator of the
+ * parent block. No plan (the executor runs the graph of Alg 11). Errors as hm_structure_build. */
+int hm_structure_build_accumulator(const double* points_xyz, int64_t n, int leaf_size, double eta,
+                                   hm_structure** out);
 int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
 /* Export (any pointer may be NULL):
  *   perm[n]                 original index of each permuted position
  *   clusters[nclusters*6]   lo, hi, son0, son1, level, parent (depth-first pre-order ids)
  *   leaves[nleaves*3]       row cluster, col cluster, admissible (block-tree pre-order)
- *   tasks[ntasks*4]         type (0 lu, 1 mul, 2 trsl, 3 trsu), c1, c2, c3 (-1 unused)
+ *   tasks[ntasks*4]         type (0 lu, 1 mul / add_upd, 2 trsl, 3 trsu, 4 shift_upd, 5 apply_upd),
+ *                           c1, c2, c3 (-1 unused)
  *   edges[nedges*2]         src, dst task indices
  *   levels[ntasks]          longest-path level of each task */
 int hm_structure_export(const hm_structure* S, int64_t* perm, int32_t* clusters, int32_t* leaves,

@@ -24,7 +24,7 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
-    "hm_structure_build", "header_functions",
+    "hm_structure_build", "hm_structure_build_accumulator", "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
 ]
 
@@ -133,6 +133,7 @@ def load_library():
         "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
+        "hm_structure_build_accumulator": ([P, I64, I, D, PP], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
         "hm_structure_export": ([P, P, P, P, P, P, P], I),
         "hm_structure_free": ([P], V),
@@ -379,6 +380,14 @@ class Structure:
                 self.handle = None
         except Exception:
             pass
+
+
+def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0):
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load_library().hm_structure_build_accumulator(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
+                                                         ctypes.byref(h)))
+    return Structure(h)
 
 
 def hm_structure_build(points, leaf_size=64, eta=2.0, with_plan=False):

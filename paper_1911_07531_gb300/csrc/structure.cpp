@@ -147,10 +147,11 @@ void collect_leaves(const BlockTree& bt, int node, std::vector<int>& out) {
   for (int q = 0; q < 4; ++q) collect_leaves(bt, b.sons[q], out);
 }
 
-// ------------------------------------------------------------------ task graph (§3.1)
+// ------------------------------------------------------------------ task graph (§3.1, §3.2)
 namespace {
 
-enum { ID_A = 0, ID_L = 1, ID_U = 2 };
+// Matrix identifiers of H-LU; the accumulator of block-tree node b has identifier ID_ACC + b.
+enum { ID_A = 0, ID_L = 1, ID_U = 2, ID_ACC = 3 };
 
 struct Dep {
   int id, r, c;
@@ -159,27 +160,53 @@ struct Dep {
 struct DagBuilder {
   const ClusterTree& ct;
   const BlockTree& bt;
+  const bool accu;               // accumulator H-LU (§3.2, Table 2) instead of Table 1
   std::vector<Task> tasks;
   std::vector<std::vector<int>> succ;
   std::vector<int> sub_first, sub_count;
+  std::vector<int> acc_self, acc_par;   // accumulator ids of a task's block and of its parent block
+  std::vector<int> parent_node;         // block-tree parent of each node, -1 at the root
 
-  DagBuilder(const ClusterTree& c, const BlockTree& b) : ct(c), bt(b) {}
-
-  // Table 1 with the identifiers H-LU passes (Alg 2 / Alg 3 arguments).
-  static int ins(const Task& t, Dep* d) {
-    switch (t.type) {
-      case T_LU: d[0] = {ID_A, t.a, t.a}; return 1;
-      case T_TRSL: d[0] = {ID_L, t.a, t.a}; d[1] = {ID_A, t.a, t.b}; return 2;
-      case T_TRSU: d[0] = {ID_U, t.a, t.a}; d[1] = {ID_A, t.b, t.a}; return 2;
-      default: d[0] = {ID_L, t.a, t.b}; d[1] = {ID_U, t.b, t.c}; return 2;
+  DagBuilder(const ClusterTree& c, const BlockTree& b, bool accumulators) : ct(c), bt(b), accu(accumulators) {
+    if (accu) {
+      parent_node.assign(bt.nodes.size(), -1);
+      for (size_t i = 0; i < bt.nodes.size(); ++i)
+        for (int q = 0; q < 4; ++q)
+          if (bt.nodes[i].sons[q] >= 0) parent_node[bt.nodes[i].sons[q]] = (int)i;
     }
   }
-  static int outs(const Task& t, Dep* d) {
+
+  // Table 1 (and Table 2 in accumulator mode) with the identifiers H-LU passes (Alg 2 / Alg 3
+  // and Alg 7 / Alg 8 arguments). T_MUL stands for hmul, or for add_upd in accumulator mode.
+  int ins(int k, Dep* d) const {
+    const Task& t = tasks[k];
+    int n = 0;
+    switch (t.type) {
+      case T_LU: d[n++] = {ID_A, t.a, t.a}; break;
+      case T_TRSL: d[n++] = {ID_L, t.a, t.a}; d[n++] = {ID_A, t.a, t.b}; break;
+      case T_TRSU: d[n++] = {ID_U, t.a, t.a}; d[n++] = {ID_A, t.b, t.a}; break;
+      case T_MUL: d[n++] = {ID_L, t.a, t.b}; d[n++] = {ID_U, t.b, t.c}; return n;
+      default: d[n++] = {ID_ACC + acc_self[k], t.a, t.b}; break;   // shift_upd, apply_upd
+    }
+    if (accu && acc_par[k] >= 0) {
+      int r = t.type == T_TRSU ? t.b : t.a, c = t.type == T_TRSU ? t.a : t.b;
+      d[n++] = {ID_ACC + acc_par[k], r, c};
+    }
+    return n;
+  }
+  int outs(int k, Dep* d) const {
+    const Task& t = tasks[k];
     switch (t.type) {
       case T_LU: d[0] = {ID_L, t.a, t.a}; d[1] = {ID_U, t.a, t.a}; return 2;
       case T_TRSL: d[0] = {ID_U, t.a, t.b}; return 1;
       case T_TRSU: d[0] = {ID_L, t.b, t.a}; return 1;
-      default: d[0] = {ID_A, t.a, t.c}; return 1;
+      case T_MUL:
+        d[0] = {ID_A, t.a, t.c};
+        if (!accu) return 1;
+        d[1] = {ID_ACC + acc_self[k], t.a, t.c};
+        return 2;
+      case T_SHIFT: d[0] = {ID_ACC + acc_self[k], t.a, t.b}; return 1;
+      default: d[0] = {ID_A, t.a, t.b}; return 1;   // apply_upd
     }
   }
   bool overlap(int x, int y) const {
@@ -190,8 +217,8 @@ struct DagBuilder {
   // Def 3.2
   bool precedes(int i, int j) const {
     if (i == j) return false;
-    Dep o[2], in[2];
-    int no = outs(tasks[i], o), ni = ins(tasks[j], in);
+    Dep o[2], in[3];
+    int no = outs(i, o), ni = ins(j, in);
     for (int p = 0; p < no; ++p)
       for (int q = 0; q < ni; ++q)
         if (o[p].id == in[q].id && overlap(o[p].r, in[q].r) && overlap(o[p].c, in[q].c)) return true;
@@ -206,41 +233,62 @@ struct DagBuilder {
     succ.emplace_back();
     sub_first.push_back(-1);
     sub_count.push_back(0);
+    if (accu) {
+      int r = a, s = b;
+      if (type == T_TRSU) r = b, s = a;
+      if (type == T_MUL) s = c;
+      int node = bt.find(r, s);
+      acc_self.push_back(node);
+      acc_par.push_back(parent_node[node]);
+    }
     return (int)tasks.size() - 1;
   }
-  // recursive bodies of Alg 2, Alg 3, its upper mirror and Alg 1, in program order
+  // accumulator mode: apply_upd of a leaf before the task that factorises or solves with it
+  void add_sub(int type, int a, int b, int c) {
+    if (accu && type != T_MUL) {
+      int r = type == T_TRSU ? b : a, s = type == T_TRSU ? a : b;
+      if (leaf_block(r, s)) add(T_APPLY, r, s, -1);
+    }
+    add(type, a, b, c);
+  }
+  // recursive bodies of Alg 2, Alg 3, its upper mirror and Alg 1 (Alg 7, Alg 8 and its mirror,
+  // Alg 4 in accumulator mode), in program order
   void generate(int g) {
     Task t = tasks[g];
+    if (t.type == T_SHIFT || t.type == T_APPLY) return;
     int first = (int)tasks.size();
     const Cluster& A = ct.cl[t.a];
     if (t.type == T_LU) {
       if (leaf_block(t.a, t.a)) return;
       int t0 = A.son0, t1 = A.son1;
-      add(T_LU, t0, t0, -1);
-      add(T_TRSU, t0, t1, -1);
-      add(T_TRSL, t0, t1, -1);
-      add(T_MUL, t1, t0, t1);
-      add(T_LU, t1, t1, -1);
+      if (accu) add(T_SHIFT, t.a, t.a, -1);
+      add_sub(T_LU, t0, t0, -1);
+      add_sub(T_TRSU, t0, t1, -1);
+      add_sub(T_TRSL, t0, t1, -1);
+      add_sub(T_MUL, t1, t0, t1);
+      add_sub(T_LU, t1, t1, -1);
     } else if (t.type == T_TRSL) {
       if (leaf_block(t.a, t.b)) return;
       const Cluster& S = ct.cl[t.b];
       int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
-      add(T_TRSL, t0, s0, -1);
-      add(T_TRSL, t0, s1, -1);
-      add(T_MUL, t1, t0, s0);
-      add(T_MUL, t1, t0, s1);
-      add(T_TRSL, t1, s0, -1);
-      add(T_TRSL, t1, s1, -1);
+      if (accu) add(T_SHIFT, t.a, t.b, -1);
+      add_sub(T_TRSL, t0, s0, -1);
+      add_sub(T_TRSL, t0, s1, -1);
+      add_sub(T_MUL, t1, t0, s0);
+      add_sub(T_MUL, t1, t0, s1);
+      add_sub(T_TRSL, t1, s0, -1);
+      add_sub(T_TRSL, t1, s1, -1);
     } else if (t.type == T_TRSU) {
       if (leaf_block(t.b, t.a)) return;
       const Cluster& S = ct.cl[t.b];
       int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
-      add(T_TRSU, t0, s0, -1);
-      add(T_TRSU, t0, s1, -1);
-      add(T_MUL, s0, t0, t1);
-      add(T_MUL, s1, t0, t1);
-      add(T_TRSU, t1, s0, -1);
-      add(T_TRSU, t1, s1, -1);
+      if (accu) add(T_SHIFT, t.b, t.a, -1);
+      add_sub(T_TRSU, t0, s0, -1);
+      add_sub(T_TRSU, t0, s1, -1);
+      add_sub(T_MUL, s0, t0, t1);
+      add_sub(T_MUL, s1, t0, t1);
+      add_sub(T_TRSU, t1, s0, -1);
+      add_sub(T_TRSU, t1, s1, -1);
     } else {
       if (leaf_block(t.a, t.b) || leaf_block(t.b, t.c) || leaf_block(t.a, t.c)) return;
       const Cluster& R = ct.cl[t.b];
@@ -262,11 +310,11 @@ struct DagBuilder {
 
 }  // namespace
 
-void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g) {
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators) {
   auto t0 = std::chrono::steady_clock::now();
   g = TaskGraph();
   if (ct.cl.empty()) return;
-  DagBuilder b(ct, bt);
+  DagBuilder b(ct, bt, accumulators);
   b.tasks.reserve(1 << 16);
   int root = b.add(T_LU, 0, 0, -1);
   std::vector<int> work{root}, next;

@@ -3,7 +3,8 @@
 //  * cluster tree by geometric bisection (Def 2.1), standard admissibility (§5.1),
 //    block tree (Def 2.2);
 //  * the H-LU task graph built by semi-automatic refinement (§3.1: Table 1, Def 3.2,
-//    Alg 9, Alg 10, Alg 11) and its longest-path levels (the waves the GPU executes).
+//    Alg 9, Alg 10, Alg 11) and its longest-path levels (the waves the GPU executes), and the
+//    task graph of the accumulator-based H-LU (§3.2, Table 2).
 //
 // All of it is integer and comparison work in FP64 with a fixed operation order; it is
 // compiled without floating-point contraction so that the admissibility decisions are
@@ -54,12 +55,13 @@ struct BlockTree {
   }
 };
 
-enum TaskType : int { T_LU = 0, T_MUL = 1, T_TRSL = 2, T_TRSU = 3 };
+enum TaskType : int { T_LU = 0, T_MUL = 1, T_TRSL = 2, T_TRSU = 3, T_SHIFT = 4, T_APPLY = 5 };
 
 struct Task {
   int type;
   int a, b, c;   // lu: (t,t,-1); trsl: (t,s,-1) L_tt X_ts = M_ts; trsu: (t,s,-1) X_st U_tt = M_st;
-                 // mul: (t,r,s) C_ts -= A_tr B_rs
+                 // mul: (t,r,s) C_ts -= A_tr B_rs (add_upd in the accumulator graph);
+                 // shift / apply: (t,s,-1) shift_upd / apply_upd of the block (t,s)
 };
 
 struct TaskGraph {
@@ -75,8 +77,11 @@ bool admissible(const Cluster& t, const Cluster& s, double eta);
 void build_block_tree(const ClusterTree& ct, double eta, BlockTree& bt);
 void collect_leaves(const BlockTree& bt, int node, std::vector<int>& out);
 
-// Alg 11 started from hlu(A, L, U) on the root cluster.
-void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g);
+// Alg 11 started from hlu(A, L, U) on the root cluster. accumulators: the task graph of the
+// accumulator-based H-LU (§3.2, Table 2) -- a refined hlu / htrsl / htrsu starts with
+// shift_upd of its block, apply_upd of a leaf precedes the task that factorises or solves with
+// it, add_upd is refined like hmul and writes the block and its accumulator.
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators = false);
 // longest-path levels; returns false if the graph has a cycle
 bool compute_levels(TaskGraph& g);
 

@@ -77,6 +77,34 @@ def test_structure_degenerate_inputs(lib):
         hm.hm_structure_build(np.zeros((10, 3)), 0, 2.0)
 
 
+ACC_TYPES = {0: D.LU, 1: D.ADD, 2: D.TRSL, 3: D.TRSU, 4: D.SHIFT, 5: D.APPLY}
+
+
+@pytest.mark.parametrize("geom,n,eta", [("line", 512, 0.0), ("sphere", 2048, 2.0), ("cube", 3000, 2.0),
+                                        ("ellipsoid", 1500, 2.0)])
+def test_accumulator_graph_bit_exact_with_oracle(lib, geom, n, eta):
+    """The library's accumulator task graph (§3.2, Table 2) equals the oracle's: tasks, edges, levels."""
+    points = W.points_for(geom, n, 21)
+    S = hm.hm_structure_build_accumulator(points, 64, eta).export()
+    ct = ClusterTree(points, 64)
+    bt = BlockTree(ct, eta)
+    nodes, edges = D.AccuTaskGraphBuilder(ct, bt).compute_dag()
+    tasks = [(ACC_TYPES[t[0]], t[1], t[2], t[3]) for t in S["tasks"].tolist()]
+    assert sorted(tasks) == sorted(nodes)
+    e_lib = {(tasks[s], tasks[d]) for s, d in S["edges"].tolist()}
+    assert len(e_lib) == len(S["edges"])
+    assert e_lib == set(edges)
+    lev = D.levels(nodes, edges)
+    assert all(lev[t] == S["levels"][i] for i, t in enumerate(tasks))
+
+
+def test_accumulator_graph_single_leaf(lib):
+    S = hm.hm_structure_build_accumulator(np.zeros((1, 3)), 64, 2.0).export()
+    assert S["tasks"].tolist() == [[0, 0, 0, -1]] and len(S["edges"]) == 0
+    with pytest.raises(hm.HMError):
+        hm.hm_structure_build_accumulator(np.zeros((10, 3)), 65, 2.0)
+
+
 def test_plan_builds_on_host(lib):
     S = hm.hm_structure_build(W.fibonacci_sphere(4096, 11), 64, 2.0, with_plan=True)
     i = S.info
