@@ -197,12 +197,17 @@ typedef struct {
  * longest-path levels. points: host n x 3. with_plan != 0 also runs the H-LU planner. */
 int hm_structure_build(const double* points_xyz, int64_t n, int leaf_size, double eta, int with_plan,
                        hm_structure** out);
-/* The same trees with the task graph of the accumulator-based H-LU (§3.2, Table 2; Alg 4-8):
- * a refined hlu / htrsl / htrsu starts with shift_upd of its block, apply_upd of a leaf precedes
- * the task that factorises or solves with it, add_upd (task type 1) is refined like hmul (Alg 1)
- * and writes the block and its accumulator; shift_upd and apply_upd read the accumulator of the
- * parent block. No plan (the executor runs the graph of Alg 11). Errors as hm_structure_build. */
-int hm_structure_build_accumulator(const double* points_xyz, int64_t n, int leaf_size, double eta,
+/* The same trees with the task graph of the accumulator-based H-LU (Alg 4-8).
+ * merged == 0: semi-automatic refinement with the dependencies of Table 2 (§3.2): a refined
+ *   hlu / htrsl / htrsu starts with shift_upd of its block, apply_upd of a leaf precedes the task
+ *   that factorises or solves with it, add_upd (task type 1) is refined like hmul (Alg 1) and
+ *   writes the block and its accumulator; the other tasks read the parent block's accumulator.
+ * merged != 0: the two-part construction of §4.3: the standard graph of Alg 11 (hmul tasks as
+ *   add_upd) plus one shift_upd / apply_upd task per block-tree node, linked by explicit edges
+ *   (parent -> son accumulator task, add_upd -> accumulator task of its destination, apply_upd
+ *   of a leaf -> the leaf task). Same tasks, fewer edges; a single-leaf matrix gets an apply_upd.
+ * No plan. Errors as hm_structure_build. */
+int hm_structure_build_accumulator(const double* points_xyz, int64_t n, int leaf_size, double eta, int merged,
                                    hm_structure** out);
 int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
 /* Export (any pointer may be NULL):

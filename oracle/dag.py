@@ -272,3 +272,31 @@ class AccuTaskGraphBuilder(TaskGraphBuilder):
                 out.append((APPLY, r, s, -1))
             out.append(t)
         return out
+
+
+def merged_accumulator_dag(ct, bt):
+    """The accumulator task graph built in two parts and linked explicitly (§4.3).
+
+    First the accumulator handling alone: one shift_upd per inner block and one apply_upd per
+    leaf block, with an edge from the task of every block to the tasks of its sons (the parent's
+    accumulator is complete before a son takes its share). Then the standard H-LU graph (Alg 11
+    with Table 1; hmul tasks become add_upd), to which two kinds of edges are added: from every
+    add_upd to the accumulator task of its destination block, and from the apply_upd of a leaf to
+    the task that factorises or solves with that leaf.
+    """
+    nodes, edges = TaskGraphBuilder(ct, bt).compute_dag()
+    ren = {t: ((ADD,) + t[1:] if t[0] == MUL else t) for t in nodes}
+    acc = {key: ((SHIFT if b.sons else APPLY), key[0], key[1], -1) for key, b in bt.blocks.items()}
+    out_nodes = [ren[t] for t in nodes] + list(acc.values())
+    out_edges = [(ren[a], ren[b]) for a, b in edges]
+    for key, b in bt.blocks.items():
+        for row in b.sons:
+            for s in row:
+                out_edges.append((acc[key], acc[s.key]))
+    for t in out_nodes:
+        ty, a, b, c = t
+        if ty == ADD:
+            out_edges.append((t, acc[(a, c)]))
+        elif ty in (LU, TRSL, TRSU):
+            out_edges.append((acc[(b, a) if ty == TRSU else (a, b)], t))
+    return out_nodes, out_edges

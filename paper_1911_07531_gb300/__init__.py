@@ -133,7 +133,7 @@ def load_library():
         "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
-        "hm_structure_build_accumulator": ([P, I64, I, D, PP], I),
+        "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
         "hm_structure_export": ([P, P, P, P, P, P, P], I),
         "hm_structure_free": ([P], V),
@@ -382,11 +382,11 @@ class Structure:
             pass
 
 
-def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0):
+def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0, merged=False):
     p = np.ascontiguousarray(points, dtype=np.float64)
     h = ctypes.c_void_p()
     _check(load_library().hm_structure_build_accumulator(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
-                                                         ctypes.byref(h)))
+                                                         int(bool(merged)), ctypes.byref(h)))
     return Structure(h)
 
 

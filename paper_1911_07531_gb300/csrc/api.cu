@@ -1017,7 +1017,8 @@ int hm_structure_build(const double* pts, int64_t n, int leaf_size, double eta, 
   return HM_OK;
 }
 
-int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, double eta, hm_structure** out) {
+int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, double eta, int merged,
+                                   hm_structure** out) {
   if (!pts || !out || n < 1) return fail(HM_EINVAL, "hm_structure_build_accumulator: bad argument");
   if (leaf_size < 1 || leaf_size > 64)
     return fail(HM_EINVAL, "hm_structure_build_accumulator: leaf_size must be in 1..64");
@@ -1026,7 +1027,10 @@ int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, 
   try {
     build_cluster_tree(pts, n, leaf_size, S->ct);
     build_block_tree(S->ct, eta, S->bt);
-    build_task_graph(S->ct, S->bt, S->g, true);
+    if (merged)
+      build_merged_accumulator_graph(S->ct, S->bt, S->g);
+    else
+      build_task_graph(S->ct, S->bt, S->g, true);
     if (!compute_levels(S->g)) return fail(HM_EINTERNAL, "hm_structure_build_accumulator: task graph has a cycle");
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_structure_build_accumulator: ") + ex.what());

@@ -381,6 +381,34 @@ void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, 
   g.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+void build_merged_accumulator_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g) {
+  auto t0 = std::chrono::steady_clock::now();
+  build_task_graph(ct, bt, g, false);
+  if (g.nodes.empty()) return;
+  const int nlu = (int)g.nodes.size();
+  // the accumulator handling alone: one task per block-tree node, parent -> sons
+  std::vector<int> acc_task(bt.nodes.size());
+  for (size_t i = 0; i < bt.nodes.size(); ++i) {
+    const BlockNode& b = bt.nodes[i];
+    acc_task[i] = (int)g.nodes.size();
+    g.nodes.push_back({b.is_leaf() ? T_APPLY : T_SHIFT, b.row, b.col, -1});
+  }
+  for (size_t i = 0; i < bt.nodes.size(); ++i)
+    for (int q = 0; q < 4; ++q)
+      if (bt.nodes[i].sons[q] >= 0) g.edges.emplace_back(acc_task[i], acc_task[bt.nodes[i].sons[q]]);
+  // links: add_upd -> accumulator task of its destination; apply_upd of a leaf -> its leaf task
+  for (int k = 0; k < nlu; ++k) {
+    const Task& t = g.nodes[k];
+    if (t.type == T_MUL) {
+      g.edges.emplace_back(k, acc_task[bt.find(t.a, t.c)]);
+    } else {
+      int r = t.type == T_TRSU ? t.b : t.a, c = t.type == T_TRSU ? t.a : t.b;
+      g.edges.emplace_back(acc_task[bt.find(r, c)], k);
+    }
+  }
+  g.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
 bool compute_levels(TaskGraph& g) {
   size_t n = g.nodes.size();
   std::vector<int> indeg(n, 0), start(n + 1, 0), adj(g.edges.size());

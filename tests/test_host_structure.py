@@ -82,13 +82,18 @@ ACC_TYPES = {0: D.LU, 1: D.ADD, 2: D.TRSL, 3: D.TRSU, 4: D.SHIFT, 5: D.APPLY}
 
 @pytest.mark.parametrize("geom,n,eta", [("line", 512, 0.0), ("sphere", 2048, 2.0), ("cube", 3000, 2.0),
                                         ("ellipsoid", 1500, 2.0)])
-def test_accumulator_graph_bit_exact_with_oracle(lib, geom, n, eta):
-    """The library's accumulator task graph (§3.2, Table 2) equals the oracle's: tasks, edges, levels."""
+@pytest.mark.parametrize("merged", [False, True])
+def test_accumulator_graph_bit_exact_with_oracle(lib, geom, n, eta, merged):
+    """The library's accumulator task graphs (§3.2 with Table 2; the merged graph of §4.3) equal
+    the oracle's: tasks, edges, levels."""
     points = W.points_for(geom, n, 21)
-    S = hm.hm_structure_build_accumulator(points, 64, eta).export()
+    S = hm.hm_structure_build_accumulator(points, 64, eta, merged).export()
     ct = ClusterTree(points, 64)
     bt = BlockTree(ct, eta)
-    nodes, edges = D.AccuTaskGraphBuilder(ct, bt).compute_dag()
+    if merged:
+        nodes, edges = D.merged_accumulator_dag(ct, bt)
+    else:
+        nodes, edges = D.AccuTaskGraphBuilder(ct, bt).compute_dag()
     tasks = [(ACC_TYPES[t[0]], t[1], t[2], t[3]) for t in S["tasks"].tolist()]
     assert sorted(tasks) == sorted(nodes)
     e_lib = {(tasks[s], tasks[d]) for s, d in S["edges"].tolist()}
@@ -101,6 +106,8 @@ def test_accumulator_graph_bit_exact_with_oracle(lib, geom, n, eta):
 def test_accumulator_graph_single_leaf(lib):
     S = hm.hm_structure_build_accumulator(np.zeros((1, 3)), 64, 2.0).export()
     assert S["tasks"].tolist() == [[0, 0, 0, -1]] and len(S["edges"]) == 0
+    S = hm.hm_structure_build_accumulator(np.zeros((1, 3)), 64, 2.0, merged=True).export()
+    assert S["tasks"].tolist() == [[0, 0, 0, -1], [5, 0, 0, -1]] and S["edges"].tolist() == [[1, 0]]
     with pytest.raises(hm.HMError):
         hm.hm_structure_build_accumulator(np.zeros((10, 3)), 65, 2.0)
 

@@ -266,3 +266,40 @@ def test_planted_add_without_accumulator_output_is_caught(monkeypatch):
     b, nodes, edges = _graph(hm)
     run = AccuTaskRunner(hm, b.parent).run_all(_eager_order(nodes, edges, 6))
     assert _rel(hm.exact_dense(), run, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
+
+
+# -- the merged accumulator graph (§4.3) ---------------------------------------------------------------
+@pytest.mark.parametrize("geom,n,eta", [("sphere", 2048, 2.0), ("cube", 3000, 2.0), ("line", 512, 0.0)])
+def test_merged_graph_same_tasks_fewer_edges_same_levels(geom, n, eta):
+    """The merged graph has the tasks of the semi-automatic accumulator graph, fewer edges (the
+    point of §4.3) and the same longest-path level for every task, so the same waves."""
+    hm = HMatrix(W.points_for(geom, n, 21), 64, eta, 1e-6, 64)
+    _, n1, e1 = _graph(hm)
+    n2, e2 = D.merged_accumulator_dag(hm.ct, hm.bt)
+    assert sorted(n1) == sorted(n2) and len(set(e2)) == len(e2) < len(e1)
+    l1, l2 = D.levels(n1, e1), D.levels(n2, e2)
+    assert all(l1[t] == l2[t] for t in n1)
+
+
+def test_merged_graph_execution_equals_recursion():
+    hm = HMatrix(W.cube_surface(700, 21), 64, 2.0, 1e-6, 64)
+    b = D.AccuTaskGraphBuilder(hm.ct, hm.bt)
+    nodes, edges = D.merged_accumulator_dag(hm.ct, hm.bt)
+    A = hm.exact_dense()
+    X = np.random.default_rng(3).standard_normal((hm.n, 4))
+    ref = AccuHLUFactor(hm).factor()
+    for order in (_level_order(nodes, edges, 7), _eager_order(nodes, edges, 8)):
+        run = AccuTaskRunner(hm, b.parent).run_all(order)
+        assert run.stats.truncations == ref.stats.truncations
+        assert np.linalg.norm(run.apply_lu(X) - ref.apply_lu(X)) / np.linalg.norm(A @ X) < 1e-4
+        assert _rel(A, run, X) <= 1e-5
+
+
+def test_planted_merged_graph_without_add_links_is_caught(monkeypatch):
+    """Without the add_upd -> accumulator-task links an eager order applies accumulators early."""
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-10, 64)
+    nodes, edges = D.merged_accumulator_dag(hm.ct, hm.bt)
+    edges = [(a, b) for a, b in edges if not (a[0] == D.ADD and b[0] in (D.SHIFT, D.APPLY))]
+    b = D.AccuTaskGraphBuilder(hm.ct, hm.bt)
+    run = AccuTaskRunner(hm, b.parent).run_all(_eager_order(nodes, edges, 6))
+    assert _rel(hm.exact_dense(), run, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
