@@ -8,6 +8,11 @@ Before a block is factorised or solved with, its accumulated updates are shifted
 sub-blocks (shift_upd) at each recursive step, and a leaf adds its accumulator once
 (apply_upd) before the dense factorisation or solve.
 
+Three accumulator formats are provided (§2.3 leaves the format open): a list of pieces
+(AccuHLUFactor, the reference form used by the task runner), a factorised low-rank matrix
+rounded at every addition (LowRankAccuHLUFactor), and a list of pieces compressed once per
+structured block when shifted to the sons (CoarseAccuHLUFactor).
+
 Readings (the paper leaves these open or prints them garbled):
 
 * Storage of an accumulator: the list of its pieces W Z^T on sub-blocks of (t, s) (the paper
@@ -22,7 +27,10 @@ Readings (the paper leaves these open or prints them garbled):
 """
 from __future__ import annotations
 
+import numpy as np
+
 from .hlu import HLUFactor
+from .hmatrix import Dense, truncate
 
 
 class AccuHLUFactor(HLUFactor):
@@ -186,3 +194,99 @@ class AccuTaskRunner(AccuHLUFactor):
         for t in order:
             self.run(t)
         return self
+
+
+class LowRankAccuHLUFactor(AccuHLUFactor):
+    """Accumulator H-LU with accumulators in factorised low-rank form (§2.3 names it the default
+    format): U_ts is a matrix U V^T over the whole block (t, s), every addition to it is a
+    rounded addition at the factorization's eps (no rank cap: an accumulator of a large block
+    may need more than the cap of a leaf), shift_upd adds the restriction of the parent's U V^T
+    to the son's accumulator (a rounded addition when the son's is not empty), and apply_upd
+    adds the accumulator to the leaf. A dense leaf keeps a dense accumulator (no rounding).
+
+    Counts every rounded addition in ``stats.truncations``.
+    """
+
+    def _dense_leaf(self, C):
+        return C.is_leaf and isinstance(self.M[C.key], Dense)
+
+    def _add_lr(self, C, U, V):
+        """U_C := U_C + U V^T (U, V over the whole block C)."""
+        old = self.acc.get(C.key)
+        if self._dense_leaf(C):
+            self.acc[C.key] = (U @ V.T) if old is None else old + U @ V.T
+            return
+        if old is not None:
+            U, V = np.hstack([old[0], U]), np.hstack([old[1], V])
+        cap = min(C.row.size, C.col.size)
+        self.acc[C.key] = truncate(U, V, self.eps, cap, self.stats)
+
+    def add_upd(self, alpha, A, B, C):
+        if not (A.is_leaf or B.is_leaf or C.is_leaf):
+            self.pending.setdefault(C.key, []).append((alpha, A, B))
+            return
+        m, n = C.row.size, C.col.size
+        Ws, Zs = [], []
+        for (r0, c0, W, Z) in self.product(A, B):
+            Wp = np.zeros((m, W.shape[1]))
+            Zp = np.zeros((n, Z.shape[1]))
+            Wp[r0:r0 + W.shape[0]] = alpha * W
+            Zp[c0:c0 + Z.shape[0]] = Z
+            Ws.append(Wp)
+            Zs.append(Zp)
+        if Ws:
+            self._add_lr(C, np.hstack(Ws), np.hstack(Zs))
+
+    def shift_upd(self, C):
+        acc = self.acc.pop(C.key, None)
+        pend = self.pending.pop(C.key, [])
+        for i in range(2):
+            for j in range(2):
+                Cs = C.sons[i][j]
+                if acc is not None:
+                    r0, c0 = Cs.row.lo - C.row.lo, Cs.col.lo - C.col.lo
+                    self._add_lr(Cs, acc[0][r0:r0 + Cs.row.size], acc[1][c0:c0 + Cs.col.size])
+                for (alpha, A, B) in pend:
+                    for l in range(2):
+                        self.add_upd(alpha, A.sons[i][l], B.sons[l][j], Cs)
+
+    def apply_upd(self, C):
+        if not C.is_leaf:
+            self.shift_upd(C)
+            for i in range(2):
+                for j in range(2):
+                    self.apply_upd(C.sons[i][j])
+            return
+        acc = self.acc.pop(C.key, None)
+        if acc is None:
+            return
+        st = self.M[C.key]
+        if isinstance(st, Dense):
+            st.D += acc
+            self.stats.flops += st.D.size
+        else:
+            self.apply_to_leaf(C, 1.0, [(0, 0, acc[0], acc[1])], C.row.lo, C.col.lo)
+
+
+class CoarseAccuHLUFactor(AccuHLUFactor):
+    """Accumulator H-LU whose accumulators collect pieces without rounding and are compressed
+    once, when shift_upd passes them to the sons: the pieces of a structured block (its own
+    products and the share of its parent) become one rounded addition over the whole block, so
+    each son receives a single low-rank piece from above. A leaf adds its pieces in one rounded
+    addition as in the piece-list form. (§2.3 leaves the accumulator format open.)"""
+
+    def shift_upd(self, C):
+        acc = self.acc.pop(C.key, [])
+        if acc:
+            m, n = C.row.size, C.col.size
+            Ws, Zs = [], []
+            for (r0, c0, Wp, Zp) in acc:
+                a = np.zeros((m, Wp.shape[1]))
+                a[r0:r0 + Wp.shape[0]] = Wp
+                b = np.zeros((n, Zp.shape[1]))
+                b[c0:c0 + Zp.shape[0]] = Zp
+                Ws.append(a)
+                Zs.append(b)
+            U, V = truncate(np.hstack(Ws), np.hstack(Zs), self.eps, min(m, n), self.stats)
+            self.acc[C.key] = [(0, 0, U, V)]
+        super().shift_upd(C)

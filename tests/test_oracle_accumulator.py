@@ -303,3 +303,28 @@ def test_planted_merged_graph_without_add_links_is_caught(monkeypatch):
     b = D.AccuTaskGraphBuilder(hm.ct, hm.bt)
     run = AccuTaskRunner(hm, b.parent).run_all(_eager_order(nodes, edges, 6))
     assert _rel(hm.exact_dense(), run, np.random.default_rng(3).standard_normal((hm.n, 2))) > 1e-3
+
+
+# -- accumulator formats (§2.3 leaves the format open) ---------------------------------------------------
+from oracle.accu import CoarseAccuHLUFactor, LowRankAccuHLUFactor
+
+
+@pytest.mark.parametrize("cls", [LowRankAccuHLUFactor, CoarseAccuHLUFactor])
+def test_accumulator_formats_dense_case_and_accuracy(cls):
+    p = W.fibonacci_sphere(300, 2)
+    hm0 = HMatrix(p, 64, 0.0, 1e-14, 64)
+    assert _rel(hm0.exact_dense(), cls(hm0).factor(), np.eye(hm0.n)) < 1e-14
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-4, 64)
+    A = hm.exact_dense()
+    f = cls(hm).factor()
+    assert np.linalg.norm(A - f.apply_lu(np.eye(hm.n)), 2) / np.linalg.norm(A, 2) <= 10 * 1e-4
+    assert not f.acc and not f.pending
+
+
+def test_accumulator_formats_truncation_order():
+    """Rounded additions: piece lists (one per low-rank leaf) <= coarse compression (plus one per
+    structured block with updates) < low-rank accumulators (one per addition) < recursive H-LU."""
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-6, 64)
+    counts = [c(hm).factor().stats.truncations
+              for c in (AccuHLUFactor, CoarseAccuHLUFactor, LowRankAccuHLUFactor, HLUFactor)]
+    assert counts[0] <= counts[1] < counts[2] < counts[3]
