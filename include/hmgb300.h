@@ -210,6 +210,37 @@ int hm_structure_build(const double* points_xyz, int64_t n, int leaf_size, doubl
 int hm_structure_build_accumulator(const double* points_xyz, int64_t n, int leaf_size, double eta, int merged,
                                    hm_structure** out);
 int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
+
+/* Host-side plan of a structure built by hm_structure_build (the standard task graph), for
+ * inspection and host-side checks; no GPU is used. which = 0: the H-LU plan at accuracy eps
+ * (> 0); which = 1: the forward / backward substitution plan for up to nrhs_max (>= 1)
+ * right-hand sides; which = 2..5: the product plan of hm_matvec for op = which - 2 (HM_OP_A,
+ * HM_OP_L, HM_OP_U, HM_OP_LU) on a work buffer of four n x nrhs_max blocks (x, y, two
+ * temporaries). rank_cap: 1..64, the capacity of the low-rank leaves. Replaces an earlier
+ * plan of S. HM_EINVAL on bad arguments or an accumulator task graph, HM_EINTERNAL if the
+ * planner fails. */
+int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max);
+
+enum {
+  HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz} int32 records, in execution order;
+                            kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core           */
+  HM_PLAN_GETRF = 1,     /* the micro-op descriptors of the batched kernels, laid out as the */
+  HM_PLAN_TRSM = 2,      /* GetrfOp, TrsmOp, GemmOp, CopyOp, TruncOp and StackEntry structs  */
+  HM_PLAN_GEMM = 3,      /* of the library's csrc/ops.h; one TRUNC record serves a stack and */
+  HM_PLAN_COPY = 4,      /* a core launch; a launch covers records [begin, begin + count).   */
+  HM_PLAN_TRUNC = 5,     /* Addresses are ((space + 1) << 60) | element offset, space 0 the  */
+  HM_PLAN_ENTRIES = 6,   /* factor values, 1 scratch, 2 work vectors, 3 matrix values (int   */
+                         /* spaces: 0 factor ranks, 1 pivots, 2 scratch ints, 3 matrix ranks) */
+  HM_PLAN_LEAVES = 7,    /* per block-tree leaf, 10 int64: row cluster, col cluster, m, n,
+                            low-rank (0/1), rank capacity, value offset (dense D or U, ld m),
+                            V offset (ld n), rank index, pivot offset (-1: none)             */
+  HM_PLAN_SIZES = 8      /* one record of 8 int64: scratch doubles, scratch ints, value
+                            doubles, ranks, pivots, rounded additions, waves, phases          */
+};
+/* Read-only view of one table of the last plan of S: *data points into S and stays valid until
+ * S is planned again or freed; *count records of *elem_bytes bytes. HM_EINVAL without a plan. */
+int hm_structure_plan_table(const hm_structure* S, int table, const void** data, int64_t* count,
+                            int64_t* elem_bytes);
 /* Export (any pointer may be NULL):
  *   perm[n]                 original index of each permuted position
  *   clusters[nclusters*6]   lo, hi, son0, son1, level, parent (depth-first pre-order ids)

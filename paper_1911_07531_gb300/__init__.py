@@ -134,6 +134,8 @@ def load_library():
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
+        "hm_structure_plan": ([P, I, D, I, I], I),
+        "hm_structure_plan_table": ([P, I, PP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
         "hm_structure_export": ([P, P, P, P, P, P, P], I),
         "hm_structure_free": ([P], V),
@@ -352,8 +354,56 @@ def hm_truncate_noalloc(W, Z, eps, cap=64, stream=None):
     return U[:, :k.value], V[:, :k.value]
 
 
+def _dt(fields):
+    return np.dtype(fields, align=True)
+
+
+_U8, _I8, _I4, _F8 = "u8", "i8", "i4", "f8"
+# record layouts of the plan tables (the micro-op descriptors of csrc/ops.h)
+PLAN_DTYPES = {
+    "launches": _dt([("kind", _I4), ("begin", _I4), ("count", _I4), ("gy", _I4), ("gz", _I4)]),
+    "getrf": _dt([("A", _U8), ("piv", _U8), ("b", _I4), ("pad", _I4)]),
+    "trsm": _dt([("T", _U8), ("piv", _U8), ("X", _U8), ("x_es", _I8), ("x_vs", _I8), ("nvd", _U8), ("nv", _I4),
+                 ("b", _I4), ("mode", _I4), ("pad", _I4)]),
+    "gemm": _dt([("A", _U8), ("B", _U8), ("C", _U8), ("a_rs", _I8), ("a_cs", _I8), ("b_rs", _I8), ("b_cs", _I8),
+                 ("c_rs", _I8), ("c_cs", _I8), ("md", _U8), ("nd", _U8), ("kd", _U8), ("m", _I4), ("n", _I4),
+                 ("k", _I4), ("flags", _I4), ("alpha", _F8), ("fclass", _I4), ("split", _I4)]),
+    "copy": _dt([("src", _U8), ("s_rs", _I8), ("s_cs", _I8), ("dst", _U8), ("d_rs", _I8), ("d_cs", _I8),
+                 ("md", _U8), ("nd", _U8), ("m", _I4), ("n", _I4), ("mode", _I4), ("pad", _I4), ("alpha", _F8)]),
+    "trunc": _dt([("U", _U8), ("V", _U8), ("rank", _U8), ("m", _I4), ("n", _I4), ("cap", _I4), ("Kcap", _I4),
+                  ("first_entry", _I4), ("n_entries", _I4), ("Wst", _U8), ("Zst", _U8), ("Gw", _U8), ("Gz", _U8),
+                  ("Tw", _U8), ("Tz", _U8), ("work", _U8), ("Kd", _U8), ("eps", _F8)]),
+    "entries": _dt([("W", _U8), ("w_rs", _I8), ("w_cs", _I8), ("Z", _U8), ("z_rs", _I8), ("z_cs", _I8),
+                    ("kd", _U8), ("k", _I4), ("row_off", _I4), ("nrows", _I4), ("col_off", _I4), ("ncols", _I4),
+                    ("pad", _I4), ("alpha", _F8)]),
+    "leaves": _dt([(f, _I8) for f in ("row", "col", "m", "n", "lr", "cap", "off", "voff", "rank_idx",
+                                      "piv_off")]),
+    "sizes": _dt([(f, _I8) for f in ("scratch_doubles", "scratch_ints", "nvalues", "nranks", "npiv", "ntrunc",
+                                     "nwaves", "nphases")]),
+}
+PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves", "sizes")
+
+
 class Structure:
     """Host-only cluster tree, block tree and H-LU task graph (no GPU needed)."""
+
+    def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1):
+        """Host plan (which 0: H-LU at eps, 1: solve for nrhs_max right-hand sides) as a dict of
+        numpy record arrays, one per table of ``PLAN_TABLES``."""
+        lib = load_library()
+        _check(lib.hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max)))
+        out = {}
+        for t, name in enumerate(PLAN_TABLES):
+            ptr, cnt, eb = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
+            _check(lib.hm_structure_plan_table(self.handle, t, ctypes.byref(ptr), ctypes.byref(cnt), ctypes.byref(eb)))
+            dt = PLAN_DTYPES[name]
+            if eb.value != dt.itemsize:
+                raise HMError(-7, f"plan table {name}: record of {eb.value} bytes, binding expects {dt.itemsize}")
+            nbytes = cnt.value * eb.value
+            raw = ctypes.string_at(ptr, nbytes) if nbytes else b""
+            out[name] = np.frombuffer(raw, dtype=dt).copy()
+        out["sizes"] = out["sizes"][0]
+        return out
 
     def __init__(self, handle):
         self.handle = handle

@@ -990,6 +990,8 @@ struct hm_structure {
   TaskGraph g;
   Plan plan;
   bool planned = false;
+  Layout lay;
+  std::vector<int64_t> leaf_table, sizes;   // plan tables built by hm_structure_plan
 };
 
 extern "C" {
@@ -1037,6 +1039,63 @@ int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, 
   }
   *out = S.release();
   return HM_OK;
+}
+
+int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max) {
+  if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
+  if (which < 0 || which > 5) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..5");
+  if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan: rank_cap must be in 1..64");
+  if (which == 0 && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
+  if (which >= 1 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
+  for (const Task& t : S->g.nodes)
+    if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan: the structure holds an accumulator task graph");
+  try {
+    build_layout(S->ct, S->bt, rank_cap, S->lay);
+    if (which == 0)
+      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan);
+    else if (which == 1)
+      plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
+    else
+      plan_matvec(S->ct, S->bt, S->lay, which - 2, nrhs_max, S->plan);
+  } catch (const std::exception& ex) {
+    S->planned = false;
+    return fail(HM_EINTERNAL, std::string("hm_structure_plan: ") + ex.what());
+  }
+  S->planned = true;
+  S->leaf_table.clear();
+  for (const LeafStore& L : S->lay.leaf) {
+    const int64_t r[10] = {L.row, L.col, L.m, L.n, L.lr ? 1 : 0, L.cap, L.off, L.voff, L.rank_idx, L.piv_off};
+    S->leaf_table.insert(S->leaf_table.end(), r, r + 10);
+  }
+  const Plan& P = S->plan;
+  S->sizes = {P.scratch_doubles, P.scratch_ints, S->lay.nvalues, S->lay.nranks, S->lay.npiv,
+              P.ntrunc,          P.nwaves,       P.nphases};
+  return HM_OK;
+}
+
+int hm_structure_plan_table(const hm_structure* S, int table, const void** data, int64_t* count,
+                            int64_t* elem_bytes) {
+  if (!S || !data || !count || !elem_bytes) return fail(HM_EINVAL, "hm_structure_plan_table: NULL argument");
+  if (!S->planned || S->sizes.empty()) return fail(HM_EINVAL, "hm_structure_plan_table: no plan (hm_structure_plan)");
+  const Plan& P = S->plan;
+  auto put = [&](const void* d, size_t n, size_t b) {
+    *data = d;
+    *count = (int64_t)n;
+    *elem_bytes = (int64_t)b;
+    return HM_OK;
+  };
+  switch (table) {
+    case HM_PLAN_LAUNCHES: return put(P.launches.data(), P.launches.size(), sizeof(Launch));
+    case HM_PLAN_GETRF: return put(P.getrf.data(), P.getrf.size(), sizeof(GetrfOp));
+    case HM_PLAN_TRSM: return put(P.trsm.data(), P.trsm.size(), sizeof(TrsmOp));
+    case HM_PLAN_GEMM: return put(P.gemm.data(), P.gemm.size(), sizeof(GemmOp));
+    case HM_PLAN_COPY: return put(P.copy.data(), P.copy.size(), sizeof(CopyOp));
+    case HM_PLAN_TRUNC: return put(P.trunc.data(), P.trunc.size(), sizeof(TruncOp));
+    case HM_PLAN_ENTRIES: return put(P.entries.data(), P.entries.size(), sizeof(StackEntry));
+    case HM_PLAN_LEAVES: return put(S->leaf_table.data(), S->leaf_table.size() / 10, 10 * sizeof(int64_t));
+    case HM_PLAN_SIZES: return put(S->sizes.data(), 1, S->sizes.size() * sizeof(int64_t));
+    default: return fail(HM_EINVAL, "hm_structure_plan_table: unknown table");
+  }
 }
 
 int hm_structure_info_get(const hm_structure* S, hm_structure_info* o) {

@@ -1,0 +1,194 @@
+"""The library's host plans executed micro-op by micro-op on the CPU (``tests/plan_sim.py``).
+
+The H-LU plan, run on the oracle's H-matrix, must give factors that reproduce A within the
+H-LU bound, and the solve plan, run on those factors, must equal the oracle's block
+substitution with the same factors: this checks the planner's addresses, strides, dynamic
+sizes, phase order and stacking on the host, independently of the CUDA kernels.
+"""
+import numpy as np
+import pytest
+
+import hm_workloads as W
+import paper_1911_07531_gb300 as hm
+from oracle.hlu import HLUFactor
+from oracle.hmatrix import DiagLU, Dense, HMatrix, LowRank
+from tests.plan_sim import IS_PIV, IS_RANK, IS_S, SP_F, SP_X, PlanSim
+
+
+def ref(space, off):
+    return ((space + 1) << 60) | int(off)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hm.build_library()
+    return hm.load_library()
+
+
+def _load(sim, leaves, store):
+    for lf in leaves:
+        st = store[(int(lf["row"]), int(lf["col"]))]
+        m, n = int(lf["m"]), int(lf["n"])
+        if lf["lr"]:
+            k = st.U.shape[1]
+            assert k <= int(lf["cap"])
+            sim.mat(ref(SP_F, lf["off"]), 1, m, m, k)[:] = st.U
+            sim.mat(ref(SP_F, lf["voff"]), 1, n, n, k)[:] = st.V
+            sim.i[IS_RANK][int(lf["rank_idx"])] = k
+        else:
+            sim.mat(ref(SP_F, lf["off"]), 1, m, m, n)[:] = st.D
+
+
+def _factor(hmat, sim, leaves):
+    """The simulated factors in the oracle's factor container."""
+    f = HLUFactor(hmat)
+    for lf in leaves:
+        key = (int(lf["row"]), int(lf["col"]))
+        m, n = int(lf["m"]), int(lf["n"])
+        if lf["lr"]:
+            k = int(sim.i[IS_RANK][int(lf["rank_idx"])])
+            U = np.array(sim.mat(ref(SP_F, lf["off"]), 1, m, m, k))
+            V = np.array(sim.mat(ref(SP_F, lf["voff"]), 1, n, n, k))
+            f.M[key] = LowRank(U, V)
+        elif key[0] == key[1]:
+            p0 = int(lf["piv_off"])
+            f.M[key] = DiagLU(np.array(sim.mat(ref(SP_F, lf["off"]), 1, m, m, n)), sim.i[IS_PIV][p0:p0 + m].copy())
+        else:
+            f.M[key] = Dense(np.array(sim.mat(ref(SP_F, lf["off"]), 1, m, m, n)))
+    return f
+
+
+@pytest.mark.parametrize("geom,n,eta,eps", [("sphere", 1024, 2.0, 1e-6), ("cube", 1500, 2.0, 1e-4),
+                                            ("line", 700, 0.0, 1e-10), ("ellipsoid", 1200, 2.0, 1e-6)])
+def test_lu_and_solve_plans_on_the_host(lib, geom, n, eta, eps):
+    pts = W.points_for(geom, n, 21)
+    hmat = HMatrix(pts, 64, eta, eps, 64)
+    S = hm.hm_structure_build(pts, 64, eta)
+    P = S.plan(0, eps, 64)
+    sim = PlanSim(P["sizes"])
+    _load(sim, P["leaves"], hmat.store)
+    sim.run(P)
+    assert sim.singular == 0
+    f = _factor(hmat, sim, P["leaves"])
+    A = hmat.exact_dense()
+    X = np.random.default_rng(3).standard_normal((n, 4))
+    err = np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X)
+    assert err <= 10 * eps, err
+    ref_f = HLUFactor(hmat).factor()
+    assert np.linalg.norm(A @ X - ref_f.apply_lu(X)) / np.linalg.norm(A @ X) <= 10 * eps
+
+    # the solve plan on the simulated factors equals the oracle's substitution with them
+    nrhs_max = 3
+    Q = S.plan(1, 0.0, 64, nrhs_max)
+    sol = PlanSim(Q["sizes"], nrhs_space=n * nrhs_max)
+    sol.d[SP_F], sol.i[IS_RANK], sol.i[IS_PIV] = sim.d[SP_F], sim.i[IS_RANK], sim.i[IS_PIV]
+    B = np.random.default_rng(4).standard_normal((n, 2))
+    sol.mat(ref(SP_X, 0), 1, n, n, 2)[:] = B
+    sol.i[IS_S][0] = 2
+    sol.run(Q)
+    Xs = np.array(sol.mat(ref(SP_X, 0), 1, n, n, 2))
+    Xo = f.usolve(hmat.ct.root, f.lsolve(hmat.ct.root, B))
+    assert np.linalg.norm(Xs - Xo) / np.linalg.norm(Xo) < 1e-12
+    assert np.linalg.norm(f.apply_lu(Xs) - B) / np.linalg.norm(B) < 1e-12
+
+
+def test_plan_sim_catches_a_planted_stride_error(lib):
+    """A planner address mistake (here the leading dimension of the low-rank V factors in the
+    rebuild products, planted in the exported plan) makes the host run fail its bound."""
+    pts = W.fibonacci_sphere(1024, 21)
+    hmat = HMatrix(pts, 64, 2.0, 1e-6, 64)
+    P = hm.hm_structure_build(pts, 64, 2.0).plan(0, 1e-6, 64)
+    sim = PlanSim(P["sizes"])
+    _load(sim, P["leaves"], hmat.store)
+    core_V = set(int(v) for v in P["trunc"]["V"])
+    g = P["gemm"]
+    hit = np.array([int(c) in core_V for c in g["C"]])
+    assert hit.any()
+    g["c_cs"][hit] += 1
+    try:
+        sim.run(P)
+    except AssertionError:
+        return
+    f = _factor(hmat, sim, P["leaves"])
+    A = hmat.exact_dense()
+    X = np.random.default_rng(3).standard_normal((hmat.n, 2))
+    assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) > 1e-3
+
+
+@pytest.mark.parametrize("name,pts,eta,eps,cap", [
+    ("ragged n = 65", W.fibonacci_sphere(65, 2), 2.0, 1e-6, 64),
+    ("all dense", W.fibonacci_sphere(1000, 3), 0.0, 1e-6, 64),
+    ("rank cap 4", W.cube_surface(1500, 3), 2.0, 1e-8, 4),
+])
+def test_lu_plan_edge_cases_on_the_host(lib, name, pts, eta, eps, cap):
+    """Ragged leaves, no low-rank block at all, and a rank cap that binds (the plan's rounded
+    additions hit the cap exactly as often as the oracle's and end at the same error)."""
+    n = len(pts)
+    hmat = HMatrix(pts, 64, eta, eps, cap)
+    P = hm.hm_structure_build(pts, 64, eta).plan(0, eps, cap)
+    sim = PlanSim(P["sizes"])
+    _load(sim, P["leaves"], hmat.store)
+    sim.run(P)
+    f = _factor(hmat, sim, P["leaves"])
+    ref_f = HLUFactor(hmat).factor()
+    A = hmat.exact_dense()
+    X = np.random.default_rng(3).standard_normal((n, 2))
+    e_plan = np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X)
+    e_ref = np.linalg.norm(A @ X - ref_f.apply_lu(X)) / np.linalg.norm(A @ X)
+    if cap < 64:
+        assert sim.cap_hits == ref_f.stats.cap_hits > 0
+        assert abs(e_plan - e_ref) <= 1e-3 * e_ref
+    else:
+        assert e_plan <= 10 * eps and sim.cap_hits == 0
+
+
+def test_matvec_plans_on_the_host(lib):
+    """hm_matvec's plans: A x equals the oracle's H-matrix product; U x, then P L of it, equals
+    the P L U x of the factors; the fused P L U plan gives the same."""
+    from oracle.hlu import hmatrix_matvec
+    pts = W.cube_surface(1200, 5)
+    n, eps, nr = len(pts), 1e-6, 2
+    hmat = HMatrix(pts, 64, 2.0, eps, 64)
+    S = hm.hm_structure_build(pts, 64, 2.0)
+    P = S.plan(0, eps, 64)
+    fac = PlanSim(P["sizes"])
+    _load(fac, P["leaves"], hmat.store)
+    fac.run(P)
+    f = _factor(hmat, fac, P["leaves"])
+    x = np.random.default_rng(8).standard_normal((n, nr))
+
+    def run(op, xin):
+        Q = S.plan(2 + op, 0.0, 64, nr)
+        sim = PlanSim(Q["sizes"], nrhs_space=4 * n * nr)
+        sim.d[SP_F], sim.i[IS_RANK], sim.i[IS_PIV] = fac.d[SP_F], fac.i[IS_RANK], fac.i[IS_PIV]
+        if op == 0:
+            sim.d[3] = np.zeros(int(P["sizes"]["nvalues"]))
+            sim.i[3] = np.zeros(int(P["sizes"]["nranks"]), np.int64)
+            _load(_Spaces(sim, 3), P["leaves"], hmat.store)
+        sim.mat(ref(SP_X, 0), 1, n, n, nr)[:] = xin
+        sim.i[IS_S][0] = nr
+        sim.run(Q)
+        return np.array(sim.mat(ref(SP_X, n * nr), 1, n, n, nr))
+
+    y = run(0, x)
+    perm = hmat.ct.perm
+    x_orig = np.empty_like(x)
+    x_orig[perm] = x
+    yo = hmatrix_matvec(hmat, x_orig).reshape(n, nr)[perm]
+    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) < 1e-13
+    A = hmat.exact_dense()
+    assert np.linalg.norm(y - A @ x) / np.linalg.norm(A @ x) < 10 * eps
+    plu = f.apply_lu(x)
+    assert np.linalg.norm(run(1, run(2, x)) - plu) / np.linalg.norm(plu) < 1e-13
+    assert np.linalg.norm(run(3, x) - plu) / np.linalg.norm(plu) < 1e-13
+
+
+class _Spaces:
+    """Loads a leaf table into the matrix-value spaces (3) of a simulator."""
+
+    def __init__(self, sim, space):
+        self.sim, self.space = sim, space
+        self.i = {IS_RANK: sim.i[space]}
+
+    def mat(self, r, rs, cs, m, n):
+        return self.sim.mat(ref(self.space, int(r) & ((1 << 60) - 1)), rs, cs, m, n)
