@@ -117,3 +117,17 @@ def test_plan_builds_on_host(lib):
     i = S.info
     assert i["plan_launches"] > 0 and i["plan_phases"] >= i["nlevels"]
     assert i["plan_truncations"] > 0 and i["plan_scratch_bytes"] > 0
+
+
+def test_plan_export_errors(lib):
+    S = hm.hm_structure_build(W.fibonacci_sphere(512, 3), 64, 2.0)
+    for args in ((9, 1e-6, 64, 1), (0, 0.0, 64, 1), (0, 1e-6, 65, 1), (1, 0.0, 64, 0)):
+        with pytest.raises(hm.HMError):
+            S.plan(*args)
+    acc = hm.hm_structure_build_accumulator(W.fibonacci_sphere(512, 3), 64, 2.0)
+    with pytest.raises(hm.HMError):
+        acc.plan(0, 1e-6, 64)
+    P = S.plan(0, 1e-6, 64)
+    assert P["sizes"]["nwaves"] == S.info["nlevels"] and len(P["leaves"]) == S.info["nleaves"]
+    k = P["launches"]["kind"]
+    assert set(k.tolist()) <= set(range(6)) and (P["launches"]["count"] > 0).all()
