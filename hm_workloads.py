@@ -75,6 +75,14 @@ def ellipsoid(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(p)
 
 
+def ellipsoid_instances(count: int = 64, seed: int = 41, n_min: int = 4096, n_max: int = 65536) -> list:
+    """Independent problems of the batching workload: n log-uniform in [n_min, n_max] (rounded),
+    each a seeded random ellipsoid surface (``ellipsoid``); returns [(n, points), ...]."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=count))).astype(int)
+    return [(int(n), ellipsoid(int(n), seed * 1000 + i)) for i, n in enumerate(ns)]
+
+
 def line_points(n: int) -> np.ndarray:
     """n points evenly spaced on [0,1] along the x axis (exact halving under bisection)."""
     p = np.zeros((n, 3), dtype=np.float64)

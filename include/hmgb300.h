@@ -234,9 +234,20 @@ enum {
   HM_PLAN_LEAVES = 7,    /* per block-tree leaf, 10 int64: row cluster, col cluster, m, n,
                             low-rank (0/1), rank capacity, value offset (dense D or U, ld m),
                             V offset (ld n), rank index, pivot offset (-1: none)             */
-  HM_PLAN_SIZES = 8      /* one record of 8 int64: scratch doubles, scratch ints, value
+  HM_PLAN_SIZES = 8,     /* one record of 8 int64: scratch doubles, scratch ints, value
                             doubles, ranks, pivots, rounded additions, waves, phases          */
+  HM_PLAN_INSTANCES = 9  /* per instance, 5 int64: first leaf record, leaf records, value,
+                            rank and pivot offsets (one instance unless batched)              */
 };
+
+/* Host-side H-LU plan of count independent structures in one launch sequence (batching
+ * across instances): wave w of every instance is expanded into the same phases, so that one
+ * launch per kernel kind and phase serves all of them. The instances' values, ranks and
+ * pivots are concatenated in the given order (value offsets rounded up to 32 doubles); the
+ * leaf table lists every instance's leaves with those offsets added. The plan is kept in
+ * S[0] (its tables as for hm_structure_plan). HM_EINVAL on bad arguments, a structure listed
+ * twice or an accumulator task graph. */
+int hm_structure_plan_lu_batch(hm_structure* const* S, int count, double eps, int rank_cap);
 /* Read-only view of one table of the last plan of S: *data points into S and stays valid until
  * S is planned again or freed; *count records of *elem_bytes bytes. HM_EINVAL without a plan. */
 int hm_structure_plan_table(const hm_structure* S, int table, const void** data, int64_t* count,

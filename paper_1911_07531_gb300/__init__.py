@@ -24,7 +24,7 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
-    "hm_structure_build", "hm_structure_build_accumulator", "header_functions",
+    "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_plan_lu_batch", "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
 ]
 
@@ -135,6 +135,7 @@ def load_library():
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
         "hm_structure_plan": ([P, I, D, I, I], I),
+        "hm_structure_plan_lu_batch": ([P, I, D, I], I),
         "hm_structure_plan_table": ([P, I, PP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
         "hm_structure_export": ([P, P, P, P, P, P, P], I),
@@ -380,8 +381,9 @@ PLAN_DTYPES = {
                                       "piv_off")]),
     "sizes": _dt([(f, _I8) for f in ("scratch_doubles", "scratch_ints", "nvalues", "nranks", "npiv", "ntrunc",
                                      "nwaves", "nphases")]),
+    "instances": _dt([(f, _I8) for f in ("first_leaf", "nleaves", "base_d", "base_r", "base_p")]),
 }
-PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves", "sizes")
+PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves", "sizes", "instances")
 
 
 class Structure:
@@ -390,19 +392,27 @@ class Structure:
     def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1):
         """Host plan (which 0: H-LU at eps, 1: solve for nrhs_max right-hand sides) as a dict of
         numpy record arrays, one per table of ``PLAN_TABLES``."""
+        _check(load_library().hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max)))
+        return self.plan_tables()
+
+    def plan_tables(self, names=PLAN_TABLES):
+        """The tables (by name, see ``PLAN_TABLES``) of the structure's last plan."""
         lib = load_library()
-        _check(lib.hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max)))
         out = {}
         for t, name in enumerate(PLAN_TABLES):
+            if name not in names:
+                continue
             ptr, cnt, eb = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
             _check(lib.hm_structure_plan_table(self.handle, t, ctypes.byref(ptr), ctypes.byref(cnt), ctypes.byref(eb)))
             dt = PLAN_DTYPES[name]
             if eb.value != dt.itemsize:
                 raise HMError(-7, f"plan table {name}: record of {eb.value} bytes, binding expects {dt.itemsize}")
-            nbytes = cnt.value * eb.value
-            raw = ctypes.string_at(ptr, nbytes) if nbytes else b""
-            out[name] = np.frombuffer(raw, dtype=dt).copy()
-        out["sizes"] = out["sizes"][0]
+            arr = np.empty(cnt.value, dtype=dt)
+            if cnt.value:
+                ctypes.memmove(arr.ctypes.data, ptr, cnt.value * eb.value)
+            out[name] = arr
+        if "sizes" in out:
+            out["sizes"] = out["sizes"][0]
         return out
 
     def __init__(self, handle):
@@ -438,6 +448,13 @@ def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0, merged=False):
     _check(load_library().hm_structure_build_accumulator(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
                                                          int(bool(merged)), ctypes.byref(h)))
     return Structure(h)
+
+
+def hm_structure_plan_lu_batch(structures, eps=1e-6, rank_cap=64, names=PLAN_TABLES):
+    """One H-LU plan for several independent structures (kept in the first); its tables."""
+    arr = (ctypes.c_void_p * len(structures))(*[s.handle for s in structures])
+    _check(load_library().hm_structure_plan_lu_batch(arr, len(structures), float(eps), int(rank_cap)))
+    return structures[0].plan_tables(names)
 
 
 def hm_structure_build(points, leaf_size=64, eta=2.0, with_plan=False):

@@ -992,6 +992,7 @@ struct hm_structure {
   bool planned = false;
   Layout lay;
   std::vector<int64_t> leaf_table, sizes;   // plan tables built by hm_structure_plan
+  std::vector<int64_t> instances;           // batched plan: first leaf, leaves, value / rank / pivot bases
 };
 
 extern "C" {
@@ -1041,6 +1042,22 @@ int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, 
   return HM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// per leaf: row, col, m, n, low-rank, cap, value offset, V offset, rank index, pivot offset,
+// with the instance's bases added
+void append_leaf_table(const Layout& lay, int64_t bd, int64_t br, int64_t bp, std::vector<int64_t>& out) {
+  for (const LeafStore& L : lay.leaf) {
+    const int64_t r[10] = {L.row,      L.col,           L.m, L.n, L.lr ? 1 : 0, L.cap, L.off + bd,
+                           L.voff + bd, L.rank_idx < 0 ? -1 : L.rank_idx + br, L.piv_off < 0 ? -1 : L.piv_off + bp};
+    out.insert(out.end(), r, r + 10);
+  }
+}
+}  // namespace
+
+extern "C" {
+
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
   if (which < 0 || which > 5) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..5");
@@ -1063,13 +1080,51 @@ int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int 
   }
   S->planned = true;
   S->leaf_table.clear();
-  for (const LeafStore& L : S->lay.leaf) {
-    const int64_t r[10] = {L.row, L.col, L.m, L.n, L.lr ? 1 : 0, L.cap, L.off, L.voff, L.rank_idx, L.piv_off};
-    S->leaf_table.insert(S->leaf_table.end(), r, r + 10);
-  }
+  append_leaf_table(S->lay, 0, 0, 0, S->leaf_table);
   const Plan& P = S->plan;
   S->sizes = {P.scratch_doubles, P.scratch_ints, S->lay.nvalues, S->lay.nranks, S->lay.npiv,
               P.ntrunc,          P.nwaves,       P.nphases};
+  S->instances = {0, (int64_t)S->lay.leaf.size(), 0, 0, 0};
+  return HM_OK;
+}
+
+int hm_structure_plan_lu_batch(hm_structure* const* S, int count, double eps, int rank_cap) {
+  if (!S || count < 1) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: bad argument");
+  if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: rank_cap must be in 1..64");
+  if (!(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: eps must be > 0");
+  for (int i = 0; i < count; ++i) {
+    if (!S[i]) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: NULL structure");
+    for (int j = 0; j < i; ++j)
+      if (S[j] == S[i]) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: a structure is listed twice");
+    for (const Task& t : S[i]->g.nodes)
+      if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan_lu_batch: an accumulator task graph");
+  }
+  hm_structure* H = S[0];
+  std::vector<LuInstance> inst;
+  std::vector<int64_t> table, insts;
+  int64_t bd = 0, br = 0, bp = 0, nleaves = 0;
+  try {
+    for (int i = 0; i < count; ++i) {
+      build_layout(S[i]->ct, S[i]->bt, rank_cap, S[i]->lay);
+      inst.push_back({&S[i]->ct, &S[i]->bt, &S[i]->lay, &S[i]->g, bd, br, bp});
+      append_leaf_table(S[i]->lay, bd, br, bp, table);
+      insts.insert(insts.end(), {nleaves, (int64_t)S[i]->lay.leaf.size(), bd, br, bp});
+      nleaves += (int64_t)S[i]->lay.leaf.size();
+      bd += (S[i]->lay.nvalues + 31) / 32 * 32;
+      br += S[i]->lay.nranks;
+      bp += S[i]->lay.npiv;
+    }
+    plan_lu_batch(inst, eps, H->plan);
+  } catch (const std::exception& ex) {
+    H->planned = false;
+    H->sizes.clear();
+    return fail(HM_EINTERNAL, std::string("hm_structure_plan_lu_batch: ") + ex.what());
+  }
+  H->planned = true;
+  H->leaf_table.swap(table);
+  H->instances.swap(insts);
+  const Plan& P = H->plan;
+  H->sizes = {P.scratch_doubles, P.scratch_ints, bd, br, bp, P.ntrunc, P.nwaves, P.nphases};
   return HM_OK;
 }
 
@@ -1094,6 +1149,7 @@ int hm_structure_plan_table(const hm_structure* S, int table, const void** data,
     case HM_PLAN_ENTRIES: return put(P.entries.data(), P.entries.size(), sizeof(StackEntry));
     case HM_PLAN_LEAVES: return put(S->leaf_table.data(), S->leaf_table.size() / 10, 10 * sizeof(int64_t));
     case HM_PLAN_SIZES: return put(S->sizes.data(), 1, S->sizes.size() * sizeof(int64_t));
+    case HM_PLAN_INSTANCES: return put(S->instances.data(), S->instances.size() / 5, 5 * sizeof(int64_t));
     default: return fail(HM_EINVAL, "hm_structure_plan_table: unknown table");
   }
 }

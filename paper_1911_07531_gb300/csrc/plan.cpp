@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <stdexcept>
 
 namespace hm {
@@ -120,8 +121,6 @@ struct Wave {
   std::vector<std::vector<AcaOp>> aca;
   std::vector<std::vector<std::vector<StackEntry>>> stack_entries;   // per phase, per stack op
   int64_t sd = 0, si = 0;
-  std::map<int, int> target_index;
-  std::vector<TargetEntries> targets;
   int nph = 0;
   void need(int ph) {
     if (ph + 1 > nph) nph = ph + 1;
@@ -155,9 +154,17 @@ struct Ctx {
   const Layout& lay;
   Spaces sp;
   Plan& plan;
-  Wave w;
+  Wave own;
+  Wave& w;   // the wave being filled: this context's own, or one shared by several instances
+  // offsets of this instance's values, ranks and pivots in their spaces (batched plans)
+  int64_t base_d = 0, base_r = 0, base_p = 0;
+  // pieces reaching low-rank leaves in the current wave, by leaf index
+  std::map<int, int> target_index;
+  std::vector<TargetEntries> targets;
   Ctx(const ClusterTree& c, const BlockTree& b, const Layout& l, Spaces s, Plan& p)
-      : ct(c), bt(b), lay(l), sp(s), plan(p) {}
+      : ct(c), bt(b), lay(l), sp(s), plan(p), w(own) {}
+  Ctx(const ClusterTree& c, const BlockTree& b, const Layout& l, Spaces s, Plan& p, Wave& shared)
+      : ct(c), bt(b), lay(l), sp(s), plan(p), w(shared) {}
 
   const Cluster& cl(int id) const { return ct.cl[id]; }
   const BlockNode& node(int id) const { return bt.nodes[id]; }
@@ -167,8 +174,9 @@ struct Ctx {
     if (id < 0) throw std::runtime_error("planner: block not in block tree");
     return id;
   }
-  uint64_t dref(int64_t off) const { return mkref(sp.d, off); }
-  uint64_t rref(const LeafStore& L) const { return mkref(sp.r, L.rank_idx); }
+  uint64_t dref(int64_t off) const { return mkref(sp.d, off + base_d); }
+  uint64_t rref(const LeafStore& L) const { return mkref(sp.r, L.rank_idx + base_r); }
+  uint64_t pref(const LeafStore& L) const { return mkref(IS_PIV, L.piv_off + base_p); }
   uint64_t sref(int64_t off) const { return mkref(SP_S, off); }
 
   // ---------------------------------------------------------------- micro-op emitters
@@ -237,7 +245,7 @@ struct Ctx {
       TrsmOp t;
       std::memset(&t, 0, sizeof(t));
       t.T = dref(D.off);
-      t.piv = (mode == TM_L_PIV || mode == TM_MUL_PL) ? mkref(IS_PIV, D.piv_off) : 0;
+      t.piv = (mode == TM_L_PIV || mode == TM_MUL_PL) ? pref(D) : 0;
       t.X = X.ref + (uint64_t)(v0 * X.vs);
       t.x_es = X.es;
       t.x_vs = X.vs;
@@ -347,7 +355,7 @@ struct Ctx {
     GetrfOp g;
     std::memset(&g, 0, sizeof(g));
     g.A = dref(L.off);
-    g.piv = mkref(IS_PIV, L.piv_off);
+    g.piv = pref(L);
     g.b = L.m;
     w.getrf[0].push_back(g);
   }
@@ -504,16 +512,16 @@ struct Ctx {
     e.col_off = col_off;
     e.ncols = ncols;
     e.alpha = p.alpha;
-    auto it = w.target_index.find(leafidx);
+    auto it = target_index.find(leafidx);
     int ti;
-    if (it == w.target_index.end()) {
-      ti = (int)w.targets.size();
-      w.target_index[leafidx] = ti;
-      w.targets.push_back({leafidx, {}});
+    if (it == target_index.end()) {
+      ti = (int)targets.size();
+      target_index[leafidx] = ti;
+      targets.push_back({leafidx, {}});
     } else {
       ti = it->second;
     }
-    w.targets[ti].e.push_back({e, p.kmax});
+    targets[ti].e.push_back({e, p.kmax});
   }
 
   // apply the pieces (relative to the origin of block Cn) to the leaves of Cn -- phase 3
@@ -570,8 +578,8 @@ struct Ctx {
       bool zero_self;
     };
     std::vector<std::vector<Chunk>> rounds;
-    for (size_t ti = 0; ti < w.targets.size(); ++ti) {
-      const TargetEntries& T = w.targets[ti];
+    for (size_t ti = 0; ti < targets.size(); ++ti) {
+      const TargetEntries& T = targets[ti];
       const LeafStore& L = lay.leaf[T.leaf];
       size_t e0 = 0;
       int round = 0;
@@ -597,7 +605,7 @@ struct Ctx {
       w.sd = base;
       bool opened = false;
       for (const Chunk& ch : rd) {
-        const LeafStore& L = lay.leaf[w.targets[ch.target].leaf];
+        const LeafStore& L = lay.leaf[targets[ch.target].leaf];
         const int Kc = ch.Kc;
         const int64_t need = (int64_t)(L.m + L.n) * Kc + 4 * (int64_t)Kc * Kc + 2 * (int64_t)Kc * L.cap + 8 * ALIGN;
         if (opened && w.sd + need - base > budget) {
@@ -627,7 +635,7 @@ struct Ctx {
         op.eps = eps;
         peak = std::max(peak, w.sd);
         std::vector<StackEntry> es;
-        const TargetEntries& T = w.targets[ch.target];
+        const TargetEntries& T = targets[ch.target];
         for (size_t q = ch.e0; q < ch.e1; ++q) es.push_back(T.e[q].first);
         w.stack[ph].push_back(op);
         w.stack_entries[ph].push_back(es);
@@ -652,6 +660,8 @@ struct Ctx {
     }
     w.sd = std::max(base, peak);
     plan.scratch_trunc_max = std::max(plan.scratch_trunc_max, w.sd - base);
+    targets.clear();
+    target_index.clear();
   }
 
   // append the wave's phases to the plan in execution order
@@ -710,6 +720,8 @@ struct Ctx {
     plan.scratch_ints = std::max(plan.scratch_ints, w.si);
     plan.nwaves++;
     w = Wave();
+    targets.clear();
+    target_index.clear();
   }
 };
 
@@ -750,25 +762,57 @@ void build_layout(const ClusterTree& ct, const BlockTree& bt, int rank_cap, Layo
 }
 
 // ------------------------------------------------------------------------------ H-LU
+namespace {
+void expand_task(Ctx& c, const Task& t) {
+  switch (t.type) {
+    case T_LU: c.task_lu(t.a); break;
+    case T_TRSL: c.task_trsl(t.a, t.b); break;
+    case T_TRSU: c.task_trsu(t.a, t.b); break;
+    default: c.task_mul(t.a, t.b, t.c); break;
+  }
+  c.plan.ntasks++;
+}
+std::vector<std::vector<int>> by_level(const TaskGraph& g) {
+  std::vector<std::vector<int>> byl(g.nlevels);
+  for (size_t i = 0; i < g.nodes.size(); ++i) byl[g.level[i]].push_back((int)i);
+  return byl;
+}
+}  // namespace
+
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
              Plan& plan) {
   plan = Plan();
-  std::vector<std::vector<int>> byl(g.nlevels);
-  for (size_t i = 0; i < g.nodes.size(); ++i) byl[g.level[i]].push_back((int)i);
+  const auto byl = by_level(g);
   Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
   for (int lv = 0; lv < g.nlevels; ++lv) {
-    for (int ti : byl[lv]) {
-      const Task& t = g.nodes[ti];
-      switch (t.type) {
-        case T_LU: c.task_lu(t.a); break;
-        case T_TRSL: c.task_trsl(t.a, t.b); break;
-        case T_TRSU: c.task_trsu(t.a, t.b); break;
-        default: c.task_mul(t.a, t.b, t.c); break;
-      }
-      plan.ntasks++;
-    }
+    for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
     c.emit_truncations(3, eps);
     c.flush();
+  }
+}
+
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan) {
+  plan = Plan();
+  Wave w;
+  std::vector<std::unique_ptr<Ctx>> cs;
+  std::vector<std::vector<std::vector<int>>> byl;
+  int nlev = 0;
+  for (const LuInstance& I : inst) {
+    cs.emplace_back(new Ctx(*I.ct, *I.bt, *I.lay, Spaces{SP_F, IS_RANK}, plan, w));
+    cs.back()->base_d = I.base_d;
+    cs.back()->base_r = I.base_r;
+    cs.back()->base_p = I.base_p;
+    byl.push_back(by_level(*I.g));
+    nlev = std::max(nlev, I.g->nlevels);
+  }
+  if (cs.empty()) return;
+  for (int lv = 0; lv < nlev; ++lv) {
+    for (size_t i = 0; i < inst.size(); ++i)
+      if (lv < inst[i].g->nlevels)
+        for (int ti : byl[i][lv]) expand_task(*cs[i], inst[i].g->nodes[ti]);
+    // every instance's rounded additions of this wave share the phases after the products
+    for (auto& c : cs) c->emit_truncations(3, eps);
+    cs[0]->flush();
   }
 }
 
@@ -814,7 +858,7 @@ void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, d
     Piece p{View{a.U, 1, L.m}, View{a.V, 1, L.n}, Dim{0, a.kd}, kmax, 0, L.m, 0, L.n, 1.0};
     c.add_entry((int)q, p, 0, L.m, 0, L.n, 0, 0);
   }
-  if (!c.w.targets.empty() || c.w.nph > 0) {
+  if (!c.targets.empty() || c.w.nph > 0) {
     c.emit_truncations(1, eps, true);
     c.flush();
   }

@@ -74,6 +74,18 @@ struct Spaces {
 // H-LU: every wave of the levelled task graph expanded into phases of micro-ops.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
              double eps, Plan& plan);
+// Independent H-LU instances in one plan: wave w of every instance is expanded into the same
+// phases, so that one launch per kind and phase serves all of them (their task graphs have no
+// edges between each other). Instance i addresses its values, ranks and pivots at the given
+// offsets of one concatenated space each; scratch is shared wave by wave.
+struct LuInstance {
+  const ClusterTree* ct;
+  const BlockTree* bt;
+  const Layout* lay;
+  const TaskGraph* g;
+  int64_t base_d, base_r, base_p;
+};
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan);
 // hm_build: dense leaf assembly, ACA + rounded truncation of the admissible leaves.
 void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, double eps, int aca_kmax,
                 int64_t scratch_budget_doubles, Plan& plan);

@@ -192,3 +192,34 @@ class _Spaces:
 
     def mat(self, r, rs, cs, m, n):
         return self.sim.mat(ref(self.space, int(r) & ((1 << 60) - 1)), rs, cs, m, n)
+
+
+def test_batched_lu_plan_on_the_host(lib):
+    """Three independent instances planned as one launch sequence (their waves share phases):
+    fewer launches than the three plans together, and every instance's factors equal its own
+    plan's result (up to the order of accumulations) and reproduce its matrix within 10 eps."""
+    cases = [("sphere", 1024, 11), ("cube", 1500, 3), ("ellipsoid", 700, 4)]
+    eps = 1e-6
+    hms = [HMatrix(W.points_for(g, n, sd), 64, 2.0, eps, 64) for g, n, sd in cases]
+    Ss = [hm.hm_structure_build(W.points_for(g, n, sd), 64, 2.0) for g, n, sd in cases]
+    single = [S.plan(0, eps, 64) for S in Ss]
+    B = hm.hm_structure_plan_lu_batch(Ss, eps, 64)
+    assert len(B["launches"]) < sum(len(p["launches"]) for p in single)
+    assert len(B["launches"]) >= max(len(p["launches"]) for p in single)
+    assert B["sizes"]["nwaves"] == max(p["sizes"]["nwaves"] for p in single)
+    assert B["sizes"]["ntrunc"] == sum(p["sizes"]["ntrunc"] for p in single)
+    sim = PlanSim(B["sizes"])
+    for hmat, I in zip(hms, B["instances"]):
+        _load(sim, B["leaves"][I["first_leaf"]:I["first_leaf"] + I["nleaves"]], hmat.store)
+    sim.run(B)
+    for hmat, I, P in zip(hms, B["instances"], single):
+        leaves = B["leaves"][I["first_leaf"]:I["first_leaf"] + I["nleaves"]]
+        f = _factor(hmat, sim, leaves)
+        one = PlanSim(P["sizes"])
+        _load(one, P["leaves"], hmat.store)
+        one.run(P)
+        g = _factor(hmat, one, P["leaves"])
+        A = hmat.exact_dense()
+        X = np.random.default_rng(3).standard_normal((hmat.n, 3))
+        assert np.linalg.norm(f.apply_lu(X) - g.apply_lu(X)) / np.linalg.norm(A @ X) < 1e-12
+        assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) <= 10 * eps
