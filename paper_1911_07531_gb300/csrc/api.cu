@@ -97,11 +97,12 @@ size_t op_size(int kind) {
   }
 }
 
-template <class T>
-int upload_vec(hm_ctx* c, Buf& b, const std::vector<T>& v) {
+template <class V>
+int upload_vec(hm_ctx* c, Buf& b, const V& v) {
   if (v.empty()) return HM_OK;
-  if (!dalloc(c, b, v.size() * sizeof(T))) return fail(HM_ENOMEM, "allocator returned NULL (plan upload)");
-  CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  const size_t bytes = v.size() * sizeof(*v.data());
+  if (!dalloc(c, b, bytes)) return fail(HM_ENOMEM, "allocator returned NULL (plan upload)");
+  CU(cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, c->stream));
   return HM_OK;
 }
 

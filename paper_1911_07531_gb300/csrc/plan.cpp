@@ -136,6 +136,20 @@ struct Wave {
       stack_entries.resize(ph + 1);
     }
   }
+  // empty every phase but keep the storage for the next wave
+  void reset() {
+    for (auto& v : getrf) v.clear();
+    for (auto& v : trsm) v.clear();
+    for (auto& v : gemm) v.clear();
+    for (auto& v : copy) v.clear();
+    for (auto& v : stack) v.clear();
+    for (auto& v : core) v.clear();
+    for (auto& v : eval) v.clear();
+    for (auto& v : aca) v.clear();
+    for (auto& v : stack_entries) v.clear();
+    sd = si = 0;
+    nph = 0;
+  }
   int64_t alloc_d(int64_t n) {
     int64_t o = sd;
     sd += align_up(n);
@@ -689,9 +703,8 @@ struct Ctx {
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
       put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
       if (!w.gemm[ph].empty()) {
-        const size_t at = plan.gemm.size();
-        plan.gemm.resize(at + w.gemm[ph].size());
-        gemm_grid_to(w.gemm[ph].data(), (int)w.gemm[ph].size(), plan.gemm.data() + at, plan.launches.back().gy,
+        GemmOp* out = plan.gemm.extend(w.gemm[ph].size());
+        gemm_grid_to(w.gemm[ph].data(), (int)w.gemm[ph].size(), out, plan.launches.back().gy,
                      plan.launches.back().gz);
       }
       if (!w.stack[ph].empty()) {
@@ -719,7 +732,7 @@ struct Ctx {
     plan.scratch_doubles = std::max(plan.scratch_doubles, w.sd);
     plan.scratch_ints = std::max(plan.scratch_ints, w.si);
     plan.nwaves++;
-    w = Wave();
+    w.reset();
     targets.clear();
     target_index.clear();
   }

@@ -2,6 +2,10 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <type_traits>
 #include <vector>
 
 #include "ops.h"
@@ -45,15 +49,88 @@ void gemm_grid(GemmOp* ops, int count, int& gy, int& gz);
 // overlapping ops).
 void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz);
 
+// Growable array of trivially copyable records that grows in place (realloc): the micro-op
+// arrays of a large plan reach gigabytes, and a std::vector would copy and zero-fill them on
+// every doubling.
+template <class T>
+class PodVec {
+  static_assert(std::is_trivially_copyable<T>::value, "PodVec holds trivially copyable records");
+  T* p_ = nullptr;
+  size_t n_ = 0, cap_ = 0;
+  void grow(size_t want) {
+    if (want <= cap_) return;
+    size_t c = cap_ ? cap_ : 64;
+    while (c < want) c *= 2;
+    void* q = std::realloc(p_, c * sizeof(T));
+    if (!q) throw std::bad_alloc();
+    p_ = static_cast<T*>(q);
+    cap_ = c;
+  }
+
+ public:
+  PodVec() = default;
+  PodVec(const PodVec& o) { append(o.p_, o.n_); }
+  PodVec(PodVec&& o) noexcept : p_(o.p_), n_(o.n_), cap_(o.cap_) { o.p_ = nullptr, o.n_ = o.cap_ = 0; }
+  PodVec& operator=(const PodVec& o) {
+    if (this != &o) {
+      n_ = 0;
+      append(o.p_, o.n_);
+    }
+    return *this;
+  }
+  PodVec& operator=(PodVec&& o) noexcept {
+    if (this != &o) {
+      std::free(p_);
+      p_ = o.p_, n_ = o.n_, cap_ = o.cap_;
+      o.p_ = nullptr, o.n_ = o.cap_ = 0;
+    }
+    return *this;
+  }
+  ~PodVec() { std::free(p_); }
+  size_t size() const { return n_; }
+  bool empty() const { return n_ == 0; }
+  T* data() { return p_; }
+  const T* data() const { return p_; }
+  T* begin() { return p_; }
+  T* end() { return p_ + n_; }
+  const T* begin() const { return p_; }
+  const T* end() const { return p_ + n_; }
+  T& operator[](size_t i) { return p_[i]; }
+  const T& operator[](size_t i) const { return p_[i]; }
+  T& back() { return p_[n_ - 1]; }
+  void clear() { n_ = 0; }
+  void push_back(const T& v) {
+    grow(n_ + 1);
+    p_[n_++] = v;
+  }
+  void append(const T* src, size_t k) {
+    if (!k) return;
+    grow(n_ + k);
+    std::memcpy(static_cast<void*>(p_ + n_), src, k * sizeof(T));
+    n_ += k;
+  }
+  template <class It>
+  void insert(T* /* at the end only */, It first, It last) {
+    append(&*first, (size_t)(last - first));
+  }
+  // k uninitialised records at the end, to be written by the caller
+  T* extend(size_t k) {
+    grow(n_ + k);
+    T* r = p_ + n_;
+    n_ += k;
+    return r;
+  }
+};
+
 struct Plan {
-  std::vector<GetrfOp> getrf;
-  std::vector<TrsmOp> trsm;
-  std::vector<GemmOp> gemm;
-  std::vector<CopyOp> copy;
-  std::vector<TruncOp> trunc;      // shared by K_STACK and K_CORE launches
-  std::vector<StackEntry> entries;
-  std::vector<EvalOp> eval;
-  std::vector<AcaOp> aca;
+  PodVec<GetrfOp> getrf;
+  PodVec<TrsmOp> trsm;
+  PodVec<GemmOp> gemm;
+  PodVec<CopyOp> copy;
+  PodVec<TruncOp> trunc;      // shared by K_STACK and K_CORE launches
+  PodVec<StackEntry> entries;
+  PodVec<EvalOp> eval;
+  PodVec<AcaOp> aca;
   std::vector<Launch> launches;    // execution order
   int64_t scratch_doubles = 0;
   int64_t scratch_ints = 0;
