@@ -216,14 +216,18 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
  * (> 0); which = 1: the forward / backward substitution plan for up to nrhs_max (>= 1)
  * right-hand sides; which = 2..5: the product plan of hm_matvec for op = which - 2 (HM_OP_A,
  * HM_OP_L, HM_OP_U, HM_OP_LU) on a work buffer of four n x nrhs_max blocks (x, y, two
- * temporaries). rank_cap: 1..64, the capacity of the low-rank leaves. Replaces an earlier
+ * temporaries); which = 6: the assembly plan of hm_build at accuracy eps (dense leaves by
+ * kernel evaluation, admissible leaves by ACA + rounded truncation, into the matrix-value space
+ * 3 from the permuted points, space 4, n x 3 row-major). rank_cap: 1..64, the capacity of the
+ * low-rank leaves. Replaces an earlier
  * plan of S. HM_EINVAL on bad arguments or an accumulator task graph, HM_EINTERNAL if the
  * planner fails. */
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max);
 
 enum {
   HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz} int32 records, in execution order;
-                            kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core           */
+                            kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core, 6 eval,
+                            7 aca                                                             */
   HM_PLAN_GETRF = 1,     /* the micro-op descriptors of the batched kernels, laid out as the */
   HM_PLAN_TRSM = 2,      /* GetrfOp, TrsmOp, GemmOp, CopyOp, TruncOp and StackEntry structs  */
   HM_PLAN_GEMM = 3,      /* of the library's csrc/ops.h; one TRUNC record serves a stack and */
@@ -236,8 +240,10 @@ enum {
                             V offset (ld n), rank index, pivot offset (-1: none)             */
   HM_PLAN_SIZES = 8,     /* one record of 8 int64: scratch doubles, scratch ints, value
                             doubles, ranks, pivots, rounded additions, waves, phases          */
-  HM_PLAN_INSTANCES = 9  /* per instance, 5 int64: first leaf record, leaf records, value,
+  HM_PLAN_INSTANCES = 9, /* per instance, 5 int64: first leaf record, leaf records, value,
                             rank and pivot offsets (one instance unless batched)              */
+  HM_PLAN_EVAL = 10,     /* EvalOp and AcaOp records of the assembly plan (kinds 6 and 7)     */
+  HM_PLAN_ACA = 11
 };
 
 /* Host-side H-LU plan of count independent structures in one launch sequence (batching

@@ -382,8 +382,12 @@ PLAN_DTYPES = {
     "sizes": _dt([(f, _I8) for f in ("scratch_doubles", "scratch_ints", "nvalues", "nranks", "npiv", "ntrunc",
                                      "nwaves", "nphases")]),
     "instances": _dt([(f, _I8) for f in ("first_leaf", "nleaves", "base_d", "base_r", "base_p")]),
+    "eval": _dt([("D", _U8), ("r0", _I4), ("c0", _I4), ("m", _I4), ("n", _I4)]),
+    "aca": _dt([("r0", _I4), ("c0", _I4), ("m", _I4), ("n", _I4), ("U", _U8), ("V", _U8), ("used", _U8),
+                ("kd", _U8), ("kmax", _I4), ("pad", _I4), ("tol", _F8)]),
 }
-PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves", "sizes", "instances")
+PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves", "sizes", "instances",
+               "eval", "aca")
 
 
 class Structure:

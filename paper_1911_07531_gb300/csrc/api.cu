@@ -1061,10 +1061,10 @@ extern "C" {
 
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
-  if (which < 0 || which > 5) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..5");
+  if (which < 0 || which > 6) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..6");
   if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan: rank_cap must be in 1..64");
-  if (which == 0 && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
-  if (which >= 1 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
+  if ((which == 0 || which == 6) && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
+  if (which >= 1 && which <= 5 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
   for (const Task& t : S->g.nodes)
     if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan: the structure holds an accumulator task graph");
   try {
@@ -1073,8 +1073,10 @@ int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int 
       plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan);
     else if (which == 1)
       plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
-    else
+    else if (which <= 5)
       plan_matvec(S->ct, S->bt, S->lay, which - 2, nrhs_max, S->plan);
+    else
+      plan_build(S->ct, S->bt, S->lay, eps, 160, (int64_t)1 << 28, S->plan);
   } catch (const std::exception& ex) {
     S->planned = false;
     return fail(HM_EINTERNAL, std::string("hm_structure_plan: ") + ex.what());
@@ -1151,6 +1153,8 @@ int hm_structure_plan_table(const hm_structure* S, int table, const void** data,
     case HM_PLAN_LEAVES: return put(S->leaf_table.data(), S->leaf_table.size() / 10, 10 * sizeof(int64_t));
     case HM_PLAN_SIZES: return put(S->sizes.data(), 1, S->sizes.size() * sizeof(int64_t));
     case HM_PLAN_INSTANCES: return put(S->instances.data(), S->instances.size() / 5, 5 * sizeof(int64_t));
+    case HM_PLAN_EVAL: return put(P.eval.data(), P.eval.size(), sizeof(EvalOp));
+    case HM_PLAN_ACA: return put(P.aca.data(), P.aca.size(), sizeof(AcaOp));
     default: return fail(HM_EINVAL, "hm_structure_plan_table: unknown table");
   }
 }

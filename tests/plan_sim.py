@@ -16,7 +16,11 @@ checked against the oracle without a GPU:
   core   from the Gram matrices of W and Z (upper triangles): coefficient matrices T_W, T_Z
          with W T_W = U_k S_k, Z T_Z = V_k for the singular values above eps s_1 (at most
          the cap), and the new rank k. Computed here by symmetric eigendecompositions of the
-         Gram matrices and an SVD of the small core, not by the kernel's algorithm.
+         Gram matrices and an SVD of the small core, not by the kernel's algorithm;
+  eval   a dense leaf 1 / (4 pi (|x_i - x_j| + h)) from the permuted points;
+  aca    a low-rank approximation U V^T of an admissible leaf to the relative tolerance, at most
+         kmax terms (here a truncated SVD of the evaluated block stands in for the cross
+         approximation: any approximation within the tolerance is a valid result).
 
 Every strided access is bounds-checked against its memory space, so a planner address error
 fails loudly here. The oracle is not used by this module.
@@ -28,10 +32,10 @@ import scipy.linalg as sla
 from numpy.lib.stride_tricks import as_strided
 
 MASK = (1 << 60) - 1
-K_GETRF, K_TRSM, K_GEMM, K_COPY, K_STACK, K_CORE = range(6)
+K_GETRF, K_TRSM, K_GEMM, K_COPY, K_STACK, K_CORE, K_EVAL, K_ACA = range(8)
 GF_ATOMIC, GF_OVERWRITE, GF_A_UPPER, GF_A_UNITLOWER, GF_SYM_UPPER = 1, 2, 4, 8, 16
-SP_F, SP_S, SP_X = 0, 1, 2
-IS_RANK, IS_PIV, IS_S = 0, 1, 2
+SP_F, SP_S, SP_X, SP_A, SP_P = 0, 1, 2, 3, 4
+IS_RANK, IS_PIV, IS_S, IS_ARANK = 0, 1, 2, 3
 KMAX_ENTRIES = 256
 
 
@@ -43,6 +47,7 @@ class PlanSim:
                   IS_S: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64)}
         self.cap_hits = 0
         self.singular = 0
+        self.h = None   # kernel regularisation (assembly plans)
 
     # -- addressing ------------------------------------------------------------------------------
     def _space(self, ref, table):
@@ -217,12 +222,30 @@ class PlanSim:
             self.mat(op["Tz"], 1, Kc, K, k)[:] = Rzi @ Yt[:k].T
         self.iset(op["rank"], k)
 
+    def _block(self, r0, c0, m, n):
+        P = self.d[SP_P].reshape(-1, 3)
+        d = np.sqrt(((P[r0:r0 + m, None, :] - P[None, c0:c0 + n, :]) ** 2).sum(-1))
+        return 1.0 / (4.0 * np.pi * (d + self.h))
+
+    def eval(self, op):
+        m, n = int(op["m"]), int(op["n"])
+        self.mat(op["D"], 1, m, m, n)[:] = self._block(int(op["r0"]), int(op["c0"]), m, n)
+
+    def aca(self, op):
+        m, n, kmax, tol = int(op["m"]), int(op["n"]), int(op["kmax"]), float(op["tol"])
+        X, s, Yt = np.linalg.svd(self._block(int(op["r0"]), int(op["c0"]), m, n), full_matrices=False)
+        k = min(int(np.count_nonzero(s > tol * s[0])), kmax) if s[0] > 0 else 0
+        self.mat(op["U"], 1, m, m, k)[:] = X[:, :k] * s[:k]
+        self.mat(op["V"], 1, n, n, k)[:] = Yt[:k].T
+        self.iset(op["kd"], k)
+
     # -- plans -------------------------------------------------------------------------------------
     def run(self, P):
         tables = {K_GETRF: P["getrf"], K_TRSM: P["trsm"], K_GEMM: P["gemm"], K_COPY: P["copy"],
-                  K_STACK: P["trunc"], K_CORE: P["trunc"]}
+                  K_STACK: P["trunc"], K_CORE: P["trunc"], K_EVAL: P.get("eval"), K_ACA: P.get("aca")}
         fns = {K_GETRF: self.getrf, K_TRSM: self.trsm, K_GEMM: self.gemm, K_COPY: self.copy,
-               K_STACK: lambda op: self.stack(op, P["entries"]), K_CORE: self.core}
+               K_STACK: lambda op: self.stack(op, P["entries"]), K_CORE: self.core, K_EVAL: self.eval,
+               K_ACA: self.aca}
         for ln in P["launches"]:
             kind, b, c = int(ln["kind"]), int(ln["begin"]), int(ln["count"])
             ops = tables[kind]

@@ -223,3 +223,49 @@ def test_batched_lu_plan_on_the_host(lib):
         X = np.random.default_rng(3).standard_normal((hmat.n, 3))
         assert np.linalg.norm(f.apply_lu(X) - g.apply_lu(X)) / np.linalg.norm(A @ X) < 1e-12
         assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) <= 10 * eps
+
+
+def test_build_then_lu_plans_on_the_host(lib):
+    """hm_build's assembly plan (dense leaves evaluated, admissible leaves approximated and
+    rounded to eps) gives an H-matrix within eps of the kernel matrix; the H-LU plan run on
+    that H-matrix, as hm_lu copies it, gives factors within 10 eps: the device pipeline's data
+    flow from points to factors, on the host."""
+    from tests.plan_sim import IS_ARANK, SP_A, SP_P
+    pts = W.cube_surface(1500, 7)
+    eps = 1e-6
+    hmat = HMatrix(pts, 64, 2.0, eps, 64)
+    S = hm.hm_structure_build(pts, 64, 2.0)
+    P = S.plan(6, eps, 64)
+    assert len(P["eval"]) and len(P["aca"])
+    sim = PlanSim(P["sizes"])
+    sim.d[SP_A] = np.zeros(int(P["sizes"]["nvalues"]))
+    sim.i[IS_ARANK] = np.zeros(int(P["sizes"]["nranks"]), np.int64)
+    sim.d[SP_P] = np.ascontiguousarray(hmat.points[hmat.ct.perm]).ravel()
+    sim.h = hmat.h
+    sim.run(P)
+    A = hmat.exact_dense()
+    AH = np.zeros_like(A)
+    for lf in P["leaves"]:
+        r0, c0 = hmat.ct.clusters[int(lf["row"])].lo, hmat.ct.clusters[int(lf["col"])].lo
+        m, n = int(lf["m"]), int(lf["n"])
+        if lf["lr"]:
+            k = int(sim.i[IS_ARANK][int(lf["rank_idx"])])
+            assert 0 < k <= int(lf["cap"])
+            U = np.array(sim.mat(ref(SP_A, lf["off"]), 1, m, m, k))
+            V = np.array(sim.mat(ref(SP_A, lf["voff"]), 1, n, n, k))
+            AH[r0:r0 + m, c0:c0 + n] = U @ V.T
+        else:
+            AH[r0:r0 + m, c0:c0 + n] = np.array(sim.mat(ref(SP_A, lf["off"]), 1, m, m, n))
+    assert np.linalg.norm(A - AH) / np.linalg.norm(A) <= eps
+    # the rank of every admissible leaf is the oracle's (its dense SVD truncated at eps)
+    for lf in P["leaves"]:
+        if lf["lr"]:
+            assert int(sim.i[IS_ARANK][int(lf["rank_idx"])]) == hmat.store[(int(lf["row"]), int(lf["col"]))].U.shape[1]
+    Q = S.plan(0, eps, 64)
+    fac = PlanSim(Q["sizes"])
+    fac.d[SP_F] = sim.d[SP_A].copy()
+    fac.i[IS_RANK] = sim.i[IS_ARANK].copy()
+    fac.run(Q)
+    f = _factor(hmat, fac, Q["leaves"])
+    X = np.random.default_rng(3).standard_normal((hmat.n, 3))
+    assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) <= 10 * eps
