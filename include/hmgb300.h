@@ -219,10 +219,10 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
  * temporaries); which = 6: the assembly plan of hm_build at accuracy eps (dense leaves by
  * kernel evaluation, admissible leaves by ACA + rounded truncation, into the matrix-value space
  * 3 from the permuted points, space 4, n x 3 row-major). rank_cap: 1..64, the capacity of the
- * low-rank leaves. Replaces an earlier
- * plan of S. HM_EINVAL on bad arguments or an accumulator task graph, HM_EINTERNAL if the
- * planner fails. */
-int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max);
+ * low-rank leaves. threads: host threads of the H-LU planner (0: all hardware threads; the plan
+ * does not depend on it). Replaces an earlier plan of S. HM_EINVAL on bad arguments or an
+ * accumulator task graph, HM_EINTERNAL if the planner fails. */
+int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads);
 
 enum {
   HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz} int32 records, in execution order;

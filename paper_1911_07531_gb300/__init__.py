@@ -134,7 +134,7 @@ def load_library():
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
-        "hm_structure_plan": ([P, I, D, I, I], I),
+        "hm_structure_plan": ([P, I, D, I, I, I], I),
         "hm_structure_plan_lu_batch": ([P, I, D, I], I),
         "hm_structure_plan_table": ([P, I, PP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
@@ -393,10 +393,12 @@ PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", 
 class Structure:
     """Host-only cluster tree, block tree and H-LU task graph (no GPU needed)."""
 
-    def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1):
-        """Host plan (which 0: H-LU at eps, 1: solve for nrhs_max right-hand sides) as a dict of
-        numpy record arrays, one per table of ``PLAN_TABLES``."""
-        _check(load_library().hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max)))
+    def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1, threads=0):
+        """Host plan (which 0: H-LU at eps, 1: solve for nrhs_max right-hand sides, 2..5: matvec,
+        6: assembly) as a dict of numpy record arrays, one per table of ``PLAN_TABLES``; threads:
+        host threads of the H-LU planner (0: all)."""
+        _check(load_library().hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max),
+                                                int(threads)))
         return self.plan_tables()
 
     def plan_tables(self, names=PLAN_TABLES):

@@ -58,7 +58,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                       "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, f), "-o", o], o))
     for f in cpp:
         o = os.path.join(OUT_DIR, f + ".o")
-        jobs.append((["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *inc, "-c",
+        jobs.append((["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", *inc, "-c",
                       os.path.join(CSRC, f), "-o", o], o))
 
     def run(cmd):
@@ -72,7 +72,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, [j[0] for j in jobs]))
     tmp = LIB + ".tmp"
-    link = [nvcc, GENCODE, "-shared", "-o", tmp, *[j[1] for j in jobs], "-lcudart"]
+    link = [nvcc, GENCODE, "-shared", "-o", tmp, *[j[1] for j in jobs], "-lcudart", "-lpthread"]
     run(link)
     os.replace(tmp, LIB)
     return LIB

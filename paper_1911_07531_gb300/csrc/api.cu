@@ -1059,18 +1059,19 @@ void append_leaf_table(const Layout& lay, int64_t bd, int64_t br, int64_t bp, st
 
 extern "C" {
 
-int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max) {
+int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
   if (which < 0 || which > 6) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..6");
   if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan: rank_cap must be in 1..64");
   if ((which == 0 || which == 6) && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
   if (which >= 1 && which <= 5 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
+  if (threads < 0) return fail(HM_EINVAL, "hm_structure_plan: threads must be >= 0");
   for (const Task& t : S->g.nodes)
     if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan: the structure holds an accumulator task graph");
   try {
     build_layout(S->ct, S->bt, rank_cap, S->lay);
     if (which == 0)
-      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan);
+      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads);
     else if (which == 1)
       plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
     else if (which <= 5)

@@ -19,11 +19,14 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <stdexcept>
+#include <string>
+#include <thread>
 
 namespace hm {
 
@@ -790,18 +793,146 @@ std::vector<std::vector<int>> by_level(const TaskGraph& g) {
   for (size_t i = 0; i < g.nodes.size(); ++i) byl[g.level[i]].push_back((int)i);
   return byl;
 }
+
+// Appends the plans of consecutive wave ranges to `plan` in order: launch begins and the
+// entry ranges of stack records are made global, counters summed, scratch sizes maximised.
+// The copies of the parts run in parallel (each part has its own destination range).
+void concat_plans(std::vector<Plan>& parts, Plan& plan, int threads) {
+  const size_t np = parts.size();
+  struct Off {
+    size_t getrf, trsm, gemm, copy, trunc, entries, eval, aca, launches;
+  };
+  std::vector<Off> off(np + 1);
+  off[0] = {plan.getrf.size(), plan.trsm.size(), plan.gemm.size(), plan.copy.size(), plan.trunc.size(),
+            plan.entries.size(), plan.eval.size(), plan.aca.size(), plan.launches.size()};
+  for (size_t k = 0; k < np; ++k) {
+    const Plan& q = parts[k];
+    off[k + 1] = {off[k].getrf + q.getrf.size(), off[k].trsm + q.trsm.size(),     off[k].gemm + q.gemm.size(),
+                  off[k].copy + q.copy.size(),   off[k].trunc + q.trunc.size(),   off[k].entries + q.entries.size(),
+                  off[k].eval + q.eval.size(),   off[k].aca + q.aca.size(),       off[k].launches + q.launches.size()};
+  }
+  const Off& end = off[np];
+  plan.getrf.extend(end.getrf - off[0].getrf);
+  plan.trsm.extend(end.trsm - off[0].trsm);
+  plan.gemm.extend(end.gemm - off[0].gemm);
+  plan.copy.extend(end.copy - off[0].copy);
+  plan.trunc.extend(end.trunc - off[0].trunc);
+  plan.entries.extend(end.entries - off[0].entries);
+  plan.eval.extend(end.eval - off[0].eval);
+  plan.aca.extend(end.aca - off[0].aca);
+  plan.launches.resize(end.launches);
+  auto put = [&](size_t k) {
+    const Plan& q = parts[k];
+    const Off& o = off[k];
+    auto cp = [](auto& dst, size_t at, const auto& src) {
+      if (src.size()) std::memcpy(static_cast<void*>(dst.data() + at), src.data(), src.size() * sizeof(*src.data()));
+    };
+    cp(plan.getrf, o.getrf, q.getrf);
+    cp(plan.trsm, o.trsm, q.trsm);
+    cp(plan.gemm, o.gemm, q.gemm);
+    cp(plan.copy, o.copy, q.copy);
+    cp(plan.trunc, o.trunc, q.trunc);
+    cp(plan.entries, o.entries, q.entries);
+    cp(plan.eval, o.eval, q.eval);
+    cp(plan.aca, o.aca, q.aca);
+    for (size_t l = 0; l < q.launches.size(); ++l) {
+      Launch L = q.launches[l];
+      size_t base = 0;
+      switch (L.kind) {
+        case K_GETRF: base = o.getrf; break;
+        case K_TRSM: base = o.trsm; break;
+        case K_GEMM: base = o.gemm; break;
+        case K_COPY: base = o.copy; break;
+        case K_STACK:
+        case K_CORE: base = o.trunc; break;
+        case K_EVAL: base = o.eval; break;
+        default: base = o.aca; break;
+      }
+      if (L.kind == K_STACK)
+        for (int r = 0; r < L.count; ++r) plan.trunc[base + L.begin + r].first_entry += (int)o.entries;
+      L.begin += (int)base;
+      plan.launches[o.launches + l] = L;
+    }
+  };
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t k; (k = next.fetch_add(1)) < np;) put(k);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (const Plan& q : parts) {
+    plan.scratch_doubles = std::max(plan.scratch_doubles, q.scratch_doubles);
+    plan.scratch_ints = std::max(plan.scratch_ints, q.scratch_ints);
+    plan.scratch_products_max = std::max(plan.scratch_products_max, q.scratch_products_max);
+    plan.scratch_trunc_max = std::max(plan.scratch_trunc_max, q.scratch_trunc_max);
+    plan.nwaves += q.nwaves;
+    plan.nphases += q.nphases;
+    plan.ntasks += q.ntasks;
+    plan.ntrunc += q.ntrunc;
+  }
+}
+
+int plan_threads(int threads) {
+  if (threads > 0) return threads;
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h, 64u));
+}
 }  // namespace
 
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
-             Plan& plan) {
+             Plan& plan, int threads) {
   plan = Plan();
   const auto byl = by_level(g);
-  Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
-  for (int lv = 0; lv < g.nlevels; ++lv) {
-    for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
-    c.emit_truncations(3, eps);
-    c.flush();
+  threads = plan_threads(threads);
+  if (threads == 1 || g.nlevels < 64) {
+    Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
+    for (int lv = 0; lv < g.nlevels; ++lv) {
+      for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
+      c.emit_truncations(3, eps);
+      c.flush();
+    }
+    return;
   }
+  // Waves are planned independently (scratch is per wave), so consecutive ranges of waves are
+  // planned on several threads and concatenated in order: the result equals the sequential plan.
+  const int nparts = std::min(g.nlevels, 8 * threads);
+  std::vector<int> first(nparts + 1, g.nlevels);
+  {
+    const double per = (double)g.nodes.size() / nparts;
+    int lv = 0;
+    size_t done = 0;
+    for (int k = 0; k < nparts; ++k) {
+      first[k] = lv;
+      while (lv < g.nlevels && (done < (size_t)((k + 1) * per) || lv == first[k])) done += byl[lv++].size();
+    }
+    first[nparts] = g.nlevels;
+  }
+  std::vector<Plan> parts(nparts);
+  std::vector<std::string> errors(nparts);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (int k; (k = next.fetch_add(1)) < nparts;) {
+      try {
+        Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, parts[k]);
+        for (int lv = first[k]; lv < first[k + 1]; ++lv) {
+          for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
+          c.emit_truncations(3, eps);
+          c.flush();
+        }
+      } catch (const std::exception& ex) {
+        errors[k] = ex.what();
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (const std::string& e : errors)
+    if (!e.empty()) throw std::runtime_error(e);
+  concat_plans(parts, plan, threads);
 }
 
 void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan) {

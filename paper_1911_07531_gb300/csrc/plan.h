@@ -148,9 +148,11 @@ struct Spaces {
   int r;   // IS_RANK or IS_ARANK
 };
 
-// H-LU: every wave of the levelled task graph expanded into phases of micro-ops.
+// H-LU: every wave of the levelled task graph expanded into phases of micro-ops. threads: host
+// threads that plan ranges of waves in parallel (0: all hardware threads); any value gives the
+// same plan.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
-             double eps, Plan& plan);
+             double eps, Plan& plan, int threads = 0);
 // Independent H-LU instances in one plan: wave w of every instance is expanded into the same
 // phases, so that one launch per kind and phase serves all of them (their task graphs have no
 // edges between each other). Instance i addresses its values, ranks and pivots at the given

@@ -131,3 +131,16 @@ def test_plan_export_errors(lib):
     assert P["sizes"]["nwaves"] == S.info["nlevels"] and len(P["leaves"]) == S.info["nleaves"]
     k = P["launches"]["kind"]
     assert set(k.tolist()) <= set(range(6)) and (P["launches"]["count"] > 0).all()
+
+
+def test_parallel_planner_equals_sequential(lib):
+    """Ranges of waves planned on several host threads and concatenated give the sequential plan
+    byte for byte (launch list, every micro-op table, sizes)."""
+    S = hm.hm_structure_build(W.fibonacci_sphere(8192, 21), 64, 2.0)
+    ref = S.plan(0, 1e-6, 64, threads=1)
+    assert ref["sizes"]["nwaves"] >= 64
+    for t in (3, 8):
+        P = S.plan(0, 1e-6, 64, threads=t)
+        for name in ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves"):
+            assert P[name].tobytes() == ref[name].tobytes(), (t, name)
+        assert P["sizes"].tobytes() == ref["sizes"].tobytes()
