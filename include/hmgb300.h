@@ -118,6 +118,11 @@ typedef struct {
 /* Last error message of the calling thread ("" if none). */
 const char* hm_last_error(void);
 
+/* Host threads used by task-graph construction (the parallel loops of Alg 13, §4.2) and by the
+ * H-LU planner, for every later call of the process (0, the default: all hardware threads).
+ * The task graph and the plan do not depend on it. HM_EINVAL if threads < 0. */
+int hm_set_host_threads(int threads);
+
 /* Context: device ordinal, a cudaStream_t (NULL = the legacy default stream) and the
  * allocator callbacks (both NULL = cudaMalloc / cudaFree). */
 int hm_ctx_create(int device, void* cuda_stream, hm_alloc_fn alloc, hm_free_fn free_fn, void* user,
@@ -219,8 +224,8 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
  * temporaries); which = 6: the assembly plan of hm_build at accuracy eps (dense leaves by
  * kernel evaluation, admissible leaves by ACA + rounded truncation, into the matrix-value space
  * 3 from the permuted points, space 4, n x 3 row-major). rank_cap: 1..64, the capacity of the
- * low-rank leaves. threads: host threads of the H-LU planner (0: all hardware threads; the plan
- * does not depend on it). Replaces an earlier plan of S. HM_EINVAL on bad arguments or an
+ * low-rank leaves. threads: host threads of the H-LU planner (0: the hm_set_host_threads
+ * setting; the plan does not depend on it). Replaces an earlier plan of S. HM_EINVAL on bad arguments or an
  * accumulator task graph, HM_EINTERNAL if the planner fails. */
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads);
 

@@ -24,7 +24,8 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
-    "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_plan_lu_batch", "header_functions",
+    "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_plan_lu_batch", "hm_set_host_threads",
+    "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
 ]
 
@@ -135,6 +136,7 @@ def load_library():
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
         "hm_structure_plan": ([P, I, D, I, I, I], I),
+        "hm_set_host_threads": ([I], I),
         "hm_structure_plan_lu_batch": ([P, I, D, I], I),
         "hm_structure_plan_table": ([P, I, PP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], I),
         "hm_structure_info_get": ([P, ctypes.POINTER(StructureInfo)], I),
@@ -454,6 +456,11 @@ def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0, merged=False):
     _check(load_library().hm_structure_build_accumulator(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
                                                          int(bool(merged)), ctypes.byref(h)))
     return Structure(h)
+
+
+def hm_set_host_threads(threads=0):
+    """Host threads of task-graph construction and planning (0: all hardware threads)."""
+    _check(load_library().hm_set_host_threads(int(threads)))
 
 
 def hm_structure_plan_lu_batch(structures, eps=1e-6, rank_cap=64, names=PLAN_TABLES):

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -23,6 +24,8 @@ using namespace hm;
 namespace {
 
 thread_local std::string g_err;
+// host threads of task-graph construction and planning (0: all hardware threads)
+std::atomic<int> g_host_threads{0};
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -509,14 +512,14 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   CU(cudaSetDevice(c->device));
   try {
     if (!A->dag_built) {
-      build_task_graph(A->ct, A->bt, A->dag);
+      build_task_graph(A->ct, A->bt, A->dag, false, g_host_threads.load());
       if (!compute_levels(A->dag)) return fail(HM_EINTERNAL, "hm_lu: task graph has a cycle");
       A->dag_built = true;
     }
     if (A->lu_plan.eps != eps) {
       free_plan(c, A->lu_plan);
       auto t0 = std::chrono::steady_clock::now();
-      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host);
+      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load());
       A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       A->lu_plan.eps = eps;
     }
@@ -1006,12 +1009,12 @@ int hm_structure_build(const double* pts, int64_t n, int leaf_size, double eta, 
   try {
     build_cluster_tree(pts, n, leaf_size, S->ct);
     build_block_tree(S->ct, eta, S->bt);
-    build_task_graph(S->ct, S->bt, S->g);
+    build_task_graph(S->ct, S->bt, S->g, false, g_host_threads.load());
     if (!compute_levels(S->g)) return fail(HM_EINTERNAL, "hm_structure_build: task graph has a cycle");
     if (with_plan) {
       Layout lay;
       build_layout(S->ct, S->bt, 64, lay);
-      plan_lu(S->ct, S->bt, lay, S->g, 1e-6, S->plan);
+      plan_lu(S->ct, S->bt, lay, S->g, 1e-6, S->plan, g_host_threads.load());
       S->planned = true;
     }
   } catch (const std::exception& ex) {
@@ -1032,9 +1035,9 @@ int hm_structure_build_accumulator(const double* pts, int64_t n, int leaf_size, 
     build_cluster_tree(pts, n, leaf_size, S->ct);
     build_block_tree(S->ct, eta, S->bt);
     if (merged)
-      build_merged_accumulator_graph(S->ct, S->bt, S->g);
+      build_merged_accumulator_graph(S->ct, S->bt, S->g, g_host_threads.load());
     else
-      build_task_graph(S->ct, S->bt, S->g, true);
+      build_task_graph(S->ct, S->bt, S->g, true, g_host_threads.load());
     if (!compute_levels(S->g)) return fail(HM_EINTERNAL, "hm_structure_build_accumulator: task graph has a cycle");
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_structure_build_accumulator: ") + ex.what());
@@ -1059,6 +1062,12 @@ void append_leaf_table(const Layout& lay, int64_t bd, int64_t br, int64_t bp, st
 
 extern "C" {
 
+int hm_set_host_threads(int threads) {
+  if (threads < 0) return fail(HM_EINVAL, "hm_set_host_threads: threads must be >= 0");
+  g_host_threads.store(threads);
+  return HM_OK;
+}
+
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
   if (which < 0 || which > 6) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..6");
@@ -1071,7 +1080,7 @@ int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int 
   try {
     build_layout(S->ct, S->bt, rank_cap, S->lay);
     if (which == 0)
-      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads);
+      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads ? threads : g_host_threads.load());
     else if (which == 1)
       plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
     else if (which <= 5)

@@ -4,9 +4,11 @@
 #include "structure.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <deque>
 #include <functional>
+#include <thread>
 
 namespace hm {
 
@@ -228,142 +230,211 @@ struct DagBuilder {
     int id = bt.find(r, c);
     return bt.nodes[id].is_leaf();
   }
-  int add(int type, int a, int b, int c) {
-    tasks.push_back({type, a, b, c});
-    succ.emplace_back();
-    sub_first.push_back(-1);
-    sub_count.push_back(0);
-    if (accu) {
-      int r = a, s = b;
-      if (type == T_TRSU) r = b, s = a;
-      if (type == T_MUL) s = c;
-      int node = bt.find(r, s);
-      acc_self.push_back(node);
-      acc_par.push_back(parent_node[node]);
-    }
-    return (int)tasks.size() - 1;
-  }
-  // accumulator mode: apply_upd of a leaf before the task that factorises or solves with it
-  void add_sub(int type, int a, int b, int c) {
-    if (accu && type != T_MUL) {
-      int r = type == T_TRSU ? b : a, s = type == T_TRSU ? a : b;
-      if (leaf_block(r, s)) add(T_APPLY, r, s, -1);
-    }
-    add(type, a, b, c);
-  }
   // recursive bodies of Alg 2, Alg 3, its upper mirror and Alg 1 (Alg 7, Alg 8 and its mirror,
-  // Alg 4 in accumulator mode), in program order
-  void generate(int g) {
-    Task t = tasks[g];
-    if (t.type == T_SHIFT || t.type == T_APPLY) return;
-    int first = (int)tasks.size();
+  // Alg 4 in accumulator mode), in program order: the sub-tasks of task g (none for a task on
+  // leaves); at most MAX_SUB
+  static constexpr int MAX_SUB = 12;
+  int list_subtasks(int g, Task* out) const {
+    const Task t = tasks[g];
+    if (t.type == T_SHIFT || t.type == T_APPLY) return 0;
+    int n = 0;
+    auto put = [&](int type, int a, int b, int c) { out[n++] = {type, a, b, c}; };
+    // accumulator mode: apply_upd of a leaf before the task that factorises or solves with it
+    auto sub = [&](int type, int a, int b, int c) {
+      if (accu && type != T_MUL) {
+        int r = type == T_TRSU ? b : a, q = type == T_TRSU ? a : b;
+        if (leaf_block(r, q)) put(T_APPLY, r, q, -1);
+      }
+      put(type, a, b, c);
+    };
     const Cluster& A = ct.cl[t.a];
     if (t.type == T_LU) {
-      if (leaf_block(t.a, t.a)) return;
+      if (leaf_block(t.a, t.a)) return 0;
       int t0 = A.son0, t1 = A.son1;
-      if (accu) add(T_SHIFT, t.a, t.a, -1);
-      add_sub(T_LU, t0, t0, -1);
-      add_sub(T_TRSU, t0, t1, -1);
-      add_sub(T_TRSL, t0, t1, -1);
-      add_sub(T_MUL, t1, t0, t1);
-      add_sub(T_LU, t1, t1, -1);
+      if (accu) put(T_SHIFT, t.a, t.a, -1);
+      sub(T_LU, t0, t0, -1);
+      sub(T_TRSU, t0, t1, -1);
+      sub(T_TRSL, t0, t1, -1);
+      sub(T_MUL, t1, t0, t1);
+      sub(T_LU, t1, t1, -1);
     } else if (t.type == T_TRSL) {
-      if (leaf_block(t.a, t.b)) return;
+      if (leaf_block(t.a, t.b)) return 0;
       const Cluster& S = ct.cl[t.b];
       int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
-      if (accu) add(T_SHIFT, t.a, t.b, -1);
-      add_sub(T_TRSL, t0, s0, -1);
-      add_sub(T_TRSL, t0, s1, -1);
-      add_sub(T_MUL, t1, t0, s0);
-      add_sub(T_MUL, t1, t0, s1);
-      add_sub(T_TRSL, t1, s0, -1);
-      add_sub(T_TRSL, t1, s1, -1);
+      if (accu) put(T_SHIFT, t.a, t.b, -1);
+      sub(T_TRSL, t0, s0, -1);
+      sub(T_TRSL, t0, s1, -1);
+      sub(T_MUL, t1, t0, s0);
+      sub(T_MUL, t1, t0, s1);
+      sub(T_TRSL, t1, s0, -1);
+      sub(T_TRSL, t1, s1, -1);
     } else if (t.type == T_TRSU) {
-      if (leaf_block(t.b, t.a)) return;
+      if (leaf_block(t.b, t.a)) return 0;
       const Cluster& S = ct.cl[t.b];
       int t0 = A.son0, t1 = A.son1, s0 = S.son0, s1 = S.son1;
-      if (accu) add(T_SHIFT, t.b, t.a, -1);
-      add_sub(T_TRSU, t0, s0, -1);
-      add_sub(T_TRSU, t0, s1, -1);
-      add_sub(T_MUL, s0, t0, t1);
-      add_sub(T_MUL, s1, t0, t1);
-      add_sub(T_TRSU, t1, s0, -1);
-      add_sub(T_TRSU, t1, s1, -1);
+      if (accu) put(T_SHIFT, t.b, t.a, -1);
+      sub(T_TRSU, t0, s0, -1);
+      sub(T_TRSU, t0, s1, -1);
+      sub(T_MUL, s0, t0, t1);
+      sub(T_MUL, s1, t0, t1);
+      sub(T_TRSU, t1, s0, -1);
+      sub(T_TRSU, t1, s1, -1);
     } else {
-      if (leaf_block(t.a, t.b) || leaf_block(t.b, t.c) || leaf_block(t.a, t.c)) return;
+      if (leaf_block(t.a, t.b) || leaf_block(t.b, t.c) || leaf_block(t.a, t.c)) return 0;
       const Cluster& R = ct.cl[t.b];
       const Cluster& C = ct.cl[t.c];
       int ai[2] = {A.son0, A.son1}, bl[2] = {R.son0, R.son1}, cj[2] = {C.son0, C.son1};
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
-          for (int l = 0; l < 2; ++l) add(T_MUL, ai[i], bl[l], cj[j]);
+          for (int l = 0; l < 2; ++l) put(T_MUL, ai[i], bl[l], cj[j]);
     }
-    int cnt = (int)tasks.size() - first;
+    return n;
+  }
+  // the accumulator identifiers of task k's block and of its parent block
+  void set_acc(int k) {
+    const Task& t = tasks[k];
+    int r = t.a, q = t.b;
+    if (t.type == T_TRSU) r = t.b, q = t.a;
+    if (t.type == T_MUL) q = t.c;
+    const int node = bt.find(r, q);
+    acc_self[k] = node;
+    acc_par[k] = parent_node[node];
+  }
+  // writes the cnt sub-tasks of g at indices [first, first + cnt) (already allocated) with the
+  // automatic local edges t_i -> t_j for i < j whenever Def 3.2 holds
+  void place(int g, int first, const Task* sub, int cnt) {
+    for (int i = 0; i < cnt; ++i) {
+      tasks[first + i] = sub[i];
+      if (accu) set_acc(first + i);
+    }
+    if (cnt == 0) return;
     sub_first[g] = first;
     sub_count[g] = cnt;
-    // automatic local edges: t_i -> t_j for i < j whenever Def 3.2 holds
     for (int i = 0; i < cnt; ++i)
       for (int j = i + 1; j < cnt; ++j)
         if (precedes(first + i, first + j)) succ[first + i].push_back(first + j);
   }
+  // room for `extra` more tasks
+  void grow(size_t extra) {
+    const size_t n = tasks.size() + extra;
+    tasks.resize(n);
+    succ.resize(n);
+    sub_first.resize(n, -1);
+    sub_count.resize(n, 0);
+    if (accu) {
+      acc_self.resize(n, -1);
+      acc_par.resize(n, -1);
+    }
+  }
+  // Alg 9 / Alg 10 for task w of the current work list: returns 0 if w retires, 1 if it stays
+  // (an unrefined task whose successors were refined), 2 if it was refined
+  int refine(int w, std::vector<int>& newsucc) {
+    if (sub_count[w] == 0) {
+      // Alg 10: refine the dependencies of an unrefined task
+      bool changed = false;
+      newsucc.clear();
+      for (int x : succ[w]) {
+        if (sub_count[x] > 0) {
+          changed = true;
+          for (int s = sub_first[x]; s < sub_first[x] + sub_count[x]; ++s)
+            if (precedes(w, s)) newsucc.push_back(s);
+        } else if (precedes(w, x)) {
+          newsucc.push_back(x);
+        }
+      }
+      succ[w] = newsucc;
+      return changed ? 1 : 0;
+    }
+    // Alg 9: inherit the dependencies on the sub-tasks
+    const int f = sub_first[w], cnt = sub_count[w];
+    for (int x : succ[w]) {
+      int xf = x, xc = 1;
+      if (sub_count[x] > 0) {
+        xf = sub_first[x];
+        xc = sub_count[x];
+      }
+      for (int tp = f; tp < f + cnt; ++tp)
+        for (int q = xf; q < xf + xc; ++q)
+          if (precedes(tp, q)) succ[tp].push_back(q);
+    }
+    return 2;
+  }
 };
+
+// fn(i) for i in [0, n) on `threads` threads (chunks handed out in order; serial when small)
+template <class F>
+void parallel_for(size_t n, int threads, F fn) {
+  if (threads <= 1 || n < 2048) {
+    for (size_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  const size_t chunk = std::max<size_t>(256, n / ((size_t)threads * 8));
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t b; (b = next.fetch_add(chunk)) < n;)
+      for (size_t i = b; i < std::min(n, b + chunk); ++i) fn(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+}
 
 }  // namespace
 
-void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators) {
+// Alg 11 with the parallel loops of Alg 13: in every iteration the sub-tasks of all work tasks
+// are generated (sizes first, then places by a prefix sum, so that task indices do not depend on
+// the thread count), then the dependencies of every work task are refined; each step writes only
+// data of its own task and its sub-tasks. The result equals the serial construction.
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators, int threads) {
   auto t0 = std::chrono::steady_clock::now();
   g = TaskGraph();
   if (ct.cl.empty()) return;
+  if (threads <= 0) threads = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
   DagBuilder b(ct, bt, accumulators);
   b.tasks.reserve(1 << 16);
-  int root = b.add(T_LU, 0, 0, -1);
-  std::vector<int> work{root}, next;
-  std::vector<int> retired;
-  std::vector<int> newsucc;
+  b.grow(1);
+  b.tasks[0] = {T_LU, 0, 0, -1};
+  if (accumulators) b.set_acc(0);
+  std::vector<int> work{0}, next, retired, cnt, first, flag;
+  std::vector<Task> lists;
   while (!work.empty()) {
-    for (int w : work) b.generate(w);
-    next.clear();
-    for (int w : work) {
-      if (b.sub_count[w] == 0) {
-        // Alg 10: refine the dependencies of an unrefined task
-        bool changed = false;
-        newsucc.clear();
-        for (int x : b.succ[w]) {
-          if (b.sub_count[x] > 0) {
-            changed = true;
-            for (int s = b.sub_first[x]; s < b.sub_first[x] + b.sub_count[x]; ++s)
-              if (b.precedes(w, s)) newsucc.push_back(s);
-          } else if (b.precedes(w, x)) {
-            newsucc.push_back(x);
-          }
-        }
-        b.succ[w] = newsucc;
-        if (changed)
-          next.push_back(w);
-        else
-          retired.push_back(w);
-      } else {
-        // Alg 9: inherit the dependencies on the sub-tasks
-        int f = b.sub_first[w], cnt = b.sub_count[w];
-        for (int x : b.succ[w]) {
-          int xf = x, xc = 1;
-          if (b.sub_count[x] > 0) {
-            xf = b.sub_first[x];
-            xc = b.sub_count[x];
-          }
-          for (int tp = f; tp < f + cnt; ++tp)
-            for (int s = xf; s < xf + xc; ++s)
-              if (b.precedes(tp, s)) b.succ[tp].push_back(s);
-        }
-        for (int tp = f; tp < f + cnt; ++tp) next.push_back(tp);
-      }
+    const size_t nw = work.size();
+    cnt.assign(nw, 0);
+    lists.resize(nw * DagBuilder::MAX_SUB);
+    parallel_for(nw, threads, [&](size_t i) { cnt[i] = b.list_subtasks(work[i], &lists[i * DagBuilder::MAX_SUB]); });
+    first.resize(nw);
+    size_t total = 0;
+    const int base = (int)b.tasks.size();
+    for (size_t i = 0; i < nw; ++i) {
+      first[i] = base + (int)total;
+      total += cnt[i];
     }
-    // refined tasks leave the graph; mark them so that no stale reference survives
-    for (int w : work)
-      if (b.sub_count[w] > 0) std::vector<int>().swap(b.succ[w]);
-    // sub-task counts only describe refinement within one iteration of Alg 11
-    for (int w : work)
-      if (b.sub_count[w] > 0) b.sub_count[w] = -1;
+    b.grow(total);
+    parallel_for(nw, threads,
+                 [&](size_t i) { b.place(work[i], first[i], &lists[i * DagBuilder::MAX_SUB], cnt[i]); });
+    flag.assign(nw, 0);
+    parallel_for(nw, threads, [&](size_t i) {
+      thread_local std::vector<int> scratch;
+      flag[i] = b.refine(work[i], scratch);
+    });
+    next.clear();
+    for (size_t i = 0; i < nw; ++i) {
+      const int w = work[i];
+      if (flag[i] == 0)
+        retired.push_back(w);
+      else if (flag[i] == 1)
+        next.push_back(w);
+      else
+        for (int tp = b.sub_first[w]; tp < b.sub_first[w] + b.sub_count[w]; ++tp) next.push_back(tp);
+    }
+    // refined tasks leave the graph; sub-task counts only describe refinement within one
+    // iteration of Alg 11
+    for (size_t i = 0; i < nw; ++i)
+      if (flag[i] == 2) {
+        std::vector<int>().swap(b.succ[work[i]]);
+        b.sub_count[work[i]] = -1;
+      }
     work.swap(next);
   }
   // compact the retired tasks into the output graph
@@ -373,17 +444,20 @@ void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, 
     remap[r] = (int)g.nodes.size();
     g.nodes.push_back(b.tasks[r]);
   }
-  size_t ne = 0;
-  for (int r : retired) ne += b.succ[r].size();
-  g.edges.reserve(ne);
-  for (int r : retired)
-    for (int s : b.succ[r]) g.edges.emplace_back(remap[r], remap[s]);
+  std::vector<size_t> eoff(retired.size() + 1, 0);
+  for (size_t i = 0; i < retired.size(); ++i) eoff[i + 1] = eoff[i] + b.succ[retired[i]].size();
+  g.edges.resize(eoff.back());
+  parallel_for(retired.size(), threads, [&](size_t i) {
+    const int r = retired[i];
+    size_t e = eoff[i];
+    for (int q : b.succ[r]) g.edges[e++] = {remap[r], remap[q]};
+  });
   g.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-void build_merged_accumulator_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g) {
+void build_merged_accumulator_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, int threads) {
   auto t0 = std::chrono::steady_clock::now();
-  build_task_graph(ct, bt, g, false);
+  build_task_graph(ct, bt, g, false, threads);
   if (g.nodes.empty()) return;
   const int nlu = (int)g.nodes.size();
   // the accumulator handling alone: one task per block-tree node, parent -> sons

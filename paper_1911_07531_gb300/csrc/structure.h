@@ -81,11 +81,14 @@ void collect_leaves(const BlockTree& bt, int node, std::vector<int>& out);
 // accumulator-based H-LU (§3.2, Table 2) -- a refined hlu / htrsl / htrsu starts with
 // shift_upd of its block, apply_upd of a leaf precedes the task that factorises or solves with
 // it, add_upd is refined like hmul and writes the block and its accumulator.
-void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators = false);
+// threads: host threads of the parallel loops of Alg 13 (0: all hardware threads); the graph
+// does not depend on it.
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators = false,
+                      int threads = 0);
 // The accumulator task graph built in two parts (§4.3): the standard graph (hmul tasks stand for
 // add_upd) plus one shift_upd / apply_upd task per block-tree node, linked by edges parent ->
 // son, add_upd -> accumulator task of its destination, apply_upd of a leaf -> its leaf task.
-void build_merged_accumulator_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g);
+void build_merged_accumulator_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, int threads = 0);
 // longest-path levels; returns false if the graph has a cycle
 bool compute_levels(TaskGraph& g);
 

@@ -144,3 +144,30 @@ def test_parallel_planner_equals_sequential(lib):
         for name in ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves"):
             assert P[name].tobytes() == ref[name].tobytes(), (t, name)
         assert P["sizes"].tobytes() == ref["sizes"].tobytes()
+
+
+def test_parallel_task_graph_equals_serial(lib):
+    """The parallel loops of Alg 13 give the serial construction's graph: same task order, same
+    edge order, same levels, for the standard and both accumulator graphs (sizes at which the
+    work lists are split across threads)."""
+    pts = W.fibonacci_sphere(8192, 21)
+    builds = (lambda: hm.hm_structure_build(pts, 64, 2.0),
+              lambda: hm.hm_structure_build_accumulator(pts, 64, 2.0),
+              lambda: hm.hm_structure_build_accumulator(pts, 64, 2.0, merged=True))
+    try:
+        for make in builds:
+            hm.hm_set_host_threads(1)
+            ref = make().export()
+            for t in (3, 8):
+                hm.hm_set_host_threads(t)
+                got = make().export()
+                for name in ("tasks", "edges", "levels"):
+                    assert np.array_equal(got[name], ref[name]), (t, name)
+    finally:
+        hm.hm_set_host_threads(0)
+    with pytest.raises(hm.HMError):
+        hm.hm_set_host_threads(-1)
+
+
+def test_parallel_task_graph_bit_exact_with_oracle_at_8192(lib):
+    _compare(W.fibonacci_sphere(8192, 21), 64, 2.0)
