@@ -30,6 +30,24 @@
 
 namespace hm {
 
+namespace {
+// worker() on the calling thread and on up to threads - 1 more (fewer if the system refuses
+// to start them); returns when all have finished
+template <class F>
+void run_workers(int threads, F worker) {
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {
+      break;
+    }
+  }
+  worker();
+  for (auto& th : pool) th.join();
+}
+}  // namespace
+
 void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz) {
   // Dynamic sizes (ranks) are not known here: each micro-op carries an expected value in
   // `split` (0: 16). A CTA should get at least ~16k FMAs (8k cycles of one SM's FP64 pipe) and
@@ -855,13 +873,9 @@ void concat_plans(std::vector<Plan>& parts, Plan& plan, int threads) {
     }
   };
   std::atomic<size_t> next{0};
-  auto worker = [&]() {
+  run_workers(threads, [&]() {   // only copies: nothing here throws
     for (size_t k; (k = next.fetch_add(1)) < np;) put(k);
-  };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto& th : pool) th.join();
+  });
   for (const Plan& q : parts) {
     plan.scratch_doubles = std::max(plan.scratch_doubles, q.scratch_doubles);
     plan.scratch_ints = std::max(plan.scratch_ints, q.scratch_ints);
@@ -923,13 +937,12 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
         }
       } catch (const std::exception& ex) {
         errors[k] = ex.what();
+      } catch (...) {
+        errors[k] = "unknown error";
       }
     }
   };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto& th : pool) th.join();
+  run_workers(threads, worker);
   for (const std::string& e : errors)
     if (!e.empty()) throw std::runtime_error(e);
   concat_plans(parts, plan, threads);

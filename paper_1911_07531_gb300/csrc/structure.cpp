@@ -7,7 +7,9 @@
 #include <atomic>
 #include <chrono>
 #include <deque>
+#include <exception>
 #include <functional>
+#include <mutex>
 #include <thread>
 
 namespace hm {
@@ -361,7 +363,8 @@ struct DagBuilder {
   }
 };
 
-// fn(i) for i in [0, n) on `threads` threads (chunks handed out in order; serial when small)
+// fn(i) for i in [0, n) on `threads` threads (chunks handed out in order; serial when small);
+// an exception of any worker is rethrown on the calling thread after all have stopped
 template <class F>
 void parallel_for(size_t n, int threads, F fn) {
   if (threads <= 1 || n < 2048) {
@@ -370,14 +373,29 @@ void parallel_for(size_t n, int threads, F fn) {
   }
   const size_t chunk = std::max<size_t>(256, n / ((size_t)threads * 8));
   std::atomic<size_t> next{0};
+  std::exception_ptr err;
+  std::mutex err_mu;
   auto worker = [&]() {
-    for (size_t b; (b = next.fetch_add(chunk)) < n;)
-      for (size_t i = b; i < std::min(n, b + chunk); ++i) fn(i);
+    try {
+      for (size_t b; (b = next.fetch_add(chunk)) < n;)
+        for (size_t i = b; i < std::min(n, b + chunk); ++i) fn(i);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
+    }
   };
   std::vector<std::thread> pool;
-  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  for (int t = 1; t < threads; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {   // no more threads: the ones started and the caller share the work
+      break;
+    }
+  }
   worker();
   for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
 }
 
 }  // namespace
