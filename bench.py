@@ -294,11 +294,14 @@ def main():
     t0 = time.perf_counter()
     bh = torch.from_numpy(W.gaussian_rhs(n, 1, cfg["rhs_seed"])[:, 0]).pin_memory()
     A2 = hm.hm_build(ctx, pts, cfg["leaf"], cfg["eta"], cfg["eps"], cfg["rank_cap"])
+    t1 = time.perf_counter()
     F2 = hm.hm_lu(ctx, A2)
+    t2 = time.perf_counter()
     bd = bh.to(f"cuda:{local}", non_blocking=True)
     xd, _ = hm.hm_solve(ctx, F2, bd)
     xh = xd.cpu()
     e2e_s = time.perf_counter() - t0
+    e2e_split = {"build_s": t1 - t0, "lu_s": t2 - t1, "solve_s": e2e_s - (t2 - t0)}
     e2e_flops = sum(F2.stats()["flops"][:4])
     F2.free()
     A2.free()
@@ -350,8 +353,9 @@ def main():
             "solve_latency_ms": {"p50": p50, "p99": p99, "nrhs": 1},
             "e2e": {"value": e2e_flops / e2e_s * 1e-9, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": int(pts.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
-                    "seconds": e2e_s, "includes": "hm_build (points H2D, trees, ACA) + hm_lu (task graph, "
-                                                  "plan, execution) + hm_solve with host RHS and result"},
+                    "seconds": e2e_s, "split": e2e_split,
+                    "includes": "hm_build (points H2D, trees, ACA) + hm_lu (task graph, "
+                                "plan, execution) + hm_solve with host RHS and result"},
             "gpu_launches": launches,
             "roofline": roofline,
             "clocks": clk.summary(),
