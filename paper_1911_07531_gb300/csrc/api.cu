@@ -1127,7 +1127,7 @@ int hm_structure_plan_lu_batch(hm_structure* const* S, int count, double eps, in
       br += S[i]->lay.nranks;
       bp += S[i]->lay.npiv;
     }
-    plan_lu_batch(inst, eps, H->plan);
+    plan_lu_batch(inst, eps, H->plan, g_host_threads.load());
   } catch (const std::exception& ex) {
     H->planned = false;
     H->sizes.clear();

@@ -893,84 +893,104 @@ int plan_threads(int threads) {
   const unsigned h = std::thread::hardware_concurrency();
   return (int)std::max(1u, std::min(h, 64u));
 }
-}  // namespace
 
-void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
-             Plan& plan, int threads) {
-  plan = Plan();
-  const auto byl = by_level(g);
+// Plans waves [0, nlev) with plan_range(part, lv0, lv1), which plans the waves [lv0, lv1) into
+// `part` in order. Waves are planned independently (scratch and rounded-addition targets are
+// per wave), so consecutive ranges, balanced by the tasks per wave, are planned on several
+// threads and concatenated in order: the result equals planning all waves in one range.
+template <class F>
+void plan_wave_ranges(int nlev, const std::vector<size_t>& tasks_per_wave, int threads, F plan_range, Plan& plan) {
   threads = plan_threads(threads);
-  if (threads == 1 || g.nlevels < 64) {
-    Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, plan);
-    for (int lv = 0; lv < g.nlevels; ++lv) {
-      for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
-      c.emit_truncations(3, eps);
-      c.flush();
-    }
+  if (threads == 1 || nlev < 64) {
+    plan_range(plan, 0, nlev);
     return;
   }
-  // Waves are planned independently (scratch is per wave), so consecutive ranges of waves are
-  // planned on several threads and concatenated in order: the result equals the sequential plan.
-  const int nparts = std::min(g.nlevels, 8 * threads);
-  std::vector<int> first(nparts + 1, g.nlevels);
+  size_t total = 0;
+  for (size_t t : tasks_per_wave) total += t;
+  const int nparts = std::min(nlev, 8 * threads);
+  std::vector<int> first(nparts + 1, nlev);
   {
-    const double per = (double)g.nodes.size() / nparts;
+    const double per = (double)total / nparts;
     int lv = 0;
     size_t done = 0;
     for (int k = 0; k < nparts; ++k) {
       first[k] = lv;
-      while (lv < g.nlevels && (done < (size_t)((k + 1) * per) || lv == first[k])) done += byl[lv++].size();
+      while (lv < nlev && (done < (size_t)((k + 1) * per) || lv == first[k])) done += tasks_per_wave[lv++];
     }
-    first[nparts] = g.nlevels;
+    first[nparts] = nlev;
   }
   std::vector<Plan> parts(nparts);
   std::vector<std::string> errors(nparts);
   std::atomic<int> next{0};
-  auto worker = [&]() {
+  run_workers(threads, [&]() {
     for (int k; (k = next.fetch_add(1)) < nparts;) {
       try {
-        Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, parts[k]);
-        for (int lv = first[k]; lv < first[k + 1]; ++lv) {
-          for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
-          c.emit_truncations(3, eps);
-          c.flush();
-        }
+        plan_range(parts[k], first[k], first[k + 1]);
       } catch (const std::exception& ex) {
         errors[k] = ex.what();
       } catch (...) {
         errors[k] = "unknown error";
       }
     }
-  };
-  run_workers(threads, worker);
+  });
   for (const std::string& e : errors)
     if (!e.empty()) throw std::runtime_error(e);
   concat_plans(parts, plan, threads);
 }
+}  // namespace
 
-void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan) {
+void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
+             Plan& plan, int threads) {
   plan = Plan();
-  Wave w;
-  std::vector<std::unique_ptr<Ctx>> cs;
+  const auto byl = by_level(g);
+  std::vector<size_t> per(g.nlevels);
+  for (int lv = 0; lv < g.nlevels; ++lv) per[lv] = byl[lv].size();
+  plan_wave_ranges(
+      g.nlevels, per, threads,
+      [&](Plan& part, int lv0, int lv1) {
+        Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, part);
+        for (int lv = lv0; lv < lv1; ++lv) {
+          for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
+          c.emit_truncations(3, eps);
+          c.flush();
+        }
+      },
+      plan);
+}
+
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads) {
+  plan = Plan();
+  if (inst.empty()) return;
   std::vector<std::vector<std::vector<int>>> byl;
   int nlev = 0;
   for (const LuInstance& I : inst) {
-    cs.emplace_back(new Ctx(*I.ct, *I.bt, *I.lay, Spaces{SP_F, IS_RANK}, plan, w));
-    cs.back()->base_d = I.base_d;
-    cs.back()->base_r = I.base_r;
-    cs.back()->base_p = I.base_p;
     byl.push_back(by_level(*I.g));
     nlev = std::max(nlev, I.g->nlevels);
   }
-  if (cs.empty()) return;
-  for (int lv = 0; lv < nlev; ++lv) {
-    for (size_t i = 0; i < inst.size(); ++i)
-      if (lv < inst[i].g->nlevels)
-        for (int ti : byl[i][lv]) expand_task(*cs[i], inst[i].g->nodes[ti]);
-    // every instance's rounded additions of this wave share the phases after the products
-    for (auto& c : cs) c->emit_truncations(3, eps);
-    cs[0]->flush();
-  }
+  std::vector<size_t> per(nlev, 0);
+  for (size_t i = 0; i < inst.size(); ++i)
+    for (int lv = 0; lv < inst[i].g->nlevels; ++lv) per[lv] += byl[i][lv].size();
+  plan_wave_ranges(
+      nlev, per, threads,
+      [&](Plan& part, int lv0, int lv1) {
+        Wave w;
+        std::vector<std::unique_ptr<Ctx>> cs;
+        for (const LuInstance& I : inst) {
+          cs.emplace_back(new Ctx(*I.ct, *I.bt, *I.lay, Spaces{SP_F, IS_RANK}, part, w));
+          cs.back()->base_d = I.base_d;
+          cs.back()->base_r = I.base_r;
+          cs.back()->base_p = I.base_p;
+        }
+        for (int lv = lv0; lv < lv1; ++lv) {
+          for (size_t i = 0; i < inst.size(); ++i)
+            if (lv < inst[i].g->nlevels)
+              for (int ti : byl[i][lv]) expand_task(*cs[i], inst[i].g->nodes[ti]);
+          // every instance's rounded additions of this wave share the phases after the products
+          for (auto& c : cs) c->emit_truncations(3, eps);
+          cs[0]->flush();
+        }
+      },
+      plan);
 }
 
 // ------------------------------------------------------------------------------ build

@@ -164,7 +164,7 @@ struct LuInstance {
   const TaskGraph* g;
   int64_t base_d, base_r, base_p;
 };
-void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan);
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads = 0);
 // hm_build: dense leaf assembly, ACA + rounded truncation of the admissible leaves.
 void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, double eps, int aca_kmax,
                 int64_t scratch_budget_doubles, Plan& plan);

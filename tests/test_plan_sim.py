@@ -203,7 +203,15 @@ def test_batched_lu_plan_on_the_host(lib):
     hms = [HMatrix(W.points_for(g, n, sd), 64, 2.0, eps, 64) for g, n, sd in cases]
     Ss = [hm.hm_structure_build(W.points_for(g, n, sd), 64, 2.0) for g, n, sd in cases]
     single = [S.plan(0, eps, 64) for S in Ss]
-    B = hm.hm_structure_plan_lu_batch(Ss, eps, 64)
+    try:   # the batched planner splits ranges of waves across host threads: same plan
+        hm.hm_set_host_threads(1)
+        B1 = hm.hm_structure_plan_lu_batch(Ss, eps, 64)
+        hm.hm_set_host_threads(6)
+        B = hm.hm_structure_plan_lu_batch(Ss, eps, 64)
+    finally:
+        hm.hm_set_host_threads(0)
+    for name in ("launches", "gemm", "trunc", "entries", "copy", "trsm", "getrf", "leaves", "instances"):
+        assert B[name].tobytes() == B1[name].tobytes(), name
     assert len(B["launches"]) < sum(len(p["launches"]) for p in single)
     assert len(B["launches"]) >= max(len(p["launches"]) for p in single)
     assert B["sizes"]["nwaves"] == max(p["sizes"]["nwaves"] for p in single)
