@@ -144,6 +144,17 @@ void hm_matrix_free(hm_matrix* A);
 int hm_lu(hm_ctx* ctx, hm_matrix* A, const hm_lu_opts* opts, hm_factor** out);
 void hm_factor_free(hm_factor* F);
 
+/* H-LU of count independent matrices in one launch sequence (batching across instances): wave
+ * w of every matrix's task graph is expanded into the same phases, so that one launch per
+ * kernel kind and phase serves all of them. out[i] receives the factor of A[i], usable and
+ * freed like one from hm_lu. The matrices are factored in consecutive groups that fit 85 % of
+ * the device memory free at the call (values, ranks, pivots and the group's plan and scratch);
+ * the factors of a group share one allocation, released with the last of them. A factor's
+ * stats (seconds, flops, launches) are those of its group. opts->eps <= 0 needs all matrices
+ * built with the same eps. Errors as hm_lu; on an error other than HM_ESINGULAR no factor is
+ * returned. */
+int hm_lu_batch(hm_ctx* ctx, hm_matrix* const* A, int count, const hm_lu_opts* opts, hm_factor** out);
+
 /* x = (P L U)^{-1} b for nrhs right-hand sides (device, column-major, leading dimension
  * ld, original order). b and x may alias. With opts->max_iter > 0 and A != NULL, iterative
  * refinement against op(A) (opts->residual_op) runs until the relative residual of every

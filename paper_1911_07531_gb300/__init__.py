@@ -23,7 +23,7 @@ from .build import LIB, build as _build_lib
 
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
-    "hm_ctx_create", "hm_build", "hm_lu", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
+    "hm_ctx_create", "hm_build", "hm_lu", "hm_lu_batch", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
     "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
@@ -126,6 +126,7 @@ def load_library():
         "hm_build": ([P, P, I64, ctypes.POINTER(BuildOpts), PP], I),
         "hm_matrix_free": ([P], V),
         "hm_lu": ([P, P, ctypes.POINTER(LuOpts), PP], I),
+        "hm_lu_batch": ([P, P, I, ctypes.POINTER(LuOpts), P], I),
         "hm_factor_free": ([P], V),
         "hm_solve": ([P, P, P, P, P, I64, I64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)], I),
         "hm_matvec": ([P, P, P, I, D, P, D, P, I64, I64], I),
@@ -283,6 +284,22 @@ def hm_lu(ctx, A, eps=0.0, allow_singular=False):
             F.free()
         _check(rc)
     return F
+
+
+def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False):
+    """H-LU of several independent matrices whose waves share kernel launches; one factor each."""
+    n = len(matrices)
+    hs = (ctypes.c_void_p * n)(*[A.handle for A in matrices])
+    outs = (ctypes.c_void_p * n)()
+    o = LuOpts(float(eps), 0)
+    rc = load_library().hm_lu_batch(ctx.handle, hs, n, ctypes.byref(o), outs)
+    Fs = [HFactor(ctx, ctypes.c_void_p(outs[i]), A) if outs[i] else None for i, A in enumerate(matrices)]
+    if rc != 0 and not (rc == -4 and allow_singular and all(F is not None for F in Fs)):
+        for F in Fs:
+            if F is not None:
+                F.free()
+        _check(rc)
+    return Fs
 
 
 def hm_solve(ctx, F, b, x=None, A=None, refine_tol=0.0, max_iter=0, residual_op=HM_OP_A):

@@ -241,11 +241,19 @@ struct hm_matrix {
   int64_t aca_unconverged = 0;
 };
 
+// One allocation of factor values, ranks and pivots shared by the factors of a batch
+// (hm_lu_batch); freed with the last of them.
+struct SharedArena {
+  Buf vals, ranks, piv;
+  int refs = 0;
+};
+
 struct hm_factor {
   hm_ctx* ctx = nullptr;
   hm_matrix* A = nullptr;
   double eps = 0.0;
-  Buf vals, ranks, piv;
+  Buf vals, ranks, piv;     // own buffers, or views into `arena`
+  SharedArena* arena = nullptr;
   DevPlan solve_plan;
   DevPlan mv_plan;
   Buf work;   // SP_X buffer of the solve / matvec plans
@@ -614,10 +622,184 @@ void hm_factor_free(hm_factor* F) {
   free_plan(c, F->solve_plan);
   free_plan(c, F->mv_plan);
   dfree(c, F->work);
-  dfree(c, F->vals);
-  dfree(c, F->ranks);
-  dfree(c, F->piv);
+  if (F->arena) {
+    if (--F->arena->refs == 0) {
+      dfree(c, F->arena->vals);
+      dfree(c, F->arena->ranks);
+      dfree(c, F->arena->piv);
+      delete F->arena;
+    }
+  } else {
+    dfree(c, F->vals);
+    dfree(c, F->ranks);
+    dfree(c, F->piv);
+  }
   delete F;
+}
+
+int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, hm_factor** out) {
+  if (!c || !A || !out || count < 1) return fail(HM_EINVAL, "hm_lu_batch: bad argument");
+  for (int i = 0; i < count; ++i) {
+    if (!A[i]) return fail(HM_EINVAL, "hm_lu_batch: NULL matrix");
+    out[i] = nullptr;
+  }
+  if (o && o->precision != 0) return fail(HM_EINVAL, "hm_lu_batch: only precision 0 (FP64) is available");
+  const bool given = o && o->eps > 0.0;
+  const double eps = given ? o->eps : A[0]->opts.eps;
+  for (int i = 0; i < count; ++i)
+    if (!given && A[i]->opts.eps != eps)
+      return fail(HM_EINVAL, "hm_lu_batch: matrices of different eps need opts->eps");
+  CU(cudaSetDevice(c->device));
+  try {
+    for (int i = 0; i < count; ++i)
+      if (!A[i]->dag_built) {
+        build_task_graph(A[i]->ct, A[i]->bt, A[i]->dag, false, g_host_threads.load());
+        if (!compute_levels(A[i]->dag)) return fail(HM_EINTERNAL, "hm_lu_batch: task graph has a cycle");
+        A[i]->dag_built = true;
+      }
+  } catch (const std::exception& ex) {
+    return fail(HM_EINTERNAL, std::string("hm_lu_batch: ") + ex.what());
+  }
+  size_t free_b = 0, total_b = 0;
+  CU(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.85 * (double)free_b;
+  std::vector<hm_factor*> made;
+  auto abort_all = [&](int rc) {
+    for (hm_factor* f : made) hm_factor_free(f);
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    return rc;
+  };
+  int singular = 0;
+  for (int i0 = 0; i0 < count;) {
+    // the next group: as many of the remaining instances as fit the device-memory budget
+    int i1 = count;
+    DevPlan dp;
+    std::vector<int64_t> bd, br, bp;
+    for (;;) {
+      std::vector<LuInstance> inst;
+      bd.assign(1, 0);
+      br.assign(1, 0);
+      bp.assign(1, 0);
+      for (int i = i0; i < i1; ++i) {
+        inst.push_back({&A[i]->ct, &A[i]->bt, &A[i]->lay, &A[i]->dag, bd.back(), br.back(), bp.back()});
+        bd.push_back(bd.back() + (A[i]->lay.nvalues + 31) / 32 * 32);
+        br.push_back(br.back() + A[i]->lay.nranks);
+        bp.push_back(bp.back() + A[i]->lay.npiv);
+      }
+      try {
+        plan_lu_batch(inst, eps, dp.host, g_host_threads.load());
+      } catch (const std::exception& ex) {
+        return abort_all(fail(HM_EINTERNAL, std::string("hm_lu_batch: ") + ex.what()));
+      }
+      const Plan& P = dp.host;
+      const double ops = (double)P.gemm.size() * sizeof(GemmOp) + (double)P.trunc.size() * sizeof(TruncOp) +
+                         (double)P.entries.size() * sizeof(StackEntry) + (double)P.copy.size() * sizeof(CopyOp) +
+                         (double)P.trsm.size() * sizeof(TrsmOp) + (double)P.getrf.size() * sizeof(GetrfOp);
+      const double need = 8.0 * bd.back() + 4.0 * (br.back() + bp.back()) + 8.0 * P.scratch_doubles +
+                          4.0 * P.scratch_ints + ops;
+      if (need <= budget || i1 - i0 == 1) break;
+      i1 = i0 + (i1 - i0 + 1) / 2;
+    }
+    int rc = upload(c, dp);
+    if (rc) {
+      free_plan(c, dp);
+      return abort_all(rc);
+    }
+    SharedArena* ar = new SharedArena;
+    Buf sd, si;
+    Counters k;
+    auto cleanup = [&](int r) {
+      free_plan(c, dp);
+      dfree(c, sd);
+      dfree(c, si);
+      dfree(c, k.b);
+      if (ar->refs == 0) {
+        dfree(c, ar->vals);
+        dfree(c, ar->ranks);
+        dfree(c, ar->piv);
+        delete ar;
+      }
+      return abort_all(r);
+    };
+    const Plan& P = dp.host;
+    if (!dalloc(c, ar->vals, (size_t)bd.back() * 8) || !dalloc(c, ar->ranks, std::max<int64_t>(1, br.back()) * 4) ||
+        !dalloc(c, ar->piv, std::max<int64_t>(1, bp.back()) * 4) ||
+        !dalloc(c, sd, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
+        !dalloc(c, si, std::max<int64_t>(1, P.scratch_ints) * 4))
+      return cleanup(fail(HM_ENOMEM, "hm_lu_batch: allocator returned NULL"));
+    if ((rc = counters_init(c, k))) return cleanup(rc);
+    cudaStream_t s = c->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t ce = cudaSuccess;
+    for (int i = i0; i < i1 && !ce; ++i) {
+      const int q = i - i0;
+      ce = cudaMemcpyAsync((char*)ar->vals.p + 8 * bd[q], A[i]->vals.p, A[i]->lay.nvalues * 8,
+                           cudaMemcpyDeviceToDevice, s);
+      if (!ce && A[i]->lay.nranks)
+        ce = cudaMemcpyAsync((char*)ar->ranks.p + 4 * br[q], A[i]->ranks.p, A[i]->lay.nranks * 4,
+                             cudaMemcpyDeviceToDevice, s);
+    }
+    if (ce) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cleanup(fail(HM_ECUDA, std::string("hm_lu_batch: copy of A: ") + cudaGetErrorString(ce)));
+    }
+    Bases B = make_bases();
+    B.d[SP_F] = (double*)ar->vals.p;
+    B.d[SP_S] = (double*)sd.p;
+    B.i[IS_RANK] = (int*)ar->ranks.p;
+    B.i[IS_PIV] = (int*)ar->piv.p;
+    B.i[IS_S] = (int*)si.p;
+    B.flops = k.flops();
+    B.status = k.status();
+    rc = run_plan(c, dp, B, 0.0, nullptr);
+    cudaEventRecord(e1, s);
+    cudaError_t se = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return cleanup(rc);
+    if (se) return cleanup(fail(HM_ECUDA, std::string("hm_lu_batch: ") + cudaGetErrorString(se)));
+    unsigned long long fl[NCOUNT];
+    int st[4];
+    if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
+    singular += st[0];
+    for (int i = i0; i < i1; ++i) {
+      const int q = i - i0;
+      hm_factor* F = new hm_factor;
+      F->ctx = c;
+      F->A = A[i];
+      F->eps = eps;
+      F->arena = ar;
+      ar->refs++;
+      F->vals = Buf{(char*)ar->vals.p + 8 * bd[q], (size_t)A[i]->lay.nvalues * 8};
+      F->ranks = Buf{(char*)ar->ranks.p + 4 * br[q], (size_t)A[i]->lay.nranks * 4};
+      F->piv = Buf{(char*)ar->piv.p + 4 * bp[q], (size_t)A[i]->lay.npiv * 4};
+      made.push_back(F);
+      out[i] = F;
+      // time, counters and launches are those of the whole group
+      fill_matrix_stats(A[i], &F->st);
+      F->st.eps = eps;
+      F->st.seconds = ms * 1e-3;
+      for (int f = 0; f < 5; ++f) F->st.flops[f] = (double)fl[f];
+      F->st.singular_pivots = st[0];
+      F->st.rank_cap_hits = st[1];
+      for (int kk = 0; kk < NKIND; ++kk) F->st.kind_flops[kk] = (double)fl[NFC + kk];
+      F->st.launches = (int64_t)P.launches.size();
+      if ((rc = read_ranks(c, F->ranks, A[i]->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
+    }
+    free_plan(c, dp);
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, k.b);
+    i0 = i1;
+  }
+  if (singular > 0) return fail(HM_ESINGULAR, "hm_lu_batch: zero pivot in a diagonal leaf");
+  return HM_OK;
 }
 
 }  // extern "C"

@@ -171,3 +171,10 @@ def test_parallel_task_graph_equals_serial(lib):
 
 def test_parallel_task_graph_bit_exact_with_oracle_at_8192(lib):
     _compare(W.fibonacci_sphere(8192, 21), 64, 2.0)
+
+
+def test_lu_batch_rejects_bad_arguments_without_a_device(lib):
+    """hm_lu_batch validates its arguments before touching the device."""
+    outs = (ctypes.c_void_p * 1)()
+    assert lib.hm_lu_batch(None, None, 1, None, outs) == -1
+    assert lib.hm_lu_batch(None, (ctypes.c_void_p * 1)(), 0, None, outs) == -1
