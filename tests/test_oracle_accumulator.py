@@ -10,6 +10,7 @@ from oracle.accu import AccuHLUFactor
 from oracle.geometry import kernel_block
 from oracle.hlu import HLUFactor
 from oracle.hmatrix import HMatrix, LowRank
+from oracle.trees import BlockTree, ClusterTree
 from tests.test_oracle_pins import _permute_within_leaf_rows
 
 
@@ -328,3 +329,32 @@ def test_accumulator_formats_truncation_order():
     counts = [c(hm).factor().stats.truncations
               for c in (AccuHLUFactor, CoarseAccuHLUFactor, LowRankAccuHLUFactor, HLUFactor)]
     assert counts[0] <= counts[1] < counts[2] < counts[3]
+
+
+def test_accumulator_edges_of_the_paper_figure():
+    """The edges that accumulator handling induces in H-LU, before and after refinement, as the
+    figure of §4.1 on sparsification draws them: shift_upd(A_tt) precedes hlu(t0) and
+    htrsu(t0, t1) (through shift_upd(A_t1t0) once refined); after refinement shift_upd(A_tt) ->
+    shift_upd(A_t0t0) -> hlu(t00) and shift_upd(A_tt) -> shift_upd(A_t1t0) -> the htrsu tasks of
+    t00. Two levels below the root, no admissible block (the line, eta = 0)."""
+    ct = ClusterTree(W.line_points(256), 64)
+    bt = BlockTree(ct, 0.0)
+    r = ct.root
+    t0, t1 = r.sons
+    t00 = t0.sons[0]
+    t10, t11 = t1.sons
+    nodes, edges = D.AccuTaskGraphBuilder(ct, bt).compute_dag()
+    E = set(edges)
+    sh = lambda a, b: (D.SHIFT, a.id, b.id, -1)
+    assert (sh(r, r), sh(t0, t0)) in E
+    assert (sh(t0, t0), (D.LU, t00.id, t00.id, -1)) in E
+    assert (sh(r, r), sh(t1, t0)) in E
+    assert (sh(t1, t0), (D.TRSU, t00.id, t10.id, -1)) in E
+    assert (sh(t1, t0), (D.TRSU, t00.id, t11.id, -1)) in E
+    # before refinement: the same dependencies on the unrefined tasks
+    b = D.AccuTaskGraphBuilder(ct, bt)
+    root = (D.LU, r.id, r.id, -1)
+    sub = b.subtasks(root)
+    assert sub[0] == sh(r, r)
+    assert b.precedes(sub[0], (D.LU, t0.id, t0.id, -1))
+    assert b.precedes(sub[0], (D.TRSU, t0.id, t1.id, -1))
