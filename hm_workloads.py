@@ -83,6 +83,34 @@ def ellipsoid_instances(count: int = 64, seed: int = 41, n_min: int = 4096, n_ma
     return [(int(n), ellipsoid(int(n), seed * 1000 + i)) for i, n in enumerate(ns)]
 
 
+def serving_requests(count: int = 2000, rate: float = 200.0, seed: int = 51, n_min: int = 2048,
+                     n_max: int = 131072, repeat_fraction: float = 0.5) -> list:
+    """The request stream of the serving workload: Poisson arrivals at `rate` per second; a
+    request either factors and solves a new problem (sphere or cube 50/50, n log-uniform in
+    [n_min, n_max], eps 1e-4 or 1e-6 50/50) or, with probability `repeat_fraction` once a factor
+    exists, solves again with an earlier problem's factor; 1..32 right-hand sides (uniform).
+    Returns dicts with rid, arrival (s), geometry, n, eps, nrhs, seed (points), rhs_seed and
+    repeat_of (the rid whose factor is reused, or None)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    firsts = []
+    for rid in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        nrhs = int(rng.integers(1, 33))
+        if firsts and rng.random() < repeat_fraction:
+            src = out[firsts[int(rng.integers(0, len(firsts)))]]
+            out.append(dict(rid=rid, arrival=t, geometry=src["geometry"], n=src["n"], eps=src["eps"], nrhs=nrhs,
+                            seed=src["seed"], rhs_seed=seed * 100000 + rid, repeat_of=src["rid"]))
+            continue
+        n = int(np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        out.append(dict(rid=rid, arrival=t, geometry="sphere" if rng.random() < 0.5 else "cube", n=n,
+                        eps=1e-4 if rng.random() < 0.5 else 1e-6, nrhs=nrhs, seed=seed * 100000 + rid,
+                        rhs_seed=seed * 100000 + 50000 + rid, repeat_of=None))
+        firsts.append(rid)
+    return out
+
+
 def line_points(n: int) -> np.ndarray:
     """n points evenly spaced on [0,1] along the x axis (exact halving under bisection)."""
     p = np.zeros((n, 3), dtype=np.float64)
