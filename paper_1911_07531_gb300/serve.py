@@ -195,8 +195,9 @@ class GpuExecutor:
             A = hm_build(ctx, W.points_for(r["geometry"], r["n"], r["seed"]), self.leaf, self.eta, r["eps"],
                          self.rank_cap)
             F = hm_lu(ctx, A)
-        st = F.stats()
-        nbytes = 2.0 * st["value_bytes"] + st["scratch_bytes"]
+        # resident: the matrix and factor values and the matrix's uploaded H-LU plan (~19 kB of
+        # micro-ops per point); the factorization's scratch is released when hm_lu returns
+        nbytes = 2.0 * F.stats()["value_bytes"] + 19_000.0 * r["n"]
         return (slot, A, F), nbytes
 
     def solve(self, slot, handle, r):
