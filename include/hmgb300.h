@@ -225,6 +225,15 @@ int hm_structure_build(const double* points_xyz, int64_t n, int leaf_size, doubl
  * No plan. Errors as hm_structure_build. */
 int hm_structure_build_accumulator(const double* points_xyz, int64_t n, int leaf_size, double eta, int merged,
                                    hm_structure** out);
+/* The standard (accumulators == 0) or accumulator (§3.2) task graph built with the removal of
+ * redundant edges of Alg 12 (§4.1) after every refinement step: an edge of a task (or of its
+ * sub-tasks) goes when its target is also reached by a path of length >= 2 inside the task's
+ * neighbourhood (its sub-tasks and its successors' sub-tasks). For the standard graph the
+ * reachability, and so every longest-path level, is unchanged; for the accumulator graph the
+ * removal can drop the ordering of an accumulator before its sons' (the hazard §4.1 points
+ * out), so such a graph is for inspection only. No plan. Errors as hm_structure_build. */
+int hm_structure_build_sparsified(const double* points_xyz, int64_t n, int leaf_size, double eta, int accumulators,
+                                  hm_structure** out);
 int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
 
 /* Host-side plan of a structure built by hm_structure_build (the standard task graph), for

@@ -98,7 +98,8 @@ class TaskGraphBuilder:
         return out
 
     # -- Alg 11 with Alg 9 (refine_sub_deps) and Alg 10 (refine_loc_deps) ---------------
-    def compute_dag(self, root_task=None):
+    def compute_dag(self, root_task=None, sparsify=False):
+        """Alg 11; with sparsify, every iteration ends with Alg 12 on each task of the work set."""
         if root_task is None:
             r = self.ct.root.id
             root_task = (LU, r, r, -1)
@@ -114,6 +115,7 @@ class TaskGraphBuilder:
                 for i, ti in enumerate(vg):
                     succ[ti] = [tj for tj in vg[i + 1:] if self.precedes(ti, tj)]
             nxt = []
+            retire = []
             for g in work:
                 vg = sub[g]
                 if not vg:
@@ -128,8 +130,7 @@ class TaskGraphBuilder:
                     if any(sub.get(x) for x in old):
                         nxt.append(g)
                     else:
-                        nodes.append(g)
-                        edges.extend((g, s) for s in new)
+                        retire.append(g)
                 else:
                     for x in succ[g]:  # refine_sub_deps(g)
                         cand = sub.get(x) or [x]
@@ -138,11 +139,46 @@ class TaskGraphBuilder:
                                 if self.precedes(tp, s):
                                     succ[tp].append(s)
                     nxt.extend(vg)
+            if sparsify:
+                for g in work:
+                    self._sparsify(g, sub, succ)
+            for g in retire:
+                nodes.append(g)
+                edges.extend((g, s) for s in succ[g])
             for g in work:
                 if sub[g]:
                     del succ[g]
             work = nxt
         return nodes, edges
+
+    # -- §4.1, Alg 12: removal of redundant edges inside a task's neighbourhood ---------------------
+    @staticmethod
+    def _sparsify(t, sub, succ):
+        """The neighbourhood N is t's sub-tasks (or t) and, for every successor, its sub-tasks (or
+        the successor). Every edge (t', s) of t's sub-tasks (or of t) whose target s is also
+        reached by a path of length at least two inside N is removed (bfs_2 of Alg 12)."""
+        vt = sub[t]
+        N = set(vt) if vt else {t}
+        for s in succ[t]:
+            vs = sub.get(s)
+            N.update(vs if vs else (s,))
+        for tp in (vt if vt else [t]):
+            seen = set()
+            stack = []
+            for s in succ[tp]:
+                if s in N:
+                    for u in succ.get(s, ()):
+                        if u in N and u not in seen:
+                            seen.add(u)
+                            stack.append(u)
+            while stack:
+                v = stack.pop()
+                for u in succ.get(v, ()):
+                    if u in N and u not in seen:
+                        seen.add(u)
+                        stack.append(u)
+            if seen:
+                succ[tp] = [s for s in succ[tp] if s not in seen]
 
 
 def canonical(nodes, edges):

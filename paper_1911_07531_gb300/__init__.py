@@ -24,7 +24,8 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_lu_batch", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
-    "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_plan_lu_batch", "hm_set_host_threads",
+    "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_build_sparsified",
+    "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
     "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
 ]
@@ -136,6 +137,7 @@ def load_library():
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
+        "hm_structure_build_sparsified": ([P, I64, I, D, I, PP], I),
         "hm_structure_plan": ([P, I, D, I, I, I], I),
         "hm_set_host_threads": ([I], I),
         "hm_structure_plan_lu_batch": ([P, I, D, I], I),
@@ -465,6 +467,14 @@ class Structure:
                 self.handle = None
         except Exception:
             pass
+
+
+def hm_structure_build_sparsified(points, leaf_size=64, eta=2.0, accumulators=False):
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load_library().hm_structure_build_sparsified(p.ctypes.data, p.shape[0], int(leaf_size), float(eta),
+                                                        int(bool(accumulators)), ctypes.byref(h)))
+    return Structure(h)
 
 
 def hm_structure_build_accumulator(points, leaf_size=64, eta=2.0, merged=False):

@@ -1244,6 +1244,25 @@ void append_leaf_table(const Layout& lay, int64_t bd, int64_t br, int64_t bp, st
 
 extern "C" {
 
+int hm_structure_build_sparsified(const double* pts, int64_t n, int leaf_size, double eta, int accumulators,
+                                  hm_structure** out) {
+  if (!pts || !out || n < 1) return fail(HM_EINVAL, "hm_structure_build_sparsified: bad argument");
+  if (leaf_size < 1 || leaf_size > 64)
+    return fail(HM_EINVAL, "hm_structure_build_sparsified: leaf_size must be in 1..64");
+  auto S = std::make_unique<hm_structure>();
+  S->n = n;
+  try {
+    build_cluster_tree(pts, n, leaf_size, S->ct);
+    build_block_tree(S->ct, eta, S->bt);
+    build_task_graph(S->ct, S->bt, S->g, accumulators != 0, g_host_threads.load(), true);
+    if (!compute_levels(S->g)) return fail(HM_EINTERNAL, "hm_structure_build_sparsified: task graph has a cycle");
+  } catch (const std::exception& ex) {
+    return fail(HM_EINTERNAL, std::string("hm_structure_build_sparsified: ") + ex.what());
+  }
+  *out = S.release();
+  return HM_OK;
+}
+
 int hm_set_host_threads(int threads) {
   if (threads < 0) return fail(HM_EINVAL, "hm_set_host_threads: threads must be >= 0");
   g_host_threads.store(threads);

@@ -361,6 +361,49 @@ struct DagBuilder {
     }
     return 2;
   }
+
+  // §4.1, Alg 12 for task t of the current work set: the neighbourhood N is t's sub-tasks (or t)
+  // and, for every successor, its sub-tasks (or the successor); every edge (t', s) of t's
+  // sub-tasks (or of t) whose target is also reached by a path of length >= 2 inside N goes.
+  std::vector<int> in_n, seen, stack_;
+  int stamp_n = 0, stamp_s = 0;
+  void sparsify(int t) {
+    if (in_n.size() < tasks.size()) {
+      in_n.resize(tasks.size(), 0);
+      seen.resize(tasks.size(), 0);
+    }
+    ++stamp_n;
+    auto add_n = [&](int x) {
+      if (sub_count[x] > 0)
+        for (int q = sub_first[x]; q < sub_first[x] + sub_count[x]; ++q) in_n[q] = stamp_n;
+      else
+        in_n[x] = stamp_n;
+    };
+    add_n(t);
+    for (int s : succ[t]) add_n(s);
+    const int f = sub_count[t] > 0 ? sub_first[t] : t, cnt = sub_count[t] > 0 ? sub_count[t] : 1;
+    for (int tp = f; tp < f + cnt; ++tp) {
+      ++stamp_s;
+      stack_.clear();
+      auto visit_from = [&](int v) {
+        for (int u : succ[v])
+          if (in_n[u] == stamp_n && seen[u] != stamp_s) {
+            seen[u] = stamp_s;
+            stack_.push_back(u);
+          }
+      };
+      for (int s : succ[tp])
+        if (in_n[s] == stamp_n) visit_from(s);
+      if (stack_.empty()) continue;
+      while (!stack_.empty()) {
+        const int v = stack_.back();
+        stack_.pop_back();
+        visit_from(v);
+      }
+      auto& S = succ[tp];
+      S.erase(std::remove_if(S.begin(), S.end(), [&](int x) { return seen[x] == stamp_s; }), S.end());
+    }
+  }
 };
 
 // fn(i) for i in [0, n) on `threads` threads (chunks handed out in order; serial when small);
@@ -404,7 +447,8 @@ void parallel_for(size_t n, int threads, F fn) {
 // are generated (sizes first, then places by a prefix sum, so that task indices do not depend on
 // the thread count), then the dependencies of every work task are refined; each step writes only
 // data of its own task and its sub-tasks. The result equals the serial construction.
-void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators, int threads) {
+void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators, int threads,
+                      bool sparsify) {
   auto t0 = std::chrono::steady_clock::now();
   g = TaskGraph();
   if (ct.cl.empty()) return;
@@ -436,6 +480,9 @@ void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, 
       thread_local std::vector<int> scratch;
       flag[i] = b.refine(work[i], scratch);
     });
+    // Alg 12 in work order (each step sees the removals of the previous ones)
+    if (sparsify)
+      for (size_t i = 0; i < nw; ++i) b.sparsify(work[i]);
     next.clear();
     for (size_t i = 0; i < nw; ++i) {
       const int w = work[i];

@@ -82,9 +82,10 @@ void collect_leaves(const BlockTree& bt, int node, std::vector<int>& out);
 // shift_upd of its block, apply_upd of a leaf precedes the task that factorises or solves with
 // it, add_upd is refined like hmul and writes the block and its accumulator.
 // threads: host threads of the parallel loops of Alg 13 (0: all hardware threads); the graph
-// does not depend on it.
+// does not depend on it. sparsify: every iteration ends with the removal of redundant edges of
+// Alg 12 (§4.1) for each task of the work set, in order.
 void build_task_graph(const ClusterTree& ct, const BlockTree& bt, TaskGraph& g, bool accumulators = false,
-                      int threads = 0);
+                      int threads = 0, bool sparsify = false);
 // The accumulator task graph built in two parts (§4.3): the standard graph (hmul tasks stand for
 // add_upd) plus one shift_upd / apply_upd task per block-tree node, linked by edges parent ->
 // son, add_upd -> accumulator task of its destination, apply_upd of a leaf -> its leaf task.

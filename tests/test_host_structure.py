@@ -178,3 +178,20 @@ def test_lu_batch_rejects_bad_arguments_without_a_device(lib):
     outs = (ctypes.c_void_p * 1)()
     assert lib.hm_lu_batch(None, None, 1, None, outs) == -1
     assert lib.hm_lu_batch(None, (ctypes.c_void_p * 1)(), 0, None, outs) == -1
+
+
+@pytest.mark.parametrize("accumulators", [False, True])
+@pytest.mark.parametrize("geom,n,eta", [("sphere", 2048, 2.0), ("cube", 3000, 2.0), ("line", 512, 0.0)])
+def test_sparsified_graph_bit_exact_with_oracle(lib, geom, n, eta, accumulators):
+    """Alg 12 (§4.1) during construction: the library's graph equals the oracle's, edge for edge."""
+    points = W.points_for(geom, n, 21)
+    S = hm.hm_structure_build_sparsified(points, 64, eta, accumulators).export()
+    ct = ClusterTree(points, 64)
+    bt = BlockTree(ct, eta)
+    builder = D.AccuTaskGraphBuilder(ct, bt) if accumulators else D.TaskGraphBuilder(ct, bt)
+    nodes, edges = builder.compute_dag(sparsify=True)
+    names = ACC_TYPES if accumulators else TYPES
+    tasks = [(names[t[0]], t[1], t[2], t[3]) for t in S["tasks"].tolist()]
+    assert sorted(tasks) == sorted(nodes)
+    assert {(tasks[s], tasks[d]) for s, d in S["edges"].tolist()} == set(edges)
+    assert len(S["edges"]) == len(edges)

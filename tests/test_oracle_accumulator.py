@@ -358,3 +358,20 @@ def test_accumulator_edges_of_the_paper_figure():
     assert sub[0] == sh(r, r)
     assert b.precedes(sub[0], (D.LU, t0.id, t0.id, -1))
     assert b.precedes(sub[0], (D.TRSU, t0.id, t1.id, -1))
+
+
+def test_sparsification_drops_accumulator_hierarchy():
+    """§4.1 warns that removing redundant edges during construction can remove edges the
+    accumulator handling needs: with Alg 12 the accumulator graph loses orderings of a parent's
+    accumulator task before its sons' (none are lost without it)."""
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-6, 64)
+
+    def misses(sparsify):
+        b = D.AccuTaskGraphBuilder(hm.ct, hm.bt)
+        nodes, edges = b.compute_dag(sparsify=sparsify)
+        idx, anc = _ancestors(nodes, edges)
+        acc_task = {(t[1], t[2]): t for t in nodes if t[0] in (D.SHIFT, D.APPLY)}
+        return sum(1 for child, par in b.parent.items() if not anc[acc_task[child]] >> idx[acc_task[par]] & 1)
+
+    assert misses(False) == 0
+    assert misses(True) > 0

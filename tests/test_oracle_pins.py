@@ -349,3 +349,29 @@ def test_planted_transposed_low_rank_solve_is_caught(monkeypatch):
     A = hm.exact_dense()
     X = np.random.default_rng(3).standard_normal((hm.n, 3))
     assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) > 1e-3
+
+
+def test_sparsification_keeps_reachability_and_levels():
+    """Alg 12 removes only edges whose target is reached by another path: the standard graph keeps
+    its transitive closure and every longest-path level, with fewer edges (§4.1)."""
+    hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, 1e-6, 64)
+    n1, e1 = D.TaskGraphBuilder(hm.ct, hm.bt).compute_dag()
+    n2, e2 = D.TaskGraphBuilder(hm.ct, hm.bt).compute_dag(sparsify=True)
+    assert sorted(n1) == sorted(n2) and set(e2) < set(e1)
+    l1, l2 = D.levels(n1, e1), D.levels(n2, e2)
+    assert all(l1[t] == l2[t] for t in n1)
+
+    def closure(nodes, edges):
+        idx = {t: i for i, t in enumerate(sorted(nodes))}
+        out = {t: [] for t in nodes}
+        for a, b in edges:
+            out[a].append(b)
+        reach = {}
+        for t in sorted(nodes, key=lambda t: -l1[t]):   # sinks first
+            m = 0
+            for b in out[t]:
+                m |= reach[b] | (1 << idx[b])
+            reach[t] = m
+        return reach
+
+    assert closure(n1, e1) == closure(n2, e2)
