@@ -172,6 +172,8 @@ struct DagBuilder {
   std::vector<int> parent_node;         // block-tree parent of each node, -1 at the root
 
   DagBuilder(const ClusterTree& c, const BlockTree& b, bool accumulators) : ct(c), bt(b), accu(accumulators) {
+    range.reserve(ct.cl.size());
+    for (const Cluster& x : ct.cl) range.emplace_back(x.lo, x.hi);
     if (accu) {
       parent_node.assign(bt.nodes.size(), -1);
       for (size_t i = 0; i < bt.nodes.size(); ++i)
@@ -213,11 +215,8 @@ struct DagBuilder {
       default: d[0] = {ID_A, t.a, t.b}; return 1;   // apply_upd
     }
   }
-  bool overlap(int x, int y) const {
-    const Cluster& cx = ct.cl[x];
-    const Cluster& cy = ct.cl[y];
-    return cx.lo < cy.hi && cy.lo < cx.hi;
-  }
+  std::vector<std::pair<int, int>> range;   // [lo, hi) of every cluster, compact for the overlap tests
+  bool overlap(int x, int y) const { return range[x].first < range[y].second && range[y].first < range[x].second; }
   // Def 3.2
   bool precedes(int i, int j) const {
     if (i == j) return false;
