@@ -277,3 +277,28 @@ def test_build_then_lu_plans_on_the_host(lib):
     f = _factor(hmat, fac, Q["leaves"])
     X = np.random.default_rng(3).standard_normal((hmat.n, 3))
     assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) <= 10 * eps
+
+
+@pytest.mark.parametrize("n", [2, 50, 64, 65])
+def test_degenerate_sizes_on_the_host(lib, n):
+    """One leaf (n <= 64: one LU micro-op, one-leaf solves) and the first split (n = 65): the H-LU
+    and solve plans reproduce A and solve with it to rounding."""
+    pts = W.fibonacci_sphere(n, 3)
+    hmat = HMatrix(pts, 64, 2.0, 1e-6, 64)
+    S = hm.hm_structure_build(pts, 64, 2.0)
+    P = S.plan(0, 1e-6, 64)
+    sim = PlanSim(P["sizes"])
+    _load(sim, P["leaves"], hmat.store)
+    sim.run(P)
+    f = _factor(hmat, sim, P["leaves"])
+    A = hmat.exact_dense()
+    X = np.random.default_rng(1).standard_normal((n, 2))
+    assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) < 1e-14
+    Q = S.plan(1, 0.0, 64, 2)
+    sol = PlanSim(Q["sizes"], nrhs_space=2 * n)
+    sol.d[SP_F], sol.i[IS_RANK], sol.i[IS_PIV] = sim.d[SP_F], sim.i[IS_RANK], sim.i[IS_PIV]
+    sol.mat(ref(SP_X, 0), 1, n, n, 2)[:] = X
+    sol.i[IS_S][0] = 2
+    sol.run(Q)
+    xs = np.array(sol.mat(ref(SP_X, 0), 1, n, n, 2))
+    assert np.linalg.norm(A @ xs - X) / np.linalg.norm(X) < 1e-13
