@@ -195,3 +195,16 @@ def test_sparsified_graph_bit_exact_with_oracle(lib, geom, n, eta, accumulators)
     assert sorted(tasks) == sorted(nodes)
     assert {(tasks[s], tasks[d]) for s, d in S["edges"].tolist()} == set(edges)
     assert len(S["edges"]) == len(edges)
+
+
+def test_batching_workload_recipe():
+    inst = W.ellipsoid_instances(64)
+    ns = np.array([n for n, _ in inst])
+    assert len(inst) == 64 and ns.min() >= 4096 and ns.max() <= 65536
+    assert 0.3 < np.mean(np.log(ns) < np.log(4096 * 4)) < 0.7      # log-uniform: half below the log-midpoint
+    for n, p in inst[:4]:
+        assert p.shape == (n, 3) and np.isfinite(p).all()
+        r = np.sqrt(((p / np.abs(p).max(axis=0)) ** 2).sum(axis=1))
+        assert r.min() > 0.3
+    again = W.ellipsoid_instances(64)
+    assert all(np.array_equal(a[1], b[1]) for a, b in zip(inst[:3], again[:3]))
