@@ -1,6 +1,7 @@
-// Cluster tree, block tree and the semi-automatic H-LU task graph (host side).
+// Cluster tree, block tree and the semi-automatic H-LU task graphs (host side).
 // Paper: Def 2.1 (cluster tree), Def 2.2 (block tree), §5.1 (standard admissibility),
-// Table 1 (task data dependencies), Def 3.2 (task relation), Alg 9-11 (refinement).
+// Table 1 (task data dependencies), Def 3.2 (task relation), Alg 9-11 (refinement), Alg 13
+// (its parallel loops), Alg 12 (edge sparsification), Table 2 and §4.3 (accumulator graphs).
 #include "structure.h"
 
 #include <algorithm>
