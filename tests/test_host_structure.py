@@ -208,3 +208,15 @@ def test_batching_workload_recipe():
         assert r.min() > 0.3
     again = W.ellipsoid_instances(64)
     assert all(np.array_equal(a[1], b[1]) for a, b in zip(inst[:3], again[:3]))
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    """Without a CUDA device the computing path refuses to start (HM_ECUDA): there is no CPU
+    fallback behind the boundary."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p()
+    assert lib.hm_ctx_create(0, None, hm.ALLOC_FN(), hm.FREE_FN(), None, ctypes.byref(h)) == -3
+    assert h.value is None
+    assert b"no CUDA device" in lib.hm_last_error()
