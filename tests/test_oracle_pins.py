@@ -375,3 +375,26 @@ def test_sparsification_keeps_reachability_and_levels():
         return reach
 
     assert closure(n1, e1) == closure(n2, e2)
+
+
+def test_fp32_products_accuracy_and_refinement():
+    """Products in FP32 (operands and accumulation), FP64 elsewhere: no visible loss at eps = 1e-4,
+    the FP32 floor (~1e-8 relative) showing at eps = 1e-8, and FP64 refinement with these
+    factors reaching a residual of 1e-10 in a few steps."""
+    from oracle.mixed import MixedHLUFactor, refine
+    X = np.random.default_rng(3).standard_normal((1024, 4))
+    errs = {}
+    for eps in (1e-4, 1e-8):
+        hm = HMatrix(W.fibonacci_sphere(1024, 11), 64, 2.0, eps, 64)
+        A = hm.exact_dense()
+        rel = lambda f: np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X)
+        f64, f32 = HLUFactor(hm).factor(), MixedHLUFactor(hm).factor()
+        errs[eps] = (rel(f64), rel(f32))
+        if eps == 1e-4:
+            b = np.random.default_rng(4).standard_normal((1024, 1))
+            _, steps, res = refine(A, f32, b, tol=1e-10)
+            assert res <= 1e-10 and steps <= 3
+    e64, e32 = errs[1e-4]
+    assert e32 <= 10 * 1e-4 and abs(e32 - e64) <= 0.05 * e64
+    e64, e32 = errs[1e-8]
+    assert e32 > 3 * e64 and e32 < 1e-6
