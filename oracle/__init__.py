@@ -9,13 +9,18 @@ Graph Construction for H-Matrix Arithmetic", arXiv 1911.07531):
 * ``trees``     — cluster tree (Def 2.1), standard admissibility (§5.1) and block tree
                   (Def 2.2);
 * ``dag``       — the semi-automatic task graph: task data dependencies (Table 1),
-                  task relation (Def 3.2), refinement (Alg 9, Alg 10, Alg 11);
+                  task relation (Def 3.2), refinement (Alg 9, Alg 10, Alg 11), removal of
+                  redundant edges (Alg 12), the accumulator graphs (Table 2, §4.3);
 * ``hmatrix``   — H-matrix storage (Def 2.3), assembly and compression, rounded
                   (truncated) addition, H-matrix times thin dense matrix, and the
                   fixed flop model used for GFLOP/s;
 * ``hlu``       — recursive H-LU (Alg 2), lower / upper H-solves (Alg 3 and its upper
                   mirror), H-multiplication (Alg 1) with each leaf update applied at once,
                   block forward/backward substitution;
+* ``accu``      — accumulator-based H-LU (Alg 4-8) in three accumulator formats, and a
+                  task-by-task runner of the accumulator task graph;
+* ``mixed``     — H-LU with FP32 factor products and FP64 elsewhere, and iterative
+                  refinement with FP64 residuals;
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import it. It shares no code with the CUDA library and never imports it.
