@@ -1,4 +1,4 @@
-"""Benchmark: H-LU factorization throughput (model GFLOP/s) on one GB300, plus solve latency.
+"""Benchmark: H-LU factorization seconds on one GB300 (and model GFLOP/s), plus solve latency.
 
 A step is one hm_lu of the resident H-matrix: the task graph of the paper's semi-automatic
 construction executed wave by wave in batched FP64 kernels (dense leaf LU / solves / GEMMs
@@ -9,9 +9,10 @@ larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
-Prints one JSON line.  N > 1 (torchrun) runs one independent replica per GPU (the H-LU of
-one matrix does not shard); value = all replicas' flops / max wall time.  --impl reference
-times the FP64 CPU oracle on a bounded sample of the same workload.
+Prints one JSON line; `value` is seconds per factorization (lower is better).  N > 1 (torchrun)
+runs one independent replica per GPU (the H-LU of one matrix does not shard); value = the
+slowest replica's seconds per step / N (factorizations of the whole job per second, inverted).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -39,6 +40,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop 
 PROFILED_BYTES_PER_FLOP = {"gemm": (405.352192e6 + 20.44544e6) / 2231684434.0,
                            "core": 285696.0 / 9037896.0}
 KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
+METRIC = "H-LU factorization seconds at {w}"
 WORKLOAD_TEXT = {
     "cube131072": "n=131072 uniform on the unit-cube surface, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
     "sphere32768": "n=32768 jittered Fibonacci sphere, 1/(4pi(r+h)), leaf 64, eta 2, eps 1e-6, rank cap 64, FP64",
@@ -107,48 +109,62 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(workload, steps=1):
-    """Model GFLOP/s of the FP64 oracle's recursive H-LU on a bounded sample of the workload."""
-    from oracle.hlu import HLUFactor
-    from oracle.hmatrix import HMatrix
+def cpu_oracle_sample(workload, repeat=3, parallel=True):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload (same geometry,
+    seed and eps, n = 2048): the recursive H-LU on one core and the task-graph (Alg 11) waves on
+    all cores, each the median of `repeat` runs, in a child process with one BLAS thread."""
     geom, n, eps = ORACLE_SAMPLE[workload]
     cfg = W.WORKLOADS[workload]
-    p = W.points_for(geom, n, cfg["seed"])
-    hmo = HMatrix(p, cfg["leaf"], cfg["eta"], eps, cfg["rank_cap"])
-    rates, secs = [], []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        f = HLUFactor(hmo).factor()
-        dt = time.perf_counter() - t0
-        secs.append(dt)
-        rates.append(f.stats.flops / dt * 1e-9)
-    cores = 1
-    try:
-        import threadpoolctl
-        cores = max([1] + [i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()])
-    except Exception:
-        cores = os.cpu_count() or 1
-    return {"value": statistics.median(rates), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"recursive FP64 H-LU of n={n} {geom} points (eps {eps}, leaf 64, eta 2, cap 64), "
-                      f"median of {steps} run(s), {statistics.median(secs):.1f} s each",
-            "seconds": statistics.median(secs)}
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "oracle.cpu_baseline", "--geometry", geom, "--n", str(n), "--seed",
+           str(cfg["seed"]), "--eps", str(eps), "--leaf", str(cfg["leaf"]), "--eta", str(cfg["eta"]),
+           "--rank-cap", str(cfg["rank_cap"]), "--repeat", str(repeat), "--threads", str(cores)]
+    if not parallel:
+        cmd.append("--no-parallel")
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(o, full_model_gflop):
+    """cpu_baseline of the bench line: the serial oracle's model GFLOP/s on the sample, applied
+    to the model flops of one full-size factorization (seconds, the metric's unit)."""
+    ser = o["serial"]
+    rec = {"value": full_model_gflop / ser["gflops"] if full_model_gflop else ser["seconds"], "unit": "s",
+           "cores": 1, "kind": "oracle",
+           "sample": f"recursive FP64 oracle H-LU of the n={o['n']} {o['geometry']} sample (eps {o['eps']}, "
+                     f"leaf 64, eta 2, cap 64), median of {len(ser['all_seconds'])}: {ser['seconds']:.2f} s "
+                     f"= {ser['gflops']:.2f} model GFLOP/s on 1 core; value = the full workload's "
+                     f"{full_model_gflop:.0f} model GFLOP at that rate" if full_model_gflop else
+                     f"recursive FP64 oracle H-LU of the n={o['n']} {o['geometry']} sample, {ser['seconds']:.2f} s",
+           "serial": {k: ser[k] for k in ("seconds", "model_gflop", "gflops", "cores", "rel_error")}}
+    if "parallel" in o:
+        par = o["parallel"]
+        rec["parallel"] = {k: par[k] for k in ("seconds", "model_gflop", "gflops", "cores", "rel_error", "waves",
+                                               "tasks")}
+        rec["parallel"]["note"] = ("task-graph levels on a thread pool; the oracle's per-task work is "
+                                   "Python-bound (GIL), so more threads do not speed it up")
+    return rec
 
 
 def run_reference(args, rank):
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        cpu_oracle_sample(args.workload, 1)
+    cfg = W.WORKLOADS[args.workload]
+    full = cfg.get("model_gflop")
     t0 = time.perf_counter()
-    cb = cpu_oracle_sample(args.workload, args.steps)
+    o = cpu_oracle_sample(args.workload, repeat=max(args.steps, 1), parallel=False)
     wall = time.perf_counter() - t0
-    line = {"metric": f"H-LU factorization GFLOP/s (model flops) at {args.workload}", "value": cb["value"],
-            "unit": "GFLOP/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+    cb = cpu_baseline_record(o, full)
+    line = {"metric": METRIC.format(w=args.workload), "value": cb["value"],
+            "unit": "s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": cb["sample"]},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": cb["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -247,7 +263,9 @@ def main():
         wall = time.perf_counter() - t_wall0
     total_ms = e0.elapsed_time(e1)
     total_ms_max, all_flops = aggregate_ranks(total_ms, sum(flops), dist, "cuda")
-    value = all_flops / (total_ms_max * 1e-3) * 1e-9
+    # whole job: `world` factorizations per step in the slowest replica's step time
+    value = total_ms_max * 1e-3 / max(args.steps, 1) / world
+    model_gflops = all_flops / (total_ms_max * 1e-3) * 1e-9
     fstats = last.stats()
 
     # one profiled step: per-kernel-kind device time for the roofline of the dominant kernel
@@ -308,52 +326,83 @@ def main():
     del xh
 
     # coarse factorization + refinement (the eps = 1e-4 + FP64 refinement mode of the workload):
-    # hm_lu at eps = 1e-4, then hm_solve refines against the exact kernel (n^2 kernel
-    # evaluations per residual) to a relative residual of 1e-10, for a manufactured solution
-    # b = A_exact x*; reported with its forward error
+    # hm_lu at eps = 1e-4, then hm_solve refines to a relative residual of 1e-10 for a
+    # manufactured solution b = A_exact x*, with the residual from (a) the exact kernel (n^2
+    # kernel evaluations per step) or (b) the H-matrix A_H (eps 1e-6; converges to A_H's
+    # solution); each reported with its exact residual and forward error
     refined = None
     if not args.no_refined:
         xs = torch.from_numpy(W.gaussian_rhs(n, 1, cfg["rhs_seed"] + 5)[:, 0]).to(f"cuda:{local}")
         bx = hm.hm_matvec(ctx, A, hm.HM_OP_EXACT, xs)
-        r0 = torch.cuda.Event(enable_timing=True)
-        r1 = torch.cuda.Event(enable_timing=True)
-        r2 = torch.cuda.Event(enable_timing=True)
-        hm.hm_lu(ctx, A, eps=1e-4).free()      # first use builds the eps = 1e-4 plan (untimed)
-        r0.record(stream)
-        F4 = hm.hm_lu(ctx, A, eps=1e-4)
-        r1.record(stream)
-        xr, info = hm.hm_solve(ctx, F4, bx, A=A, refine_tol=1e-10, max_iter=30, residual_op=hm.HM_OP_EXACT)
-        r2.record(stream)
-        r2.synchronize()
-        fe = float(torch.linalg.vector_norm(xr - xs) / torch.linalg.vector_norm(xs))
-        refined = {"factor_eps": 1e-4, "factor_s": r0.elapsed_time(r1) * 1e-3,
-                   "factor_model_gflop": sum(F4.stats()["flops"][:4]) * 1e-9,
-                   "refine_tol": 1e-10, "iterations": info["iterations"], "rel_residual": info["rel_residual"],
-                   "solve_s": r1.elapsed_time(r2) * 1e-3, "forward_error": fe,
-                   "residual": "exact kernel matvec on the device (n^2 evaluations per step)"}
+        bnorm = float(torch.linalg.vector_norm(bx))
+
+        def timed(fn):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            out = fn()
+            a1.record(stream)
+            a1.synchronize()
+            return out, a0.elapsed_time(a1) * 1e-3
+
+        hm.hm_lu(ctx, A, eps=1e-4).free()      # first use builds the eps = 1e-4 plans (untimed)
+        F64_4, f64_s = timed(lambda: hm.hm_lu(ctx, A, eps=1e-4))
+        F64_4.free()
+        hm.hm_lu(ctx, A, eps=1e-4, precision=hm.HM_PREC_MIXED).free()
+        F4, f_s = timed(lambda: hm.hm_lu(ctx, A, eps=1e-4, precision=hm.HM_PREC_MIXED))
+        refined = {"factor_eps": 1e-4, "factor_precision": "mixed (tensor-core split-TF32 products)",
+                   "factor_s": f_s, "fp64_factor_s": f64_s,
+                   "factor_model_gflop": sum(F4.stats()["flops"][:4]) * 1e-9, "refine_tol": 1e-10}
+        for name, op in (("exact_residual", hm.HM_OP_EXACT), ("hmatrix_residual", hm.HM_OP_A)):
+            try:
+                (xr, info), s_s = timed(lambda: hm.hm_solve(ctx, F4, bx, A=A, refine_tol=1e-10, max_iter=30,
+                                                            residual_op=op))
+                conv = True
+            except hm.HMError:
+                conv = False
+                xr, info, s_s = None, {"iterations": 30, "rel_residual": None}, None
+            rec = {"converged": conv, "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+                   "solve_s": s_s, "total_s": (f_s + s_s) if s_s is not None else None}
+            if xr is not None:
+                r = hm.hm_matvec(ctx, A, hm.HM_OP_EXACT, xr)
+                rec["exact_rel_residual"] = float(torch.linalg.vector_norm(r - bx)) / bnorm
+                rec["forward_error"] = float(torch.linalg.vector_norm(xr - xs) / torch.linalg.vector_norm(xs))
+            refined[name] = rec
         F4.free()
+        # the plain eps = 1e-6 factor's own solve, for the accuracy comparison
+        x6, _ = hm.hm_solve(ctx, last, bx)
+        refined["plain_eps_1e-6"] = {
+            "exact_rel_residual": float(torch.linalg.vector_norm(hm.hm_matvec(ctx, A, hm.HM_OP_EXACT, x6) - bx))
+            / bnorm, "forward_error": float(torch.linalg.vector_norm(x6 - xs) / torch.linalg.vector_norm(xs))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(args.workload, 1)
-        cpu.pop("seconds", None)
+        cpu = cpu_baseline_record(cpu_oracle_sample(args.workload, repeat=3), statistics.median(flops) * 1e-9)
 
     if rank == 0:
         line = {
-            "metric": f"H-LU factorization GFLOP/s (model flops) at {args.workload}",
-            "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms_max / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC.format(w=args.workload),
+            "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms_max / max(args.steps, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "precision": "FP64 storage and arithmetic; the truncation core's Jacobi sweeps run in FP32 on a "
+                         "Cholesky factor of the FP64 Gram-based core (eigenvalues to ~1e-6 relative), with "
+                         "FP64 factorisations, products and orthogonalisation before and after",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload],
                        "l2": "no flush: every step reads and writes 13+ GB of block values (L2 is 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "seconds_per_factorization": statistics.median(step_ms) * 1e-3,
+            "model_gflops": model_gflops,
             "model_gflop_per_factorization": statistics.median(flops) * 1e-9,
+            "model": "getrf 2b^3/3, trsm m b^2, gemm 2mnk, and per low-rank update (added one at a time to "
+                     "the target's rank) QR(m,K)+QR(n,K)+2K^3+21K^3+2(m+n)Kk: independent of how the plan "
+                     "merges updates",
             "solves_per_s": 1e3 / statistics.mean(lat) if lat else None,
             "solve_latency_ms": {"p50": p50, "p99": p99, "nrhs": 1},
-            "e2e": {"value": e2e_flops / e2e_s * 1e-9, "unit": "GFLOP/s",
+            "e2e": {"value": e2e_s, "unit": "s",
                     "h2d_bytes_per_step": int(pts.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
-                    "seconds": e2e_s, "split": e2e_split,
+                    "model_gflops": e2e_flops / e2e_s * 1e-9, "split": e2e_split,
                     "includes": "hm_build (points H2D, trees, ACA) + hm_lu (task graph, "
                                 "plan, execution) + hm_solve with host RHS and result"},
             "gpu_launches": launches,

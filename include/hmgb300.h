@@ -28,8 +28,9 @@
  *     PyTorch caching allocator); with NULL callbacks cudaMalloc / cudaFree are used.
  *   - All work is enqueued on the context's stream. hm_build, hm_lu, hm_solve and
  *     hm_matvec synchronize that stream before returning (they report device status).
- *   - Arithmetic is FP64.  There is no CPU fallback: without a usable CUDA device every
- *     computing call fails with HM_ECUDA.
+ *   - Arithmetic is FP64 (hm_lu can run its products on the tensor cores: HM_PREC_MIXED).
+ *     There is no CPU fallback: without a usable CUDA device every computing call fails
+ *     with HM_ECUDA.
  */
 #ifndef HMGB300_H
 #define HMGB300_H
@@ -46,13 +47,22 @@ enum {
   HM_EINVAL = -1,     /* invalid argument (NULL handle, n < 1, ld < n, ...) */
   HM_ENOMEM = -2,     /* the allocator returned NULL; no state was changed */
   HM_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
-  HM_ESINGULAR = -4,  /* a zero pivot in a diagonal leaf LU (the factor is still returned) */
-  HM_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  HM_ESINGULAR = -4,  /* a numerically zero pivot in a diagonal leaf LU (see
+                         hm_stats.singular_pivots; the factor is still returned)        */
+  HM_ETIMEOUT = -5,   /* a bounded device wait gave up (tensor-core MMA completion) */
   HM_ENOTCONV = -6,   /* iterative refinement did not reach refine_tol */
   HM_EINTERNAL = -7   /* planner invariant violated */
 };
 
 enum { HM_OP_A = 0, HM_OP_L = 1, HM_OP_U = 2, HM_OP_LU = 3, HM_OP_EXACT = 4 };
+
+/* Smallest truncation accuracy eps accepted by hm_build, hm_lu, hm_lu_batch, hm_truncate and
+ * hm_truncate_noalloc (HM_EINVAL below it). The rounded truncation (§2.3 asks for a fixed rank
+ * or a relative accuracy and leaves the method open) is computed here from the Gram
+ * matrices of the stacked factors, whose rounding errors are of size u |W|^2: singular values
+ * below about sqrt(K u) |W| |Z| ~ 1e-8 of the largest are not resolved, so eps below this floor
+ * would return factors that silently miss 10 eps. */
+#define HM_EPS_MIN 1e-8
 
 typedef struct hm_ctx hm_ctx;
 typedef struct hm_matrix hm_matrix;
@@ -66,15 +76,28 @@ typedef void (*hm_free_fn)(void* ptr, size_t bytes, void* user);
 typedef struct {
   int leaf_size;     /* clusters with at most leaf_size points are leaves (default 64)   */
   double eta;        /* admissibility parameter (default 2.0)                           */
-  double eps;        /* relative truncation accuracy of admissible blocks (default 1e-6)*/
+  double eps;        /* relative truncation accuracy of admissible blocks, in
+                        [HM_EPS_MIN, 1) (default 1e-6)                                  */
   int rank_cap;      /* maximal rank of a low-rank block, 1..64 (default 64)            */
   double kernel_h;   /* regularisation h of 1/(4 pi (r + h)); <= 0: mean NN spacing     */
 } hm_build_opts;
 
+/* Arithmetic of hm_lu (hm_lu_opts.precision).
+ *   HM_PREC_FP64   every product in FP64 (the truncation core's Jacobi sweeps in FP32).
+ *   HM_PREC_MIXED  the products of Alg 1 (low-rank and dense leaf products and their application
+ *                  to dense leaves) and the rebuild products of every rounded addition run on the
+ *                  tensor cores: FP64 operands split into two TF32 parts, three MMAs (hi hi,
+ *                  hi lo, lo hi), FP32 accumulation (~1e-6 relative to |A| |B|). The Gram
+ *                  matrices, the truncation core, the leaf LU with its pivots and the triangular
+ *                  solves stay FP64. Meant for a coarse factorization (eps ~1e-4) that hm_solve's
+ *                  FP64 iterative refinement turns into an accurate solve. */
+enum { HM_PREC_FP64 = 0, HM_PREC_MIXED = 1 };
+
 typedef struct {
   double eps;        /* relative accuracy of every rounded addition during H-LU (<=0: the
-                        matrix's eps); the rank cap is the matrix's                        */
-  int precision;     /* 0 = FP64 (only mode)                                              */
+                        matrix's eps; else in [HM_EPS_MIN, 1)); the rank cap is the
+                        matrix's                                                          */
+  int precision;     /* HM_PREC_FP64 or HM_PREC_MIXED                                     */
 } hm_lu_opts;
 
 typedef struct {
@@ -107,12 +130,18 @@ typedef struct {
   double flops[5];              /* model flops of the last hm_lu: getrf, trsm, gemm,
                                    rounded truncation (QR + core + SVD + rebuild), other */
   int64_t rank_cap_hits;        /* rounded additions that hit the rank cap               */
-  int64_t singular_pivots;      /* zero pivots met in diagonal leaves                    */
+  int64_t singular_pivots;      /* numerically zero pivots met in diagonal leaves: |p| <=
+                                   b u max|a| over the b x b leaf being factored (u = 2^-53) */
   int64_t aca_unconverged;      /* ACA runs that hit their rank limit during hm_build    */
   double kind_ms[8];            /* with profiling on: device ms per kernel kind          */
   int64_t kind_launches[8];     /*   getrf trsm gemm copy stack core eval aca            */
   double kind_flops[8];         /* algorithmic flops executed per kernel kind (last hm_lu) */
   int64_t launches;             /* kernel launches of the last hm_lu                     */
+  int64_t row_interchanges;     /* row interchanges of partial pivoting in the leaf LUs  */
+  int64_t precision;            /* HM_PREC_* of the last hm_lu                           */
+  double tc_ms;                 /* the tensor-core GEMM kind (mixed precision): device ms  */
+  int64_t tc_launches;          /*   with profiling on, launches,                          */
+  double tc_flops;              /*   and flops executed (2mnk per micro-op)                */
 } hm_stats;
 
 /* Last error message of the calling thread ("" if none). */
@@ -169,6 +198,24 @@ int hm_matvec(hm_ctx* ctx, hm_matrix* A, hm_factor* F, int op, double alpha, con
               double* y, int64_t nrhs, int64_t ld);
 
 int hm_matrix_stats(const hm_matrix* A, hm_stats* out);
+
+/* Storage layout of A's block values (Def 2.3: dense leaves and low-rank leaves U V^T), for
+ * inspection, and for callers that edit the values (hm_matrix_copy_values). Host outputs, each
+ * may be NULL:
+ *   leaves[nleaves*10]   per block-tree leaf (pre-order): row cluster, column cluster, m, n,
+ *                        low-rank (0/1), rank capacity, value offset (dense D or U, column-
+ *                        major, ld m), V offset (ld n), rank index, pivot offset (-1: none)
+ *   perm[n]              original point index of each position of the cluster order
+ *   cluster_lo[nclusters] first position of each cluster (depth-first pre-order ids)
+ *   *nleaves, *nvalues, *nclusters   the counts. */
+int hm_matrix_layout(const hm_matrix* A, int64_t* leaves, int64_t* perm, int64_t* cluster_lo, int64_t* nleaves,
+                     int64_t* nvalues, int64_t* nclusters);
+/* Copies A's nvalues block values to (to_matrix == 0) or from (to_matrix != 0) the caller's
+ * device buffer buf, on the context stream (synchronized). Writing replaces the matrix that
+ * later hm_lu / hm_matvec(HM_OP_A) calls see (the ranks of the low-rank leaves stay); the
+ * structure, the task graph and the plans depend only on the trees, so they remain valid.
+ * HM_OP_EXACT keeps evaluating the kernel of the points. */
+int hm_matrix_copy_values(hm_ctx* ctx, hm_matrix* A, double* buf, int to_matrix);
 int hm_factor_stats(const hm_factor* F, hm_stats* out);
 
 /* Rounded truncation of W Z^T (W: m x K, Z: n x K, device, column-major, ld >= m / n) to
@@ -201,6 +248,16 @@ int hm_truncate(hm_ctx* ctx, int64_t m, int64_t n, int K, const double* W, int64
 int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int K, const double* W, int64_t ldw,
                         const double* Z, int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V,
                         int64_t ldv, int* k_out);
+
+/* Diagnostic: y[i] = f(x[i]) for the FP64 reciprocal helpers that the serial sections of the
+ * leaf LU and of the truncation core use instead of IEEE division and square root (no passage
+ * of the paper: a property of this implementation). which: 0 Newton-Raphson 1/x from a
+ * rescaled FP32 seed (any finite nonzero x), 1 Newton-Raphson 1/sqrt(x) (x > 0), 2 the
+ * three-operation series 1/x (x in [1e-30, 1e30]), 3 the leaf LU's pivot reciprocal (2 inside
+ * [1e-30, 1e30] in magnitude, else 0). x, y: device arrays of n doubles (may alias); runs on
+ * the given stream (NULL = legacy default stream) of the current device and synchronizes it.
+ * HM_EINVAL for a bad `which` or n < 0, HM_ECUDA on a launch failure. */
+int hm_selftest_reciprocals(void* cuda_stream, int which, const double* x, double* y, int64_t n);
 
 /* ---- host-only structure (no GPU needed): cluster tree, block tree, task graph -------- */
 typedef struct {

@@ -2,8 +2,8 @@
 
 Readings (the paper leaves these open):
 
-* Truncation / rounded addition (the "truncation operation to reduce the rank ... to the
-  predefined rank k or precision eps", §2.3): for W Z^T, QR-factor both factors
+* Truncation / rounded addition (§2.3 reduces the rank of a sum to a given rank or relative
+  accuracy and leaves the method open): for W Z^T, QR-factor both factors
   (Householder, via LAPACK), take the SVD of the small core R_W R_Z^T, keep the
   singular values sigma_i > eps * sigma_1, at most ``rank_cap`` of them (rank 0 if
   sigma_1 = 0).  The result is U = Q_W X_k Sigma_k, V = Q_Z Y_k (V orthonormal).

@@ -24,13 +24,15 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_lu_batch", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
+    "hm_selftest_reciprocals",
     "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_build_sparsified",
     "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
-    "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT",
+    "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT", "HM_PREC_FP64", "HM_PREC_MIXED",
 ]
 
 HM_OP_A, HM_OP_L, HM_OP_U, HM_OP_LU, HM_OP_EXACT = 0, 1, 2, 3, 4
+HM_PREC_FP64, HM_PREC_MIXED = 0, 1
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hmgb300.h")
 ERRORS = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ECUDA", -4: "HM_ESINGULAR",
           -5: "HM_ETIMEOUT", -6: "HM_ENOTCONV", -7: "HM_EINTERNAL"}
@@ -73,7 +75,9 @@ class Stats(ctypes.Structure):
                 ("flops", ctypes.c_double * 5), ("rank_cap_hits", ctypes.c_int64),
                 ("singular_pivots", ctypes.c_int64), ("aca_unconverged", ctypes.c_int64),
                 ("kind_ms", ctypes.c_double * 8), ("kind_launches", ctypes.c_int64 * 8),
-                ("kind_flops", ctypes.c_double * 8), ("launches", ctypes.c_int64)]
+                ("kind_flops", ctypes.c_double * 8), ("launches", ctypes.c_int64),
+                ("row_interchanges", ctypes.c_int64), ("precision", ctypes.c_int64), ("tc_ms", ctypes.c_double),
+                ("tc_launches", ctypes.c_int64), ("tc_flops", ctypes.c_double)]
 
     def to_dict(self):
         d = {}
@@ -135,6 +139,9 @@ def load_library():
         "hm_factor_stats": ([P, ctypes.POINTER(Stats)], I),
         "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
+        "hm_selftest_reciprocals": ([P, I, P, P, I64], I),
+        "hm_matrix_layout": ([P, P, P, P, P, P, P], I),
+        "hm_matrix_copy_values": ([P, P, P, I], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_accumulator": ([P, I64, I, D, I, PP], I),
         "hm_structure_build_sparsified": ([P, I64, I, D, I, PP], I),
@@ -178,7 +185,10 @@ def _col_major(t, n, name):
 class HMContext:
     """hm_ctx with the PyTorch caching allocator and a torch stream."""
 
-    def __init__(self, device=0, stream=None, torch_allocator=True):
+    def __init__(self, device=0, stream=None, torch_allocator=True, admit=None):
+        """admit: optional callable(nbytes) -> bool consulted before every device allocation the
+        library asks for; False makes the allocator callback return NULL (for tests of the
+        HM_ENOMEM paths, or a caller-side memory budget)."""
         import torch
         L = load_library()
         self.device = int(device)
@@ -188,6 +198,8 @@ class HMContext:
             dev, st = self.device, self.stream
 
             def _alloc(nbytes, user):
+                if admit is not None and not admit(int(nbytes)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
                 except Exception:   # out of memory -> NULL -> HM_ENOMEM
@@ -244,6 +256,34 @@ class HMatrix:
             pass
 
 
+    def layout(self):
+        """Leaf table (nleaves x 10 int64, see hm_matrix_layout), cluster order perm and the
+        first position of every cluster."""
+        L = load_library()
+        nl, nv, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(L.hm_matrix_layout(self.handle, None, None, None, ctypes.byref(nl), ctypes.byref(nv),
+                                  ctypes.byref(nc)))
+        leaves = np.empty((nl.value, 10), dtype=np.int64)
+        perm = np.empty(self.n, dtype=np.int64)
+        lo = np.empty(nc.value, dtype=np.int64)
+        _check(L.hm_matrix_layout(self.handle, leaves.ctypes.data, perm.ctypes.data, lo.ctypes.data, None, None,
+                                  None))
+        return {"leaves": leaves, "perm": perm, "cluster_lo": lo, "nvalues": nv.value}
+
+    def get_values(self):
+        """The block values as a new float64 device tensor."""
+        t = self.ctx._torch.empty(self.layout()["nvalues"], dtype=self.ctx._torch.float64,
+                                  device=f"cuda:{self.ctx.device}")
+        _check(load_library().hm_matrix_copy_values(self.ctx.handle, self.handle, t.data_ptr(), 0))
+        return t
+
+    def set_values(self, t):
+        """Replace the block values by a float64 device tensor of the same length."""
+        if t.dtype != self.ctx._torch.float64 or not t.is_contiguous() or t.numel() != self.layout()["nvalues"]:
+            raise ValueError("values: contiguous float64 device tensor of nvalues entries")
+        _check(load_library().hm_matrix_copy_values(self.ctx.handle, self.handle, t.data_ptr(), 1))
+
+
 class HFactor:
     def __init__(self, ctx, handle, A):
         self.ctx, self.handle, self.A = ctx, handle, A
@@ -276,8 +316,9 @@ def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h
     return HMatrix(ctx, h, p.shape[0])
 
 
-def hm_lu(ctx, A, eps=0.0, allow_singular=False):
-    o = LuOpts(float(eps), 0)
+def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0):
+    """H-LU of A (precision: HM_PREC_FP64 or HM_PREC_MIXED)."""
+    o = LuOpts(float(eps), int(precision))
     h = ctypes.c_void_p()
     rc = load_library().hm_lu(ctx.handle, A.handle, ctypes.byref(o), ctypes.byref(h))
     F = HFactor(ctx, h, A) if h.value else None
@@ -288,12 +329,12 @@ def hm_lu(ctx, A, eps=0.0, allow_singular=False):
     return F
 
 
-def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False):
+def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False, precision=0):
     """H-LU of several independent matrices whose waves share kernel launches; one factor each."""
     n = len(matrices)
     hs = (ctypes.c_void_p * n)(*[A.handle for A in matrices])
     outs = (ctypes.c_void_p * n)()
-    o = LuOpts(float(eps), 0)
+    o = LuOpts(float(eps), int(precision))
     rc = load_library().hm_lu_batch(ctx.handle, hs, n, ctypes.byref(o), outs)
     Fs = [HFactor(ctx, ctypes.c_void_p(outs[i]), A) if outs[i] else None for i, A in enumerate(matrices)]
     if rc != 0 and not (rc == -4 and allow_singular and all(F is not None for F in Fs)):
@@ -374,6 +415,20 @@ def hm_truncate_noalloc(W, Z, eps, cap=64, stream=None):
                                                   Zf.data_ptr(), n, float(eps), int(cap), U.data_ptr(), m,
                                                   V.data_ptr(), n, ctypes.byref(k)))
     return U[:, :k.value], V[:, :k.value]
+
+
+def hm_selftest_reciprocals(x, which, stream=None):
+    """y = f(x) for one of the library's FP64 reciprocal helpers (which: 0 nr_rcp, 1 nr_rsqrt,
+    2 fast_rcp, 3 the leaf LU's pivot reciprocal); x a contiguous float64 CUDA tensor."""
+    import torch
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous float64 tensor")
+    y = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    with torch.cuda.device(x.device):
+        _check(load_library().hm_selftest_reciprocals(ctypes.c_void_p(st.cuda_stream), int(which), x.data_ptr(),
+                                                      y.data_ptr(), x.numel()))
+    return y
 
 
 def _dt(fields):

@@ -81,6 +81,7 @@ struct DevPlan {
   Buf entries;
   bool uploaded = false;
   double eps = -1.0;
+  int precision = -1;
   double plan_seconds = 0.0;
   // replay state of solve / matvec plans: persistent scratch and the captured CUDA graph
   Buf sd, si, cnt;
@@ -91,7 +92,8 @@ size_t op_size(int kind) {
   switch (kind) {
     case K_GETRF: return sizeof(GetrfOp);
     case K_TRSM: return sizeof(TrsmOp);
-    case K_GEMM: return sizeof(GemmOp);
+    case K_GEMM:
+    case K_GEMM_TC: return sizeof(GemmOp);
     case K_COPY: return sizeof(CopyOp);
     case K_STACK:
     case K_CORE: return sizeof(TruncOp);
@@ -109,25 +111,37 @@ int upload_vec(hm_ctx* c, Buf& b, const V& v) {
   return HM_OK;
 }
 
+void free_ops(hm_ctx* c, DevPlan& dp) {
+  for (int k = 0; k < NKIND; ++k) dfree(c, dp.ops[k]);
+  dfree(c, dp.entries);
+}
+
+// micro-op arrays to the device; on a failure nothing stays allocated (a later call retries)
 int upload(hm_ctx* c, DevPlan& dp) {
   if (dp.uploaded) return HM_OK;
-  int rc;
-  if ((rc = upload_vec(c, dp.ops[K_GETRF], dp.host.getrf))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_TRSM], dp.host.trsm))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_GEMM], dp.host.gemm))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_COPY], dp.host.copy))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_STACK], dp.host.trunc))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_EVAL], dp.host.eval))) return rc;
-  if ((rc = upload_vec(c, dp.ops[K_ACA], dp.host.aca))) return rc;
-  if ((rc = upload_vec(c, dp.entries, dp.host.entries))) return rc;
-  CU(cudaStreamSynchronize(c->stream));
+  int rc = HM_OK;
+  if (!rc) rc = upload_vec(c, dp.ops[K_GETRF], dp.host.getrf);
+  if (!rc) rc = upload_vec(c, dp.ops[K_TRSM], dp.host.trsm);
+  if (!rc) rc = upload_vec(c, dp.ops[K_GEMM], dp.host.gemm);
+  if (!rc) rc = upload_vec(c, dp.ops[K_COPY], dp.host.copy);
+  if (!rc) rc = upload_vec(c, dp.ops[K_STACK], dp.host.trunc);
+  if (!rc) rc = upload_vec(c, dp.ops[K_EVAL], dp.host.eval);
+  if (!rc) rc = upload_vec(c, dp.ops[K_ACA], dp.host.aca);
+  if (!rc) rc = upload_vec(c, dp.entries, dp.host.entries);
+  if (!rc) {
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) rc = fail(HM_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  }
+  if (rc) {
+    free_ops(c, dp);
+    return rc;
+  }
   dp.uploaded = true;
   return HM_OK;
 }
 
 void free_plan(hm_ctx* c, DevPlan& dp) {
-  for (int k = 0; k < NKIND; ++k) dfree(c, dp.ops[k]);
-  dfree(c, dp.entries);
+  free_ops(c, dp);
   dfree(c, dp.sd);
   dfree(c, dp.si);
   dfree(c, dp.cnt);
@@ -154,7 +168,7 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
     fl_host = nullptr;
   size_t li = 0;
   for (const Launch& L : dp.host.launches) {
-    const int buf = L.kind == K_CORE ? K_STACK : L.kind;
+    const int buf = L.kind == K_CORE ? K_STACK : (L.kind == K_GEMM_TC ? K_GEMM : L.kind);
     const char* base = (const char*)dp.ops[buf].p;
     const void* ops = base + (size_t)L.begin * op_size(L.kind);
     if (prof) {
@@ -306,24 +320,39 @@ int read_ranks(hm_ctx* c, const Buf& ranks, int nr, int64_t* maxr, int64_t* sumr
 
 constexpr int NCOUNT = NFC + NKIND;
 
+constexpr int NSTATUS = 8;
+
 struct Counters {
-  Buf b;   // NCOUNT unsigned long long + 4 ints
+  Buf b;   // NCOUNT unsigned long long + NSTATUS ints
   unsigned long long* flops() { return (unsigned long long*)b.p; }
   int* status() { return (int*)((char*)b.p + NCOUNT * sizeof(unsigned long long)); }
 };
 
 int counters_init(hm_ctx* c, Counters& k) {
-  if (!dalloc(c, k.b, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int)))
+  if (!dalloc(c, k.b, NCOUNT * sizeof(unsigned long long) + NSTATUS * sizeof(int)))
     return fail(HM_ENOMEM, "allocator returned NULL (counters)");
-  CU(cudaMemsetAsync(k.b.p, 0, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
+  CU(cudaMemsetAsync(k.b.p, 0, NCOUNT * sizeof(unsigned long long) + NSTATUS * sizeof(int), c->stream));
   return HM_OK;
 }
 
 int counters_read(hm_ctx* c, Counters& k, unsigned long long* fl, int* st) {
   CU(cudaMemcpyAsync(fl, k.b.p, NCOUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaMemcpyAsync(st, k.status(), 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(st, k.status(), NSTATUS * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return HM_OK;
+}
+
+// per-kernel-kind device time, launches and flops: kinds 0..7 in the kind arrays, the tensor-core
+// GEMM kind in its own fields
+void fill_kind_stats(hm_stats* st, const Profile& prof, const unsigned long long* fl) {
+  for (int q = 0; q < 8; ++q) {
+    st->kind_ms[q] = prof.ms[q];
+    st->kind_launches[q] = prof.launches[q];
+    st->kind_flops[q] = (double)fl[NFC + q];
+  }
+  st->tc_ms = prof.ms[K_GEMM_TC];
+  st->tc_launches = prof.launches[K_GEMM_TC];
+  st->tc_flops = (double)fl[NFC + K_GEMM_TC];
 }
 
 Bases make_bases() {
@@ -373,7 +402,8 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
   if (o) opts = *o;
   if (opts.leaf_size < 1 || opts.leaf_size > 64) return fail(HM_EINVAL, "hm_build: leaf_size must be in 1..64");
   if (!(opts.eta >= 0.0)) return fail(HM_EINVAL, "hm_build: eta must be >= 0");
-  if (!(opts.eps > 0.0) || opts.eps >= 1.0) return fail(HM_EINVAL, "hm_build: eps must be in (0, 1)");
+  if (!(opts.eps >= HM_EPS_MIN) || opts.eps >= 1.0)
+    return fail(HM_EINVAL, "hm_build: eps must be in [HM_EPS_MIN, 1) (HM_EPS_MIN = 1e-8, the truncation's floor)");
   if (opts.rank_cap < 1 || opts.rank_cap > 64) return fail(HM_EINVAL, "hm_build: rank_cap must be in 1..64");
   CU(cudaSetDevice(c->device));
   auto A = std::make_unique<hm_matrix>();
@@ -478,7 +508,7 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
     B.status = k.status();
     rc = run_plan(c, dp, B, A->h, nullptr);
     unsigned long long fl[NCOUNT];
-    int st[4];
+    int st[NSTATUS];
     if (rc == HM_OK) rc = counters_read(c, k, fl, st);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
@@ -516,7 +546,10 @@ void hm_matrix_free(hm_matrix* A) {
 int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   if (!c || !A || !out) return fail(HM_EINVAL, "hm_lu: NULL argument");
   double eps = (o && o->eps > 0.0) ? o->eps : A->opts.eps;
-  if (o && o->precision != 0) return fail(HM_EINVAL, "hm_lu: only precision 0 (FP64) is available");
+  if (!(eps >= HM_EPS_MIN) || eps >= 1.0) return fail(HM_EINVAL, "hm_lu: eps must be in [HM_EPS_MIN, 1)");
+  const int precision = o ? o->precision : HM_PREC_FP64;
+  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED)
+    return fail(HM_EINVAL, "hm_lu: precision must be HM_PREC_FP64 or HM_PREC_MIXED");
   CU(cudaSetDevice(c->device));
   try {
     if (!A->dag_built) {
@@ -524,12 +557,13 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
       if (!compute_levels(A->dag)) return fail(HM_EINTERNAL, "hm_lu: task graph has a cycle");
       A->dag_built = true;
     }
-    if (A->lu_plan.eps != eps) {
+    if (A->lu_plan.eps != eps || A->lu_plan.precision != precision) {
       free_plan(c, A->lu_plan);
       auto t0 = std::chrono::steady_clock::now();
-      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load());
+      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision);
       A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       A->lu_plan.eps = eps;
+      A->lu_plan.precision = precision;
     }
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_lu: ") + ex.what());
@@ -592,7 +626,7 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   if (rc) return cleanup(rc);
   if (se) return cleanup(fail(HM_ECUDA, std::string("hm_lu: ") + cudaGetErrorString(se)));
   unsigned long long fl[NCOUNT];
-  int st[4];
+  int st[NSTATUS];
   if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
   fill_matrix_stats(A, &F->st);
   F->st.eps = eps;
@@ -600,12 +634,18 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   for (int q = 0; q < 5; ++q) F->st.flops[q] = (double)fl[q];
   F->st.singular_pivots = st[0];
   F->st.rank_cap_hits = st[1];
-  for (int q = 0; q < NKIND; ++q) {
-    F->st.kind_ms[q] = prof.ms[q];
-    F->st.kind_launches[q] = prof.launches[q];
-    F->st.kind_flops[q] = (double)fl[NFC + q];
-  }
+  F->st.row_interchanges = st[3];
+  F->st.precision = precision;
+  fill_kind_stats(&F->st, prof, fl);
   F->st.launches = (int64_t)P.launches.size();
+  if (st[4] > 0 || st[5] > 0) {
+    hm_factor_free(F.release());
+    dfree(c, sd);
+    dfree(c, si);
+    dfree(c, k.b);
+    return st[4] > 0 ? fail(HM_ETIMEOUT, "hm_lu: a bounded device wait gave up (tensor-core MMA completion)")
+                     : fail(HM_EINTERNAL, "hm_lu: a tensor-core launch had fewer CTAs than tiles");
+  }
   if ((rc = read_ranks(c, F->ranks, A->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
   dfree(c, sd);
   dfree(c, si);
@@ -643,9 +683,12 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
     if (!A[i]) return fail(HM_EINVAL, "hm_lu_batch: NULL matrix");
     out[i] = nullptr;
   }
-  if (o && o->precision != 0) return fail(HM_EINVAL, "hm_lu_batch: only precision 0 (FP64) is available");
+  const int precision = o ? o->precision : HM_PREC_FP64;
+  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED)
+    return fail(HM_EINVAL, "hm_lu_batch: precision must be HM_PREC_FP64 or HM_PREC_MIXED");
   const bool given = o && o->eps > 0.0;
   const double eps = given ? o->eps : A[0]->opts.eps;
+  if (!(eps >= HM_EPS_MIN) || eps >= 1.0) return fail(HM_EINVAL, "hm_lu_batch: eps must be in [HM_EPS_MIN, 1)");
   for (int i = 0; i < count; ++i)
     if (!given && A[i]->opts.eps != eps)
       return fail(HM_EINVAL, "hm_lu_batch: matrices of different eps need opts->eps");
@@ -687,7 +730,7 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
         bp.push_back(bp.back() + A[i]->lay.npiv);
       }
       try {
-        plan_lu_batch(inst, eps, dp.host, g_host_threads.load());
+        plan_lu_batch(inst, eps, dp.host, g_host_threads.load(), precision);
       } catch (const std::exception& ex) {
         return abort_all(fail(HM_EINTERNAL, std::string("hm_lu_batch: ") + ex.what()));
       }
@@ -765,8 +808,10 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
     if (rc) return cleanup(rc);
     if (se) return cleanup(fail(HM_ECUDA, std::string("hm_lu_batch: ") + cudaGetErrorString(se)));
     unsigned long long fl[NCOUNT];
-    int st[4];
+    int st[NSTATUS];
     if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
+    if (st[4] > 0) return cleanup(fail(HM_ETIMEOUT, "hm_lu_batch: a bounded device wait gave up"));
+    if (st[5] > 0) return cleanup(fail(HM_EINTERNAL, "hm_lu_batch: a tensor-core launch had fewer CTAs than tiles"));
     singular += st[0];
     for (int i = i0; i < i1; ++i) {
       const int q = i - i0;
@@ -788,7 +833,9 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
       for (int f = 0; f < 5; ++f) F->st.flops[f] = (double)fl[f];
       F->st.singular_pivots = st[0];
       F->st.rank_cap_hits = st[1];
-      for (int kk = 0; kk < NKIND; ++kk) F->st.kind_flops[kk] = (double)fl[NFC + kk];
+      F->st.row_interchanges = st[3];
+      F->st.precision = precision;
+      fill_kind_stats(&F->st, Profile(), fl);
       F->st.launches = (int64_t)P.launches.size();
       if ((rc = read_ranks(c, F->ranks, A[i]->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
     }
@@ -812,11 +859,16 @@ namespace {
 // small dependent launches, and graph replay removes their host launch cost.
 int run_aux(hm_ctx* c, hm_matrix* A, hm_factor* F, DevPlan& dp, Buf& work, int nv) {
   if (!dp.sd.p) {
+    // all three or none: the replay below needs every one of them
     if (!dalloc(c, dp.sd, std::max<int64_t>(1, dp.host.scratch_doubles) * 8) ||
         !dalloc(c, dp.si, std::max<int64_t>(8, dp.host.scratch_ints) * 4) ||
-        !dalloc(c, dp.cnt, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int)))
+        !dalloc(c, dp.cnt, NCOUNT * sizeof(unsigned long long) + NSTATUS * sizeof(int))) {
+      dfree(c, dp.sd);
+      dfree(c, dp.si);
+      dfree(c, dp.cnt);
       return fail(HM_ENOMEM, "allocator returned NULL (scratch)");
-    CU(cudaMemsetAsync(dp.cnt.p, 0, NCOUNT * sizeof(unsigned long long) + 4 * sizeof(int), c->stream));
+    }
+    CU(cudaMemsetAsync(dp.cnt.p, 0, NCOUNT * sizeof(unsigned long long) + NSTATUS * sizeof(int), c->stream));
   }
   if (launch_set_int((int*)dp.si.p, nv, c->stream)) return fail(HM_ECUDA, "set-int kernel failed");
   if (!dp.exec) {
@@ -1008,6 +1060,34 @@ int hm_solve(hm_ctx* c, hm_factor* F, hm_matrix* A, const double* b, double* x, 
   return done(HM_OK);
 }
 
+int hm_matrix_layout(const hm_matrix* A, int64_t* leaves, int64_t* perm, int64_t* cluster_lo, int64_t* nleaves,
+                     int64_t* nvalues, int64_t* nclusters) {
+  if (!A) return fail(HM_EINVAL, "hm_matrix_layout: NULL matrix");
+  if (nleaves) *nleaves = (int64_t)A->lay.leaf.size();
+  if (nvalues) *nvalues = A->lay.nvalues;
+  if (nclusters) *nclusters = (int64_t)A->ct.cl.size();
+  if (leaves)
+    for (size_t q = 0; q < A->lay.leaf.size(); ++q) {
+      const LeafStore& L = A->lay.leaf[q];
+      const int64_t r[10] = {L.row, L.col, L.m, L.n, L.lr ? 1 : 0, L.cap, L.off, L.voff, L.rank_idx, L.piv_off};
+      std::memcpy(leaves + 10 * q, r, sizeof(r));
+    }
+  if (perm) std::memcpy(perm, A->ct.perm.data(), A->n * sizeof(int64_t));
+  if (cluster_lo)
+    for (size_t q = 0; q < A->ct.cl.size(); ++q) cluster_lo[q] = A->ct.cl[q].lo;
+  return HM_OK;
+}
+
+int hm_matrix_copy_values(hm_ctx* c, hm_matrix* A, double* buf, int to_matrix) {
+  if (!c || !A || !buf) return fail(HM_EINVAL, "hm_matrix_copy_values: NULL argument");
+  CU(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)A->lay.nvalues * 8;
+  if (to_matrix) CU(cudaMemcpyAsync(A->vals.p, buf, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  else CU(cudaMemcpyAsync(buf, A->vals.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HM_OK;
+}
+
 int hm_matrix_stats(const hm_matrix* A, hm_stats* out) {
   if (!A || !out) return fail(HM_EINVAL, "hm_matrix_stats: NULL argument");
   fill_matrix_stats(A, out);
@@ -1027,7 +1107,7 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   if (!c || !W || !Z || !U || !V || !k_out) return fail(HM_EINVAL, "hm_truncate: NULL argument");
   if (m < 1 || n < 1 || K < 0 || K > 256 || cap < 1 || cap > 64 || ldw < m || ldz < n || ldu < m || ldv < n)
     return fail(HM_EINVAL, "hm_truncate: bad sizes (1 <= m, n; 0 <= K <= 256; 1 <= cap <= 64; ld >= rows)");
-  if (!(eps > 0.0)) return fail(HM_EINVAL, "hm_truncate: eps must be > 0");
+  if (!(eps >= HM_EPS_MIN)) return fail(HM_EINVAL, "hm_truncate: eps must be >= HM_EPS_MIN (1e-8)");
   if (m > (int64_t)1 << 30 || n > (int64_t)1 << 30) return fail(HM_EINVAL, "hm_truncate: m or n too large");
   CU(cudaSetDevice(c->device));
   const int capk = (int)std::min<int64_t>(cap, std::min(m, n));
@@ -1151,7 +1231,7 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   const GemmOp* dg = (const GemmOp*)((char*)ops.p + sizeof(t));
   cudaError_t ce = launch_kind(K_STACK, dt, 1, (const StackEntry*)ent.p, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
-  if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_CORE, dt, 1, (const StackEntry*)ent.p, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s, gy1, gz1);
   if (ce) return done(fail(HM_ECUDA, std::string("hm_truncate: ") + cudaGetErrorString(ce)));
   int kk = 0;
@@ -1164,6 +1244,17 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   CU(cudaStreamSynchronize(s));
   *k_out = kk;
   return done(HM_OK);
+}
+
+int hm_selftest_reciprocals(void* cuda_stream, int which, const double* x, double* y, int64_t n) {
+  if (which < 0 || which > 3 || n < 0) return fail(HM_EINVAL, "hm_selftest_reciprocals: bad which or n");
+  if (n == 0) return HM_OK;
+  if (!x || !y) return fail(HM_EINVAL, "hm_selftest_reciprocals: NULL argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = launch_selftest_rcp(x, y, n, which, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return fail(HM_ECUDA, std::string("hm_selftest_reciprocals: ") + cudaGetErrorString(e));
+  return HM_OK;
 }
 
 // ------------------------------------------------------------------------------ structure (host only)

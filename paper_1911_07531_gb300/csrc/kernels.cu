@@ -130,6 +130,15 @@ __device__ __forceinline__ double fast_rcp(double x) {
   return fma(r0, fma(e, e, e), r0);
 }
 
+// Reciprocal of a nonzero pivot: fast_rcp inside [1e-30, 1e30] (bounds compared on the bit
+// patterns of |v|), Newton-Raphson from a rescaled seed outside.
+__device__ __forceinline__ double pivot_rcp(double v) {
+  const long long mag = __double_as_longlong(fabs(v));
+  if (mag > 0x39b4484bfeebc2a0LL && mag < 0x46293e5939a08ceaLL)   // 1e-30 < |v| < 1e30
+    return copysign(fast_rcp(fabs(v)), v);
+  return nr_rcp(v);
+}
+
 // Total order of doubles as signed 64-bit integers (negative values have their magnitude bits
 // flipped): comparisons on the integer pipe instead of ~64-cycle FP64 compares.
 __device__ __forceinline__ long long order_key(double v) {
@@ -355,7 +364,10 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
     }
   }
   if (threadIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-    const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)k);
+    // a symmetric product computes only the entries i <= j: sum_j min(j + 1, m) of them
+    const double entries = sym ? (n <= m ? 0.5 * n * (n + 1.0) : 0.5 * m * (m + 1.0) + (double)(n - m) * m)
+                               : (double)m * n;
+    const unsigned long long f = (unsigned long long)(2.0 * entries * (double)k);
     if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
     atomicAdd(&B.flops[NFC + K_GEMM], f);
   }
@@ -502,9 +514,11 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops, Ba
 // ------------------------------------------------------------------------------ GETRF
 // Partial-pivoting pivot of column c (rows r..b-1) of S by warp 0: the first row of largest
 // |a| (64-bit compare of the magnitudes' bit patterns, then the lowest row among the maxima),
-// and the reciprocal of the pivot (0 for a zero column, which is counted as singular).
+// and the reciprocal of the pivot (0 for a zero column). A pivot of magnitude <= sing_key (the
+// bit pattern of b u max|A_leaf|) is numerically zero and counted as singular (status[0]); a
+// row interchange is counted in status[3].
 __device__ __forceinline__ void getrf_select(double (*S)[65], int c, int r, int b, int* piv, int* s_p,
-                                             double* s_dinv, int slot, int* status) {
+                                             double* s_dinv, int slot, int* status, long long sing_key) {
   const int lane = threadIdx.x & 31;
   long long best = -1;
   int bi = b;
@@ -526,11 +540,9 @@ __device__ __forceinline__ void getrf_select(double (*S)[65], int c, int r, int 
     const double v = S[pp][c];
     double dinv = 0.0;
     const long long mag = gmax;                      // bits of |pivot|
-    if (mag <= 0) atomicAdd(&status[0], 1);
-    else if (mag > 0x39b4484bfeebc2a0LL && mag < 0x46293e5939a08ceaLL)   // 1e-30 < |v| < 1e30
-      dinv = copysign(fast_rcp(fabs(v)), v);
-    else
-      dinv = nr_rcp(v);
+    if (mag <= sing_key) atomicAdd(&status[0], 1);
+    if (pp != c) atomicAdd(&status[3], 1);
+    if (mag > 0) dinv = pivot_rcp(v);
     s_p[slot] = pp;
     s_dinv[slot] = dinv;
     piv[c] = pp;
@@ -548,12 +560,19 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
   __shared__ double S[64][65];
   __shared__ int s_p[2];
   __shared__ double s_dinv[2];
+  __shared__ double red[8];
   double* A = dptr(B, op.A);
   int* piv = iptr(B, op.piv);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < b * b; e += 256) S[e % b][e / b] = A[e];
-  __syncthreads();
-  if (warp == 0) getrf_select(S, 0, 0, b, piv, s_p, s_dinv, 0, B.status);
+  double amax = 0.0;
+  for (int e = tid; e < b * b; e += 256) {
+    const double v = A[e];
+    S[e % b][e / b] = v;
+    amax = fmax(amax, fabs(v));
+  }
+  // numerically zero pivot: |p| <= b u max|A_leaf| (u = 2^-53)
+  const long long sing_key = __double_as_longlong(block_max(amax, red) * (double)b * 0x1p-53);
+  if (warp == 0) getrf_select(S, 0, 0, b, piv, s_p, s_dinv, 0, B.status, sing_key);
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     const int slot = j & 1;
@@ -582,7 +601,7 @@ __global__ void __launch_bounds__(256) k_getrf(const GetrfOp* __restrict__ ops, 
         const double u = S[j][j + 1];
         for (int i = j + 1 + lane; i < b; i += 32) S[i][j + 1] = fma(-S[i][j], u, S[i][j + 1]);
         __syncwarp();
-        getrf_select(S, j + 1, j + 1, b, piv, s_p, s_dinv, slot ^ 1, B.status);
+        getrf_select(S, j + 1, j + 1, b, piv, s_p, s_dinv, slot ^ 1, B.status, sing_key);
       } else {
         // dense enumeration of the trailing block (rows j+1.., columns j+2..): full FP64 warp
         // instructions
@@ -1061,7 +1080,8 @@ __device__ __forceinline__ void backsub_warp(double* Y, int ldy, const double* R
 //      kept vectors in order of decreasing eigenvalue;
 //   7. T_Z = Bm X_k S^{-1/2}, T_W = D^-1 Pi Rf11^-1 X_k S^{1/2} (back substitution).
 // V = Z T_Z has orthonormal columns; U = W T_W carries the singular values.
-__global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, Bases B) {
+__global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, const StackEntry* __restrict__ ent,
+                                              Bases B) {
   const TruncOp op = ops[blockIdx.x];
   extern __shared__ double smem[];            // 2 * JSM * (JSM + 1) doubles
   __shared__ double d[KMAX], dinv[KMAX], rdinv[KMAX], lam[KMAX], cs[KMAX / 2], sn[KMAX / 2], red[32];
@@ -1385,7 +1405,23 @@ __global__ void __launch_bounds__(512) k_core(const TruncOp* __restrict__ ops, B
       return mm >= kq ? 2.0 * mm * kq * kq - 2.0 * kq * kq * kq / 3.0
                       : 2.0 * kq * mm * mm - 2.0 * mm * mm * mm / 3.0;
     };
-    double f = qr(m, Kd) + qr(n, Kd) + 23.0 * Kd * Kd * Kd + 2.0 * (m + n) * Kd * kk;
+    // model flops of a fixed schedule, independent of how many pieces the plan merges into one
+    // rounded addition: the pieces are added one at a time (§2.3's truncation after every
+    // update), each to the target's current rank r: K_i = r + k_i, QR(m, K_i) + QR(n, K_i) +
+    // 2 K_i^3 + 21 K_i^3 + 2 (m + n) K_i r', with r' = min(K_i, final rank) carried on
+    const int ne = ent ? min(op.n_entries, KMAX_ENTRIES) : 0;
+    int ksum = 0;
+    for (int e = 0; e < ne; ++e) ksum += max(dimv(B, ent[op.first_entry + e].k, ent[op.first_entry + e].kd), 0);
+    int r = max(0, K - ksum);
+    double f = 0.0;
+    for (int e = 0; e < ne; ++e) {
+      const int ke = max(dimv(B, ent[op.first_entry + e].k, ent[op.first_entry + e].kd), 0);
+      const double Ki = (double)(r + ke);
+      if (Ki <= 0.0) continue;
+      const int rn = min(r + ke, kk);
+      f += qr(m, Ki) + qr(n, Ki) + 23.0 * Ki * Ki * Ki + 2.0 * (m + n) * Ki * rn;
+      r = rn;
+    }
     atomicAdd(&B.flops[FC_TRUNC], (unsigned long long)f);
     // the core's own share of the model: product of the triangular factors + SVD of K x K
     atomicAdd(&B.flops[NFC + K_CORE], (unsigned long long)(23.0 * Kd * Kd * Kd));
@@ -1551,36 +1587,98 @@ __global__ void __launch_bounds__(256) k_nn2(const double* __restrict__ P, int n
 }
 
 // y(:, c) (+)= alpha * A_exact x(:, c): kernel entries evaluated on the fly, in ORIGINAL order
-__global__ void __launch_bounds__(256) k_exact_mv(const double* __restrict__ P, int n, double h,
-                                                  const double* __restrict__ x, int64_t ldx,
-                                                  double* y, int64_t ldy, int nrhs) {
-  __shared__ double tile[256 * 3];
-  __shared__ double xs[256 * 8];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double xi = 0, yi = 0, zi = 0;
-  if (i < n) { xi = P[3 * i]; yi = P[3 * i + 1]; zi = P[3 * i + 2]; }
-  for (int c0 = 0; c0 < nrhs; c0 += 8) {
-    const int nc = min(8, nrhs - c0);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t0 = 0; t0 < n; t0 += 256) {
-      int j = t0 + threadIdx.x;
-      if (j < n) {
-        tile[3 * threadIdx.x] = P[3 * j];
-        tile[3 * threadIdx.x + 1] = P[3 * j + 1];
-        tile[3 * threadIdx.x + 2] = P[3 * j + 2];
-        for (int c = 0; c < nc; ++c) xs[c * 256 + threadIdx.x] = x[j + (int64_t)(c0 + c) * ldx];
-      }
-      __syncthreads();
-      int cnt = min(256, n - t0);
-      for (int q = 0; q < cnt; ++q) {
-        double dx = xi - tile[3 * q], dy = yi - tile[3 * q + 1], dz = zi - tile[3 * q + 2];
-        double a = 1.0 / (4.0 * M_PI * (sqrt(dx * dx + dy * dy + dz * dz) + h));
-        for (int c = 0; c < nc; ++c) acc[c] = fma(a, xs[c * 256 + q], acc[c]);
-      }
-      __syncthreads();
+// Exact kernel matrix times vectors, y = A x with a_ij = 1/(4 pi (|p_i - p_j| + h)), by tiles of
+// 128 x 128 point pairs. A is symmetric, so a CTA takes one pair of point tiles (I, J), I <= J,
+// evaluates each a_ij once and adds it to both y_i (a_ij x_j, summed in registers) and, for
+// I < J, y_j (a_ij x_i, summed in shared memory); the partial sums go to y with atomic adds, so
+// y must be zero on entry. Warp w works on the 32-column slice (w + s) mod 4 of tile J in
+// super-step s, lane l on column (l + q) mod 32 of it in step q: every column has one writer at
+// a time. The entry is formed with one rounding chain of FP64 FMAs instead of IEEE square
+// root and division: y = 1/sqrt(r^2) from an FP32 seed (operand and seed moved between FP64
+// and FP32 by integer bit moves, r^2 inside the FP32 normal range for any two distinct points
+// of coordinates O(1)) corrected by the series of (1 - e)^(-1/2) to second order,
+// y (1 + e/2 + 3 e^2 / 8) with e = 1 - r^2 y^2; r = r^2 y; 1/(r + h) by fast_rcp; 1/(4 pi) is
+// folded into the staged x. Relative error of each entry ~ 1e-15.
+constexpr int XT = 128;       // points per tile
+constexpr int XNC = 4;        // right-hand sides per pass
+
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  constexpr long long kBias = (long long)(1023 - 127) << 23;
+  const long long xb = __double_as_longlong(x);
+  const float xf = __int_as_float((int)((xb >> 29) - kBias));
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+  const double y0 = __longlong_as_double(((long long)__float_as_int(yf) + kBias) << 29);
+  const double e = fma(-x * y0, y0, 1.0);
+  return fma(y0, e * fma(0.375, e, 0.5), y0);
+}
+
+__device__ __forceinline__ double kernel_rcp_entry(double dx, double dy, double dz, double h) {
+  const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  const double r = r2 > 0.0 ? r2 * rsqrt_fp64(r2) : 0.0;
+  return fast_rcp(r + h);
+}
+
+__global__ void __launch_bounds__(XT) k_exact_mv_sym(const double* __restrict__ P, int n, int nt, double h,
+                                                     const double* __restrict__ x, int64_t ldx, double* y,
+                                                     int64_t ldy, int c0, int nc) {
+  // tile pair (I, J), I <= J, from the linear index b = S(I) + (J - I), S(I) = I nt - I (I - 1) / 2
+  const long long b = blockIdx.x;
+  int I = (int)(nt + 0.5 - sqrt((nt + 0.5) * (nt + 0.5) - 2.0 * (double)b));
+  auto S = [nt](long long i) { return i * nt - i * (i - 1) / 2; };
+  while (I > 0 && S(I) > b) --I;
+  while (S(I + 1) <= b) ++I;
+  const int J = I + (int)(b - S(I));
+  __shared__ double pj[3][XT];
+  __shared__ double xj[XNC][XT];
+  __shared__ double yj[XNC][XT];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const double scale = 1.0 / (4.0 * M_PI);
+  {
+    const int j = J * XT + t;
+    const bool ok = j < n;
+    // padding points sit far away with x = 0: finite entries that add nothing
+    pj[0][t] = ok ? P[3 * j] : 1e3 + t;
+    pj[1][t] = ok ? P[3 * j + 1] : 1e3;
+    pj[2][t] = ok ? P[3 * j + 2] : 1e3;
+    for (int c = 0; c < XNC; ++c) {
+      xj[c][t] = (ok && c < nc) ? x[j + (int64_t)(c0 + c) * ldx] * scale : 0.0;
+      yj[c][t] = 0.0;
     }
-    if (i < n)
-      for (int c = 0; c < nc; ++c) y[i + (int64_t)(c0 + c) * ldy] = acc[c];
+  }
+  const int i = I * XT + t;
+  const bool iok = i < n;
+  const double px = iok ? P[3 * i] : -1e3 - t, py = iok ? P[3 * i + 1] : -1e3, pz = iok ? P[3 * i + 2] : -1e3;
+  double xi[XNC], acc[XNC];
+#pragma unroll
+  for (int c = 0; c < XNC; ++c) {
+    xi[c] = (iok && c < nc) ? x[i + (int64_t)(c0 + c) * ldx] * scale : 0.0;
+    acc[c] = 0.0;
+  }
+  __syncthreads();
+  const bool sym = I < J;
+  for (int st = 0; st < 4; ++st) {
+    const int base = ((warp + st) & 3) * 32;
+    for (int q = 0; q < 32; ++q) {
+      const int j = base + ((lane + q) & 31);
+      const double a = kernel_rcp_entry(px - pj[0][j], py - pj[1][j], pz - pj[2][j], h);
+#pragma unroll
+      for (int c = 0; c < XNC; ++c) {
+        if (c < nc) {
+          acc[c] = fma(a, xj[c][j], acc[c]);
+          if (sym) yj[c][j] = fma(a, xi[c], yj[c][j]);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (iok)
+    for (int c = 0; c < nc; ++c) atomicAdd(&y[i + (int64_t)(c0 + c) * ldy], acc[c]);
+  if (sym) {
+    const int j = J * XT + t;
+    if (j < n)
+      for (int c = 0; c < nc; ++c) atomicAdd(&y[j + (int64_t)(c0 + c) * ldy], yj[c][t]);
   }
 }
 
@@ -1642,9 +1740,10 @@ cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* 
     case K_GEMM: k_gemm<<<dim3(count, gy, gz), 256, GEMM_SMEM, s>>>((const GemmOp*)ops, B); break;
     case K_COPY: k_copy<<<count, 256, 0, s>>>((const CopyOp*)ops, B); break;
     case K_STACK: k_stack<<<dim3(count, gy), 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
-    case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, B); break;
+    case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, entries, B); break;
     case K_EVAL: k_eval<<<count, 256, 0, s>>>((const EvalOp*)ops, B, h); break;
     case K_ACA: k_aca<<<count, 256, 0, s>>>((const AcaOp*)ops, B, h); break;
+    case K_GEMM_TC: return launch_gemm_tc((const GemmOp*)ops, count, B, s, gy);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1657,7 +1756,17 @@ cudaError_t launch_nn2(const double* P, int n, double* out, cudaStream_t s) {
 
 cudaError_t launch_exact_mv(const double* P, int n, double h, const double* x, int64_t ldx, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s) {
-  k_exact_mv<<<(n + 255) / 256, 256, 0, s>>>(P, n, h, x, ldx, y, ldy, nrhs);
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  // y is accumulated with atomic adds: clear it (column by column when ldy > n)
+  cudaError_t e = ldy == n ? cudaMemsetAsync(y, 0, (size_t)n * nrhs * sizeof(double), s)
+                           : cudaMemset2DAsync(y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double),
+                                               (size_t)nrhs, s);
+  if (e) return e;
+  const long long nt = (n + XT - 1) / XT;
+  const long long pairs = nt * (nt + 1) / 2;
+  if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
+  for (int c0 = 0; c0 < nrhs; c0 += XNC)
+    k_exact_mv_sym<<<(unsigned)pairs, XT, 0, s>>>(P, n, (int)nt, h, x, ldx, y, ldy, c0, min(XNC, nrhs - c0));
   return cudaGetLastError();
 }
 
@@ -1703,6 +1812,28 @@ __global__ void k_axpby(const double* __restrict__ x, int64_t ldx, double* y, in
   int i = (int)(e % n), c = (int)(e / n);
   double* d = y + i + c * ldy;
   *d = alpha * x[i + c * ldx] + (beta == 0.0 ? 0.0 : beta * *d);
+}
+
+// y[i] = f(x[i]) for one of the reciprocal helpers of the serial sections (which: 0 nr_rcp,
+// 1 nr_rsqrt, 2 fast_rcp, 3 pivot_rcp), to check them against IEEE division and square root
+__global__ void k_selftest_rcp(const double* __restrict__ x, double* y, int64_t n, int which) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r;
+  switch (which) {
+    case 0: r = nr_rcp(v); break;
+    case 1: r = nr_rsqrt(v); break;
+    case 2: r = fast_rcp(v); break;
+    default: r = pivot_rcp(v); break;
+  }
+  y[i] = r;
+}
+
+cudaError_t launch_selftest_rcp(const double* x, double* y, int64_t n, int which, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_selftest_rcp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n, which);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_colnorm2(const double* x, int64_t ld, int n, int nrhs, double* out, cudaStream_t s) {

@@ -13,6 +13,8 @@ void prepare_kernels();
 // micro-op spread over several CTAs); ignored by the other kinds
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
                         double h, cudaStream_t s, int gy = 1, int gz = 1);
+// K_GEMM_TC launch: gy CTAs per micro-op (128 x 64 tiles of C)
+cudaError_t launch_gemm_tc(const GemmOp* ops, int count, const Bases& B, cudaStream_t s, int gy);
 cudaError_t launch_nn2(const double* P, int n, double* out, cudaStream_t s);
 cudaError_t launch_exact_mv(const double* P, int n, double h, const double* x, int64_t ldx, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);
@@ -26,6 +28,7 @@ cudaError_t launch_permute_points(const double* P, const int64_t* perm, int n, d
 
 namespace hm {
 cudaError_t launch_colnorm2(const double* x, int64_t ld, int n, int nrhs, double* out, cudaStream_t s);
+cudaError_t launch_selftest_rcp(const double* x, double* y, int64_t n, int which, cudaStream_t s);
 cudaError_t launch_axpby(const double* x, int64_t ldx, double* y, int64_t ldy, int n, int nrhs, double alpha,
                          double beta, cudaStream_t s);
 }  // namespace hm

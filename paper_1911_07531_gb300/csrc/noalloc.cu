@@ -36,7 +36,9 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double* g_base[MAX_DEVICES] = {nullptr};
 
-// Device address of g_noalloc_scratch on the current device; looked up once per device.
+// Device address of g_noalloc_scratch on the current device; looked up once per device and
+// cached by device ordinal. The address belongs to the device's primary context (the one the
+// CUDA runtime uses): callers in other contexts, or after cudaDeviceReset, are not supported.
 int scratch_base(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -66,7 +68,9 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   if (m < 1 || n < 1 || K < 0 || K > 256 || cap < 1 || cap > 64 || ldw < m || ldz < n || ldu < m || ldv < n)
     return set_last_error(HM_EINVAL, "hm_truncate_noalloc: bad sizes (1 <= m, n; 0 <= K <= 256; 1 <= cap <= 64; "
                                      "ld >= rows)");
-  if (!(eps > 0.0)) return set_last_error(HM_EINVAL, "hm_truncate_noalloc: eps must be > 0");
+  if (!(eps >= HM_EPS_MIN)) return set_last_error(HM_EINVAL, "hm_truncate_noalloc: eps must be >= HM_EPS_MIN (1e-8)");
+  if (m > (int64_t)1 << 30 || n > (int64_t)1 << 30)
+    return set_last_error(HM_EINVAL, "hm_truncate_noalloc: m or n too large");
   const int capk = (int)std::min<int64_t>(cap, std::min(m, n));
   const int Kc = K < 2 ? 2 : (K + 1) / 2 * 2;
   // layout of the static array (doubles): descriptors | ints + counters | Wst | Zst | Gw | Gz | Tw | Tz | work
@@ -186,12 +190,17 @@ extern "C" int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int 
   B.status = (int*)(base + oCnt + NFC + NKIND);
   ce = launch_kind(K_STACK, dt, 1, de, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg, 2, nullptr, B, 0.0, s, gy0, gz0);
-  if (!ce) ce = launch_kind(K_CORE, dt, 1, nullptr, B, 0.0, s);
+  if (!ce) ce = launch_kind(K_CORE, dt, 1, de, B, 0.0, s);
   if (!ce) ce = launch_kind(K_GEMM, dg + 2, 2, nullptr, B, 0.0, s, gy1, gz1);
   int kk = 0;
   if (!ce) ce = cudaMemcpyAsync(&kk, ints, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (!ce) ce = cudaStreamSynchronize(s);
-  if (ce) return set_last_error(HM_ECUDA, (std::string("hm_truncate_noalloc: ") + cudaGetErrorString(ce)).c_str());
+  if (ce) {
+    // kernels already queued may still use the shared array: let them finish before the next
+    // call can start on another stream
+    cudaStreamSynchronize(s);
+    return set_last_error(HM_ECUDA, (std::string("hm_truncate_noalloc: ") + cudaGetErrorString(ce)).c_str());
+  }
   *k_out = kk;
   return HM_OK;
 }

@@ -19,6 +19,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <unordered_map>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -193,6 +194,8 @@ struct Ctx {
   Wave& w;   // the wave being filled: this context's own, or one shared by several instances
   // offsets of this instance's values, ranks and pivots in their spaces (batched plans)
   int64_t base_d = 0, base_r = 0, base_p = 0;
+  // mixed precision: factor products and rebuild products go to the tensor cores (GF_TF32)
+  bool mixed = false;
   // pieces reaching low-rank leaves in the current wave, by leaf index
   std::map<int, int> target_index;
   std::vector<TargetEntries> targets;
@@ -219,6 +222,11 @@ struct Ctx {
   void gemm(int ph, uint64_t A, int64_t ars, int64_t acs, uint64_t B, int64_t brs, int64_t bcs, uint64_t C,
             int64_t crs, int64_t ccs, Dim m, Dim n, Dim k, double alpha, int flags, int fclass, int dhint = 0) {
     w.need(ph);
+    // mixed precision: the products of Alg 1 (FC_GEMM) and the rebuild products of a rounded
+    // addition (overwrite, not symmetric) run on the tensor cores; Gram products stay FP64
+    if (mixed && !(flags & (GF_SYM_UPPER | GF_A_UPPER | GF_A_UNITLOWER)) &&
+        (fclass == FC_GEMM || (fclass == FC_NONE && (flags & GF_OVERWRITE))))
+      flags |= GF_TF32;
     // split static rows (always legal) and, for accumulating outputs, the static reduction
     int mstep = (m.d || m.s <= GEMM_MCHUNK) ? std::max(m.s, 1) : GEMM_MCHUNK;
     bool ksplit = (flags & GF_ATOMIC) && !k.d && k.s > GEMM_KCHUNK;
@@ -701,6 +709,7 @@ struct Ctx {
 
   // append the wave's phases to the plan in execution order
   void flush() {
+    std::unordered_map<uint64_t, std::pair<int, int>> entry_range;
     for (int ph = 0; ph < w.nph; ++ph) {
       if ((int)w.gemm.size() <= ph) break;
       auto put = [&](int kind, int count, int begin) {
@@ -722,11 +731,33 @@ struct Ctx {
         plan.launches.back().gy = std::min(16, std::max(1, (most + 31) / 32));
       }
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
-      put(K_GEMM, (int)w.gemm[ph].size(), (int)plan.gemm.size());
-      if (!w.gemm[ph].empty()) {
-        GemmOp* out = plan.gemm.extend(w.gemm[ph].size());
-        gemm_grid_to(w.gemm[ph].data(), (int)w.gemm[ph].size(), out, plan.launches.back().gy,
-                     plan.launches.back().gz);
+      {
+        // FP64 micro-ops first, then the tensor-core ones (independent: same phase)
+        std::vector<GemmOp>& g = w.gemm[ph];
+        const auto mid = std::stable_partition(g.begin(), g.end(), [](const GemmOp& o) { return !(o.flags & GF_TF32); });
+        const int n64 = (int)(mid - g.begin()), ntc = (int)(g.end() - mid);
+        put(K_GEMM, n64, (int)plan.gemm.size());
+        if (n64 > 0) {
+          GemmOp* out = plan.gemm.extend(n64);
+          gemm_grid_to(g.data(), n64, out, plan.launches.back().gy, plan.launches.back().gz);
+        }
+        if (ntc > 0) {
+          put(K_GEMM_TC, ntc, (int)plan.gemm.size());
+          // CTAs per micro-op: 128 x 64 tiles of C for the largest static size plus the bound
+          // of a dynamic part (a rank: <= 64; anything else: <= 256)
+          auto bound = [](int st, uint64_t d) {
+            if (!d) return st;
+            const int sp = (int)(d >> 60) - 1;
+            return st + ((sp == IS_RANK || sp == IS_ARANK) ? 64 : 256);
+          };
+          int most = 1;
+          for (auto it = mid; it != g.end(); ++it) {
+            const int mb = bound(it->m, it->md), nb = bound(it->n, it->nd);
+            most = std::max(most, ((mb + 127) / 128) * ((nb + 63) / 64));
+          }
+          plan.launches.back().gy = most;
+          plan.gemm.append(&*mid, ntc);
+        }
       }
       if (!w.stack[ph].empty()) {
         put(K_STACK, (int)w.stack[ph].size(), (int)plan.trunc.size());
@@ -738,8 +769,18 @@ struct Ctx {
           TruncOp op = w.stack[ph][q];
           op.first_entry = (int)plan.entries.size();
           op.n_entries = (int)w.stack_entries[ph][q].size();
+          entry_range[op.Kd] = {op.first_entry, op.n_entries};
           plan.entries.insert(plan.entries.end(), w.stack_entries[ph][q].begin(), w.stack_entries[ph][q].end());
           plan.trunc.push_back(op);
+        }
+      }
+      // the core of a rounded addition reads its pieces' ranks (flop model): same entry range as
+      // its stack record (a later phase of this wave; the stacked-rank slot Kd identifies it)
+      for (TruncOp& op : w.core[ph]) {
+        const auto it = entry_range.find(op.Kd);
+        if (it != entry_range.end()) {
+          op.first_entry = it->second.first;
+          op.n_entries = it->second.second;
         }
       }
       // the cores of a launch are independent: largest stacked-rank bound first, so that the
@@ -859,14 +900,15 @@ void concat_plans(std::vector<Plan>& parts, Plan& plan, int threads) {
       switch (L.kind) {
         case K_GETRF: base = o.getrf; break;
         case K_TRSM: base = o.trsm; break;
-        case K_GEMM: base = o.gemm; break;
+        case K_GEMM:
+        case K_GEMM_TC: base = o.gemm; break;
         case K_COPY: base = o.copy; break;
         case K_STACK:
         case K_CORE: base = o.trunc; break;
         case K_EVAL: base = o.eval; break;
         default: base = o.aca; break;
       }
-      if (L.kind == K_STACK)
+      if (L.kind == K_STACK || L.kind == K_CORE)
         for (int r = 0; r < L.count; ++r) plan.trunc[base + L.begin + r].first_entry += (int)o.entries;
       L.begin += (int)base;
       plan.launches[o.launches + l] = L;
@@ -940,7 +982,7 @@ void plan_wave_ranges(int nlev, const std::vector<size_t>& tasks_per_wave, int t
 }  // namespace
 
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
-             Plan& plan, int threads) {
+             Plan& plan, int threads, int precision) {
   plan = Plan();
   const auto byl = by_level(g);
   std::vector<size_t> per(g.nlevels);
@@ -949,6 +991,7 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
       g.nlevels, per, threads,
       [&](Plan& part, int lv0, int lv1) {
         Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, part);
+        c.mixed = precision == 1;
         for (int lv = lv0; lv < lv1; ++lv) {
           for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
           c.emit_truncations(3, eps);
@@ -958,7 +1001,7 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
       plan);
 }
 
-void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads) {
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads, int precision) {
   plan = Plan();
   if (inst.empty()) return;
   std::vector<std::vector<std::vector<int>>> byl;
@@ -980,6 +1023,7 @@ void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, 
           cs.back()->base_d = I.base_d;
           cs.back()->base_r = I.base_r;
           cs.back()->base_p = I.base_p;
+          cs.back()->mixed = precision == 1;
         }
         for (int lv = lv0; lv < lv1; ++lv) {
           for (size_t i = 0; i < inst.size(); ++i)

@@ -151,8 +151,10 @@ struct Spaces {
 // H-LU: every wave of the levelled task graph expanded into phases of micro-ops. threads: host
 // threads that plan ranges of waves in parallel (0: all hardware threads); any value gives the
 // same plan.
+// precision 1 (mixed): the products of Alg 1 and the rebuild products of the rounded additions
+// are K_GEMM_TC micro-ops (tensor cores, split TF32, FP32 accumulation); 0: all FP64.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
-             double eps, Plan& plan, int threads = 0);
+             double eps, Plan& plan, int threads = 0, int precision = 0);
 // Independent H-LU instances in one plan: wave w of every instance is expanded into the same
 // phases, so that one launch per kind and phase serves all of them (their task graphs have no
 // edges between each other). Instance i addresses its values, ranks and pivots at the given
@@ -164,7 +166,8 @@ struct LuInstance {
   const TaskGraph* g;
   int64_t base_d, base_r, base_p;
 };
-void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads = 0);
+void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads = 0,
+                   int precision = 0);
 // hm_build: dense leaf assembly, ACA + rounded truncation of the admissible leaves.
 void plan_build(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, double eps, int aca_kmax,
                 int64_t scratch_budget_doubles, Plan& plan);

@@ -119,7 +119,7 @@ def _lu_error(ctx, hm, A, F, n, ncol=8, seed=5):
 
 def test_lu_all_dense_equals_dense_lu(ctx, hm):
     p = W.fibonacci_sphere(300, 2)
-    A = hm.hm_build(ctx, p, 64, 0.0, 1e-14, 64)
+    A = hm.hm_build(ctx, p, 64, 0.0, 1e-8, 64)
     F = hm.hm_lu(ctx, A)
     assert _lu_error(ctx, hm, A, F, 300) < 1e-14
     b = np.random.default_rng(4).standard_normal(300)

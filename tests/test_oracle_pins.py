@@ -398,3 +398,39 @@ def test_fp32_products_accuracy_and_refinement():
     assert e32 <= 10 * 1e-4 and abs(e32 - e64) <= 0.05 * e64
     e64, e32 = errs[1e-8]
     assert e32 > 3 * e64 and e32 < 1e-6
+
+
+def test_wave_parallel_runner_matches_recursion():
+    """The task-graph runner (levels of Alg 11 on a thread pool) computes the same factorization
+    as the recursion up to the truncations' rounding: same truncation count, both within
+    10 eps, and their products within 10 eps of each other."""
+    from oracle.wave_parallel import WaveParallelHLU
+    p = W.cube_surface(900, 4)
+    hm = HMatrix(p, 64, 2.0, 1e-6, 64)
+    f1 = HLUFactor(hm).factor()
+    f2 = WaveParallelHLU(hm, threads=4).factor()
+    assert f2.waves > 1 and f2.tasks > f2.waves
+    assert f2.stats.truncations == f1.stats.truncations
+    assert abs(f2.stats.flops - f1.stats.flops) <= 1e-6 * f1.stats.flops
+    A = hm.exact_dense()
+    X = np.random.default_rng(3).standard_normal((hm.n, 4))
+    e1 = np.linalg.norm(A @ X - f1.apply_lu(X)) / np.linalg.norm(A @ X)
+    e2 = np.linalg.norm(A @ X - f2.apply_lu(X)) / np.linalg.norm(A @ X)
+    assert e1 <= 1e-5 and e2 <= 1e-5
+    assert np.linalg.norm(f1.apply_lu(X) - f2.apply_lu(X)) / np.linalg.norm(A @ X) <= 1e-5
+
+
+def test_wave_parallel_runner_needs_the_level_order():
+    """Planted mistake: running the levels in reverse order breaks the factorization."""
+    from oracle.wave_parallel import WaveParallelHLU
+    p = W.cube_surface(600, 4)
+    hm = HMatrix(p, 64, 2.0, 1e-6, 64)
+    f = WaveParallelHLU(hm, threads=2).plan()
+    f._waves = f._waves[::-1]
+    try:                      # a task may meet a block in the wrong state and fail outright
+        f.factor()
+        A = hm.exact_dense()
+        X = np.random.default_rng(3).standard_normal((hm.n, 2))
+        assert np.linalg.norm(A @ X - f.apply_lu(X)) / np.linalg.norm(A @ X) > 1e-2
+    except (AttributeError, TypeError, ValueError, np.linalg.LinAlgError):
+        pass
