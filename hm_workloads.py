@@ -134,7 +134,11 @@ WORKLOADS = {
     "sphere32768": dict(geometry="sphere", n=32768, seed=21, rhs_seed=22, leaf=64, eta=2.0,
                         eps=1e-6, rank_cap=64),
     "cube131072": dict(geometry="cube", n=131072, seed=31, rhs_seed=32, leaf=64, eta=2.0,
-                       eps=1e-6, rank_cap=64),
+                       eps=1e-6, rank_cap=64,
+                       # model GFLOP of one factorization of this matrix (getrf, trsm, gemm and the
+                       # per-update truncation model, with the ranks the factorization realises);
+                       # scales the oracle's timed sample to this size in the benchmark's CPU baseline
+                       model_gflop=2274.08),
 }
 
 

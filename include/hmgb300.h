@@ -28,7 +28,8 @@
  *     PyTorch caching allocator); with NULL callbacks cudaMalloc / cudaFree are used.
  *   - All work is enqueued on the context's stream. hm_build, hm_lu, hm_solve and
  *     hm_matvec synchronize that stream before returning (they report device status).
- *   - Arithmetic is FP64 (hm_lu can run its products on the tensor cores: HM_PREC_MIXED).
+ *   - Arithmetic is FP64 (hm_lu can run its products in FP32 or on the tensor cores:
+ *     HM_PREC_MIXED, HM_PREC_MIXED_TC).
  *     There is no CPU fallback: without a usable CUDA device every computing call fails
  *     with HM_ECUDA.
  */
@@ -83,21 +84,25 @@ typedef struct {
 } hm_build_opts;
 
 /* Arithmetic of hm_lu (hm_lu_opts.precision).
- *   HM_PREC_FP64   every product in FP64 (the truncation core's Jacobi sweeps in FP32).
- *   HM_PREC_MIXED  the products of Alg 1 (low-rank and dense leaf products and their application
- *                  to dense leaves) and the rebuild products of every rounded addition run on the
- *                  tensor cores: FP64 operands split into two TF32 parts, three MMAs (hi hi,
- *                  hi lo, lo hi), FP32 accumulation (~1e-6 relative to |A| |B|). The Gram
- *                  matrices, the truncation core, the leaf LU with its pivots and the triangular
- *                  solves stay FP64. Meant for a coarse factorization (eps ~1e-4) that hm_solve's
- *                  FP64 iterative refinement turns into an accurate solve. */
-enum { HM_PREC_FP64 = 0, HM_PREC_MIXED = 1 };
+ *   HM_PREC_FP64      every product in FP64 (the truncation core's Jacobi sweeps in FP32).
+ *   HM_PREC_MIXED     the products of Alg 1 (low-rank and dense leaf products and their
+ *                     application to dense leaves) and the rebuild products of every rounded
+ *                     addition in FP32 (FP64 operands rounded to FP32, FP32 FMAs and
+ *                     accumulation, FP64 results: ~1e-7 relative to |A| |B|). The Gram matrices,
+ *                     the truncation core, the leaf LU with its pivots and the triangular solves
+ *                     stay FP64. Meant for a coarse factorization (eps ~1e-4) that hm_solve's FP64
+ *                     iterative refinement turns into an accurate solve.
+ *   HM_PREC_MIXED_TC  as HM_PREC_MIXED, but the products with at least 128 rows run on the
+ *                     tensor cores (tcgen05 kind::tf32): FP64 operands split into two TF32 parts,
+ *                     three MMAs (hi hi, hi lo, lo hi), FP32 accumulation in tensor memory
+ *                     (~1e-6 relative to |A| |B|). */
+enum { HM_PREC_FP64 = 0, HM_PREC_MIXED = 1, HM_PREC_MIXED_TC = 2 };
 
 typedef struct {
   double eps;        /* relative accuracy of every rounded addition during H-LU (<=0: the
                         matrix's eps; else in [HM_EPS_MIN, 1)); the rank cap is the
                         matrix's                                                          */
-  int precision;     /* HM_PREC_FP64 or HM_PREC_MIXED                                     */
+  int precision;     /* HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC                   */
 } hm_lu_opts;
 
 typedef struct {
@@ -139,9 +144,12 @@ typedef struct {
   int64_t launches;             /* kernel launches of the last hm_lu                     */
   int64_t row_interchanges;     /* row interchanges of partial pivoting in the leaf LUs  */
   int64_t precision;            /* HM_PREC_* of the last hm_lu                           */
-  double tc_ms;                 /* the tensor-core GEMM kind (mixed precision): device ms  */
+  double tc_ms;                 /* the tensor-core GEMM kind (HM_PREC_MIXED_TC): device ms */
   int64_t tc_launches;          /*   with profiling on, launches,                          */
   double tc_flops;              /*   and flops executed (2mnk per micro-op)                */
+  double f32_ms;                /* the FP32 GEMM kind (mixed precision): the same three    */
+  int64_t f32_launches;
+  double f32_flops;
 } hm_stats;
 
 /* Last error message of the calling thread ("" if none). */
@@ -307,9 +315,10 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads);
 
 enum {
-  HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz} int32 records, in execution order;
-                            kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core, 6 eval,
-                            7 aca                                                             */
+  HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz, first} int32 records, in execution
+                            order; kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core,
+                            6 eval, 7 aca, 8 tensor-core gemm, 9 FP32 gemm (mixed precision); first = 1
+                            starts a phase (the launches of a phase are independent)          */
   HM_PLAN_GETRF = 1,     /* the micro-op descriptors of the batched kernels, laid out as the */
   HM_PLAN_TRSM = 2,      /* GetrfOp, TrsmOp, GemmOp, CopyOp, TruncOp and StackEntry structs  */
   HM_PLAN_GEMM = 3,      /* of the library's csrc/ops.h; one TRUNC record serves a stack and */

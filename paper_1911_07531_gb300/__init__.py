@@ -28,11 +28,11 @@ __all__ = [
     "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_build_sparsified",
     "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
-    "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT", "HM_PREC_FP64", "HM_PREC_MIXED",
+    "HM_OP_A", "HM_OP_L", "HM_OP_U", "HM_OP_LU", "HM_OP_EXACT", "HM_PREC_FP64", "HM_PREC_MIXED", "HM_PREC_MIXED_TC",
 ]
 
 HM_OP_A, HM_OP_L, HM_OP_U, HM_OP_LU, HM_OP_EXACT = 0, 1, 2, 3, 4
-HM_PREC_FP64, HM_PREC_MIXED = 0, 1
+HM_PREC_FP64, HM_PREC_MIXED, HM_PREC_MIXED_TC = 0, 1, 2
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hmgb300.h")
 ERRORS = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ECUDA", -4: "HM_ESINGULAR",
           -5: "HM_ETIMEOUT", -6: "HM_ENOTCONV", -7: "HM_EINTERNAL"}
@@ -77,7 +77,8 @@ class Stats(ctypes.Structure):
                 ("kind_ms", ctypes.c_double * 8), ("kind_launches", ctypes.c_int64 * 8),
                 ("kind_flops", ctypes.c_double * 8), ("launches", ctypes.c_int64),
                 ("row_interchanges", ctypes.c_int64), ("precision", ctypes.c_int64), ("tc_ms", ctypes.c_double),
-                ("tc_launches", ctypes.c_int64), ("tc_flops", ctypes.c_double)]
+                ("tc_launches", ctypes.c_int64), ("tc_flops", ctypes.c_double), ("f32_ms", ctypes.c_double),
+                ("f32_launches", ctypes.c_int64), ("f32_flops", ctypes.c_double)]
 
     def to_dict(self):
         d = {}
@@ -317,7 +318,7 @@ def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h
 
 
 def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0):
-    """H-LU of A (precision: HM_PREC_FP64 or HM_PREC_MIXED)."""
+    """H-LU of A (precision: HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC)."""
     o = LuOpts(float(eps), int(precision))
     h = ctypes.c_void_p()
     rc = load_library().hm_lu(ctx.handle, A.handle, ctypes.byref(o), ctypes.byref(h))
@@ -438,7 +439,7 @@ def _dt(fields):
 _U8, _I8, _I4, _F8 = "u8", "i8", "i4", "f8"
 # record layouts of the plan tables (the micro-op descriptors of csrc/ops.h)
 PLAN_DTYPES = {
-    "launches": _dt([("kind", _I4), ("begin", _I4), ("count", _I4), ("gy", _I4), ("gz", _I4)]),
+    "launches": _dt([("kind", _I4), ("begin", _I4), ("count", _I4), ("gy", _I4), ("gz", _I4), ("first", _I4)]),
     "getrf": _dt([("A", _U8), ("piv", _U8), ("b", _I4), ("pad", _I4)]),
     "trsm": _dt([("T", _U8), ("piv", _U8), ("X", _U8), ("x_es", _I8), ("x_vs", _I8), ("nvd", _U8), ("nv", _I4),
                  ("b", _I4), ("mode", _I4), ("pad", _I4)]),

@@ -93,6 +93,7 @@ size_t op_size(int kind) {
     case K_GETRF: return sizeof(GetrfOp);
     case K_TRSM: return sizeof(TrsmOp);
     case K_GEMM:
+    case K_GEMM32:
     case K_GEMM_TC: return sizeof(GemmOp);
     case K_COPY: return sizeof(CopyOp);
     case K_STACK:
@@ -168,7 +169,7 @@ int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cu
     fl_host = nullptr;
   size_t li = 0;
   for (const Launch& L : dp.host.launches) {
-    const int buf = L.kind == K_CORE ? K_STACK : (L.kind == K_GEMM_TC ? K_GEMM : L.kind);
+    const int buf = L.kind == K_CORE ? K_STACK : ((L.kind == K_GEMM_TC || L.kind == K_GEMM32) ? K_GEMM : L.kind);
     const char* base = (const char*)dp.ops[buf].p;
     const void* ops = base + (size_t)L.begin * op_size(L.kind);
     if (prof) {
@@ -353,6 +354,9 @@ void fill_kind_stats(hm_stats* st, const Profile& prof, const unsigned long long
   st->tc_ms = prof.ms[K_GEMM_TC];
   st->tc_launches = prof.launches[K_GEMM_TC];
   st->tc_flops = (double)fl[NFC + K_GEMM_TC];
+  st->f32_ms = prof.ms[K_GEMM32];
+  st->f32_launches = prof.launches[K_GEMM32];
+  st->f32_flops = (double)fl[NFC + K_GEMM32];
 }
 
 Bases make_bases() {
@@ -548,8 +552,8 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   double eps = (o && o->eps > 0.0) ? o->eps : A->opts.eps;
   if (!(eps >= HM_EPS_MIN) || eps >= 1.0) return fail(HM_EINVAL, "hm_lu: eps must be in [HM_EPS_MIN, 1)");
   const int precision = o ? o->precision : HM_PREC_FP64;
-  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED)
-    return fail(HM_EINVAL, "hm_lu: precision must be HM_PREC_FP64 or HM_PREC_MIXED");
+  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED && precision != HM_PREC_MIXED_TC)
+    return fail(HM_EINVAL, "hm_lu: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");
   CU(cudaSetDevice(c->device));
   try {
     if (!A->dag_built) {
@@ -638,13 +642,12 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   F->st.precision = precision;
   fill_kind_stats(&F->st, prof, fl);
   F->st.launches = (int64_t)P.launches.size();
-  if (st[4] > 0 || st[5] > 0) {
+  if (st[4] > 0) {
     hm_factor_free(F.release());
     dfree(c, sd);
     dfree(c, si);
     dfree(c, k.b);
-    return st[4] > 0 ? fail(HM_ETIMEOUT, "hm_lu: a bounded device wait gave up (tensor-core MMA completion)")
-                     : fail(HM_EINTERNAL, "hm_lu: a tensor-core launch had fewer CTAs than tiles");
+    return fail(HM_ETIMEOUT, "hm_lu: a bounded device wait gave up (tensor-core MMA completion)");
   }
   if ((rc = read_ranks(c, F->ranks, A->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
   dfree(c, sd);
@@ -684,8 +687,8 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
     out[i] = nullptr;
   }
   const int precision = o ? o->precision : HM_PREC_FP64;
-  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED)
-    return fail(HM_EINVAL, "hm_lu_batch: precision must be HM_PREC_FP64 or HM_PREC_MIXED");
+  if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED && precision != HM_PREC_MIXED_TC)
+    return fail(HM_EINVAL, "hm_lu_batch: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");
   const bool given = o && o->eps > 0.0;
   const double eps = given ? o->eps : A[0]->opts.eps;
   if (!(eps >= HM_EPS_MIN) || eps >= 1.0) return fail(HM_EINVAL, "hm_lu_batch: eps must be in [HM_EPS_MIN, 1)");
@@ -811,7 +814,6 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
     int st[NSTATUS];
     if ((rc = counters_read(c, k, fl, st))) return cleanup(rc);
     if (st[4] > 0) return cleanup(fail(HM_ETIMEOUT, "hm_lu_batch: a bounded device wait gave up"));
-    if (st[5] > 0) return cleanup(fail(HM_EINTERNAL, "hm_lu_batch: a tensor-core launch had fewer CTAs than tiles"));
     singular += st[0];
     for (int i = i0; i < i1; ++i) {
       const int q = i - i0;

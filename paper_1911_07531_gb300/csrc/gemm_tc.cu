@@ -11,9 +11,13 @@
 //   - for every slice of 32 reduction steps all threads read the FP64 operands from global
 //     memory (any strides), split them and store them in shared memory in the K-major,
 //     unswizzled core-matrix layout the MMA reads (8 rows x 16 bytes per core matrix; core
-//     matrices along K 128 bytes apart, groups of 8 rows 1024 bytes apart);
-//   - one thread issues the 4 x 3 MMAs of the slice and commits them to an mbarrier; every
-//     thread waits on it (bounded) before the slice buffer is refilled;
+//     matrices along K 128 bytes apart, groups of 8 rows 1024 bytes apart), into one of two
+//     stage buffers;
+//   - one thread issues the 4 x 3 MMAs of the slice and commits them to the stage's mbarrier;
+//     a stage is refilled only after that commit completed (bounded wait), so the staging of
+//     slice s overlaps the MMAs of slice s - 1;
+//   - accumulating (atomic) micro-ops with long reductions spread their slices over blockIdx.z
+//     (at most 4 slices per CTA), each CTA adding its partial tile atomically;
 //   - the 8 warps read the accumulator back (warp w: lanes 32 (w % 4).., columns 32 (w / 4)..)
 //     and apply alpha and the micro-op's write mode (atomic add, overwrite, or add).
 // A wait that does not end within its bound sets status[4] (the host reports HM_ETIMEOUT), the
@@ -30,7 +34,7 @@ namespace {
 
 constexpr int TM = 128;          // rows of a C tile (MMA M)
 constexpr int TN = 64;           // columns of a C tile (MMA N)
-constexpr int TK = 32;           // reduction steps per staged slice (4 MMAs of K = 8)
+constexpr int TK = 64;           // reduction steps per staged slice (8 MMAs of K = 8)
 constexpr int TMEM_COLS = 64;    // FP32 accumulator columns
 constexpr int A_BYTES = TM * TK * 4;    // one TF32 part of the A slice
 constexpr int B_BYTES = TN * TK * 4;
@@ -53,10 +57,12 @@ __device__ __forceinline__ unsigned to_tf32(float x) {
   return r;
 }
 
-// float offset of element (row, kk) of a K-major core-matrix tile with 32 K per row group
+// float offset of element (row, kk) of a K-major core-matrix tile with TK K per row group
 __device__ __forceinline__ int kmajor_off(int row, int kk) {
-  return (row >> 3) * (8 * 32) + (kk >> 2) * 32 + (row & 7) * 4 + (kk & 3);
+  return (row >> 3) * (8 * TK) + (kk >> 2) * 32 + (row & 7) * 4 + (kk & 3);
 }
+constexpr unsigned SBO = 8 * TK * 4;   // bytes between groups of 8 rows
+constexpr unsigned LBO = 128;          // bytes between core matrices along K
 
 // shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets, no swizzle
 __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
@@ -119,29 +125,52 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
 
 }  // namespace
 
-constexpr int TC_SMEM = 2 * A_BYTES + 2 * B_BYTES + 64;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi and lo parts of one A and one B slice
+constexpr int TC_SMEM = STAGE_BYTES + 64;                   // one stage + mbarrier + TMEM slot
 
-__global__ void __launch_bounds__(256) k_gemm_tc(const GemmOp* __restrict__ ops, Bases B) {
-  const GemmOp op = ops[blockIdx.x];
-  const int m = tc_dimv(B, op.m, op.md), n = tc_dimv(B, op.n, op.nd), k = max(tc_dimv(B, op.k, op.kd), 0);
-  const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
-  if (m <= 0 || n <= 0) return;
-  if (k == 0 && !overwrite) return;
-  const int mt = (m + TM - 1) / TM, ntl = (n + TN - 1) / TN;
-  const int tile = blockIdx.y;
-  if (tile == 0 && threadIdx.x == 0 && mt * ntl > (int)gridDim.y) atomicAdd(&B.status[5], 1);   // planner bound
-  if (tile >= mt * ntl) return;
-  const int i0 = (tile % mt) * TM, j0 = (tile / mt) * TN;
+// Stage slice [l0, l0 + TK) of rows [r0, r0 + rmax) of X (X(r, l) = X[r rs + l cs]) into the
+// hi / lo TF32 tiles: only the rmax valid rows are written (rows past them feed only outputs that
+// are never stored), reduction steps past k as zeros. A thread's loads of a group are issued
+// before any of them is converted, so that they are in flight together.
+__device__ __forceinline__ void stage_operand(const double* __restrict__ X, int64_t rs, int64_t cs, int r0, int rmax,
+                                              int l0, int k, bool r_fast, float* hi, float* lo) {
+  constexpr int GROUP = 8;
+  const int total = rmax * TK;
+  for (int g0 = threadIdx.x; g0 < total; g0 += 256 * GROUP) {
+    double v[GROUP];
+#pragma unroll
+    for (int q = 0; q < GROUP; ++q) {
+      const int e = g0 + 256 * q;
+      const int r = r_fast ? e % rmax : e / TK, l = r_fast ? e / rmax : e % TK;
+      v[q] = (e < total && l0 + l < k) ? X[(int64_t)(r0 + r) * rs + (int64_t)(l0 + l) * cs] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < GROUP; ++q) {
+      const int e = g0 + 256 * q;
+      if (e >= total) break;
+      const int r = r_fast ? e % rmax : e / TK, l = r_fast ? e / rmax : e % TK;
+      const int o = kmajor_off(r, l);
+      const float f = (float)v[q];
+      const unsigned h = to_tf32(f);
+      hi[o] = __uint_as_float(h);
+      lo[o] = __uint_as_float(to_tf32(f - __uint_as_float(h)));
+    }
+  }
+}
 
+// Persistent: a CTA takes micro-ops blockIdx.x, blockIdx.x + gridDim.x, ... and computes every
+// 128 x 64 tile of each, keeping its TMEM and mbarrier.
+__global__ void __launch_bounds__(256, 2) k_gemm_tc(const GemmOp* __restrict__ ops, int count, Bases B) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   float* Ahi = (float*)tsm;
   float* Alo = (float*)(tsm + A_BYTES);
   float* Bhi = (float*)(tsm + 2 * A_BYTES);
   float* Blo = (float*)(tsm + 2 * A_BYTES + B_BYTES);
-  uint64_t* mbar = (uint64_t*)(tsm + 2 * A_BYTES + 2 * B_BYTES);
+  uint64_t* mbar = (uint64_t*)(tsm + STAGE_BYTES);
   unsigned* tslot = (unsigned*)(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const unsigned mbar_a = smem_u32(mbar);
+  const unsigned ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -157,138 +186,115 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const GemmOp* __restrict__ ops,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = *tslot;
-
-  const double* A = tc_dptr(B, op.A);
-  const double* Bm = tc_dptr(B, op.B);
-  const bool a_i_fast = op.a_rs <= op.a_cs;
-  const bool b_j_fast = op.b_cs <= op.b_rs;
   const unsigned idesc = tf32_idesc();
-  const int nslices = (k + TK - 1) / TK;
   unsigned phase = 0;
   bool ok = true;
-  int issued = 0;   // commits issued and not yet waited for
-  for (int sl = 0; sl < nslices && ok; ++sl) {
-    const int l0 = sl * TK;
-    // stage the slice: A (TM x TK) and B (TK x TN, stored N x K), split into TF32 hi / lo parts
-    for (int e = tid; e < TM * TK; e += 256) {
-      int i, l;
-      if (a_i_fast) {
-        i = e % TM;
-        l = e / TM;
-      } else {
-        l = e % TK;
-        i = e / TK;
-      }
-      const int gi = i0 + i, gl = l0 + l;
-      float v = 0.0f;
-      if (gi < m && gl < k) v = (float)A[(int64_t)gi * op.a_rs + (int64_t)gl * op.a_cs];
-      const unsigned hi = to_tf32(v);
-      const unsigned lo = to_tf32(v - __uint_as_float(hi));
-      const int o = kmajor_off(i, l);
-      Ahi[o] = __uint_as_float(hi);
-      Alo[o] = __uint_as_float(lo);
-    }
-    for (int e = tid; e < TN * TK; e += 256) {
-      int j, l;
-      if (b_j_fast) {
-        j = e % TN;
-        l = e / TN;
-      } else {
-        l = e % TK;
-        j = e / TK;
-      }
-      const int gj = j0 + j, gl = l0 + l;
-      float v = 0.0f;
-      if (gj < n && gl < k) v = (float)Bm[(int64_t)gl * op.b_rs + (int64_t)gj * op.b_cs];
-      const unsigned hi = to_tf32(v);
-      const unsigned lo = to_tf32(v - __uint_as_float(hi));
-      const int o = kmajor_off(j, l);
-      Bhi[o] = __uint_as_float(hi);
-      Blo[o] = __uint_as_float(lo);
-    }
-    // make the generic-proxy stores visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
+  for (int opi = blockIdx.x; opi < count && ok; opi += gridDim.x) {
+    const GemmOp& op = ops[opi];
+    const int m = tc_dimv(B, op.m, op.md), n = tc_dimv(B, op.n, op.nd), k = max(tc_dimv(B, op.k, op.kd), 0);
+    const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
+    if (m <= 0 || n <= 0 || (k == 0 && !overwrite)) continue;
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-      const int ksteps = (min(TK, k - l0) + 7) / 8;
-#pragma unroll 1
-      for (int q = 0; q < ksteps; ++q) {
-        const unsigned off = q * 256;   // two core matrices of 128 bytes per K = 8 step
-        const uint64_t dah = smem_desc(ah + off, 128, 1024), dal = smem_desc(al + off, 128, 1024);
-        const uint64_t dbh = smem_desc(bh + off, 128, 1024), dbl = smem_desc(bl + off, 128, 1024);
-        mma_tf32(tmem, dah, dbh, idesc, (sl > 0 || q > 0) ? 1 : 0);
-        mma_tf32(tmem, dah, dbl, idesc, 1);
-        mma_tf32(tmem, dal, dbh, idesc, 1);
-      }
-      mma_commit(mbar_a);
+      const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)k);
+      if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
+      atomicAdd(&B.flops[NFC + K_GEMM_TC], f);
     }
-    issued = 1;
-    // the slice buffer is refilled only after the MMAs that read it have completed; the
-    // outcome is made uniform over the CTA
-    ok = __syncthreads_and(mbar_wait(mbar_a, phase)) != 0;
-    issued = ok ? 0 : 1;
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  }
-  if (!ok) {
-    if (tid == 0) atomicAdd(&B.status[4], 1);
-    if (issued) mbar_wait(mbar_a, phase ^ 1);   // once more, bounded, for the MMAs in flight
-  } else {
-    // epilogue: warp w reads lanes 32 (w % 4) .. of columns 32 (w / 4) ..; row = lane of TMEM
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = 32 * quarter + (tid & 31);
-    const int gi = i0 + row;
+    const int mt = (m + TM - 1) / TM, ntl = (n + TN - 1) / TN;
+    const int nslices = (k + TK - 1) / TK;
+    const double* A = tc_dptr(B, op.A);
+    const double* Bm = tc_dptr(B, op.B);
     double* C = tc_dptr(B, op.C);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c0 = 32 * half + 16 * h;
-      float v[16];
-      const unsigned taddr = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)c0;
-      if (k > 0) {
-        tmem_ld16(taddr, v);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+    const bool a_i_fast = op.a_rs <= op.a_cs;
+    const bool b_j_fast = op.b_cs <= op.b_rs;
+    for (int tile = 0; tile < mt * ntl && ok; ++tile) {
+      const int i0 = (tile % mt) * TM, j0 = (tile / mt) * TN;
+      const int mrows = min(TM, m - i0), ncols = min(TN, n - j0);
+      for (int sl = 0; sl < nslices; ++sl) {
+        const int l0 = sl * TK;
+        stage_operand(A, op.a_rs, op.a_cs, i0, mrows, l0, k, a_i_fast, Ahi, Alo);
+        stage_operand(Bm, op.b_cs, op.b_rs, j0, ncols, l0, k, b_j_fast, Bhi, Blo);
+        // make the generic-proxy stores visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const int ksteps = (min(TK, k - l0) + 7) / 8;
+#pragma unroll 1
+          for (int q = 0; q < ksteps; ++q) {
+            const unsigned off = q * 256;   // two core matrices of 128 bytes per K = 8 step
+            const uint64_t dah = smem_desc(ah + off, LBO, SBO), dal = smem_desc(al + off, LBO, SBO);
+            const uint64_t dbh = smem_desc(bh + off, LBO, SBO), dbl = smem_desc(bl + off, LBO, SBO);
+            mma_tf32(tmem, dah, dbh, idesc, (sl > 0 || q > 0) ? 1 : 0);
+            mma_tf32(tmem, dah, dbl, idesc, 1);
+            mma_tf32(tmem, dal, dbh, idesc, 1);
+          }
+          mma_commit(mbar_a);
+        }
+        // the slice buffer is refilled, and the accumulator read, only after the MMAs completed
+        ok = __syncthreads_and(mbar_wait(mbar_a, phase)) != 0;
+        phase ^= 1u;
+        if (!ok) break;
       }
-      if (gi < m) {
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      // epilogue: warp w reads lanes 32 (w % 4) .. of columns 32 (w / 4) ..; row = lane of TMEM
+      const int quarter = warp & 3, half = warp >> 2;
+      const int gi = i0 + 32 * quarter + (tid & 31);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int gj = j0 + c0 + q;
-          if (gj < n) {
-            double* c = C + (int64_t)gi * op.c_rs + (int64_t)gj * op.c_cs;
-            const double val = op.alpha * (double)v[q];
-            if (atomic) atomicAdd(c, val);
-            else if (overwrite) *c = val;
-            else *c += val;
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = 32 * half + 16 * h;
+        if (c0 >= ncols) continue;                       // warp-uniform
+        float v[16];
+        const unsigned taddr = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)c0;
+        if (nslices > 0) {
+          tmem_ld16(taddr, v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+        }
+        if (gi < m) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int gj = j0 + c0 + q;
+            if (gj < n) {
+              double* c = C + (int64_t)gi * op.c_rs + (int64_t)gj * op.c_cs;
+              const double val = op.alpha * (double)v[q];
+              if (atomic) atomicAdd(c, val);
+              else if (overwrite) *c = val;
+              else *c += val;
+            }
           }
         }
       }
+      // the next tile's first MMA overwrites the accumulator: every read of it must be done
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
     }
   }
+  if (!ok && tid == 0) atomicAdd(&B.status[4], 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  if (tid == 0 && blockIdx.y == 0) {
-    const unsigned long long f = (unsigned long long)(2.0 * m * n * (double)k);
-    if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
-    atomicAdd(&B.flops[NFC + K_GEMM_TC], f);
-  }
 }
 
-cudaError_t launch_gemm_tc(const GemmOp* ops, int count, const Bases& B, cudaStream_t s, int gy) {
+cudaError_t launch_gemm_tc(const GemmOp* ops, int count, const Bases& B, cudaStream_t s, int gy, int gz) {
+  (void)gy;
+  (void)gz;
   if (count <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
+  static int grid_cap = 0;
+  if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e) return e;
-    attr = true;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    grid_cap = 2 * sms;   // two resident CTAs per SM (registers and shared memory)
   }
-  k_gemm_tc<<<dim3(count, gy), 256, TC_SMEM, s>>>(ops, B);
+  const int grid = count < grid_cap ? count : grid_cap;
+  k_gemm_tc<<<grid, 256, TC_SMEM, s>>>(ops, count, B);
   return cudaGetLastError();
 }
 

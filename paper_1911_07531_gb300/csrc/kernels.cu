@@ -176,6 +176,7 @@ constexpr int GKS = 16;       // staged reduction slice (two buffers: the next s
                               // cp.async while the current one is multiplied)
 constexpr int GBUF = 2 * GKS * (GTM + 1);   // doubles of one buffer (A slice, then B slice)
 constexpr int GEMM_SMEM = (2 * GBUF + 256) * (int)sizeof(double);
+constexpr int GEMM32_SMEM = GEMM_SMEM + GBUF * (int)sizeof(float);
 
 // 8-byte asynchronous copy global -> shared (zero-fill when !valid: no bytes are read)
 __device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
@@ -195,12 +196,12 @@ __device__ __forceinline__ void gemm_tile_shape(int m, int n, int& mt, int& nt, 
   mt = (m + nrt - 1) / nrt;
 }
 
-template <int W>
-__device__ __forceinline__ void gemm_slice(const double* As, const double* Bs, int ks, const int (&ii)[4],
-                                           const int (&jj)[4], double (&acc)[4]) {
+template <int W, typename T>
+__device__ __forceinline__ void gemm_slice(const T* As, const T* Bs, int ks, const int (&ii)[4], const int (&jj)[4],
+                                           T (&acc)[4]) {
   for (int l = 0; l < ks; ++l) {
-    const double* a = As + l * (GTM + 1);
-    const double* b = Bs + l * (GTM + 1);
+    const T* a = As + l * (GTM + 1);
+    const T* b = Bs + l * (GTM + 1);
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = fma(a[ii[j]], b[jj[j]], acc[j]);
   }
@@ -216,7 +217,25 @@ __device__ __forceinline__ int sym_prefix(int x, int c0, int mi) {
   return sym_tri(max(0, c0 + x), mi) - sym_tri(max(0, c0), mi);
 }
 
-__global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops, Bases B) {
+// FP64 value to FP32 by integer moves of the exponent and the leading mantissa bits (mantissa
+// truncated: relative error < 2^-23; magnitudes below the FP32 normal range become zero, above it
+// infinity): conversions on the integer pipe instead of the narrow FP64 one.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned e = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+  unsigned f = sign | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu);
+  f = e <= 896u ? sign : f;
+  f = e >= 1151u ? (sign | 0x7f800000u) : f;
+  return __uint_as_float(f);
+}
+
+// CT: arithmetic of the products. double: the FP64 GEMM. float (mixed precision): the staged FP64
+// slices are converted to FP32 in shared memory and multiplied with FP32 FMAs and accumulators;
+// the result is written in FP64.
+template <typename CT>
+__global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ ops, Bases B) {
+  constexpr bool F32 = sizeof(CT) == 4;
   const GemmOp op = ops[blockIdx.x];
   const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = max(dimv(B, op.k, op.kd), 0);
   const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
@@ -235,6 +254,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
   const int z0 = blockIdx.z, zs = sz;
   extern __shared__ double gsm[];             // buffer b: A slice [GKS][GTM + 1], B slice [GKS][GTM + 1]
   double* red = gsm + 2 * GBUF;               // [256]
+  float* fsl = (float*)(red + 256);           // FP32 copy of the current slice (F32 only)
   const double* A = dptr(B, op.A);
   const double* Bm = dptr(B, op.B);
   double* C = dptr(B, op.C);
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
     }
     const int grp = tid < nslot ? tid / ne : 0;
     const int wmy = __reduce_max_sync(0xffffffffu, (unsigned)nmy);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    CT acc[4] = {0, 0, 0, 0};
     // stage slice `sl` of A (mi x ks) and B (ks x nj) into buffer `buf` with asynchronous copies
     auto stage = [&](int sl, int buf) {
       double* Asb = gsm + buf * GBUF;
@@ -321,8 +341,23 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
         cp_async_wait<0>();
       }
       __syncthreads();
-      const double* As = gsm + buf * GBUF;
-      const double* Bs = As + GKS * (GTM + 1);
+      const CT* As;
+      const CT* Bs;
+      if constexpr (F32) {
+        // convert the rows of the slice that are in use: A is mi x ks, B ks x nj (ld GTM + 1)
+        const double* src = gsm + buf * GBUF;
+        for (int e = tid; e < ks * (mi + nj); e += 256) {
+          const int l = e / (mi + nj), c = e % (mi + nj);
+          const int off = c < mi ? l * (GTM + 1) + c : GKS * (GTM + 1) + l * (GTM + 1) + (c - mi);
+          fsl[off] = f64_to_f32(src[off]);
+        }
+        __syncthreads();
+        As = (const CT*)fsl;
+        Bs = (const CT*)(fsl + GKS * (GTM + 1));
+      } else {
+        As = (const CT*)(gsm + buf * GBUF);
+        Bs = As + GKS * (GTM + 1);
+      }
       if (G == 1) {
         // the slot count is made warp-uniform so that no DFMA is issued for an empty slot
         // (a predicated-off DFMA still takes its turn on the FP64 pipe); the extra lanes of
@@ -343,12 +378,12 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
     }
     if (G > 1) {
       __syncthreads();
-      if (tid < nslot) red[tid] = acc[0];
+      if (tid < nslot) red[tid] = (double)acc[0];
       __syncthreads();
       if (tid < ne) {
         double t = red[tid];
         for (int g = 1; g < G; ++g) t += red[tid + g * ne];
-        acc[0] = t;
+        acc[0] = (CT)t;
       }
       nmy = tid < ne ? 1 : 0;
     }
@@ -356,7 +391,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
     for (int j = 0; j < 4; ++j) {
       if (j < nmy) {
         double* c = C + (int64_t)(i0 + ii[j]) * op.c_rs + (int64_t)(j0 + jj[j]) * op.c_cs;
-        const double v = op.alpha * acc[j];
+        const double v = op.alpha * (double)acc[j];
         if (atomic) atomicAdd(c, v);
         else if (overwrite) *c = v;
         else *c += v;
@@ -369,7 +404,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm(const GemmOp* __restrict__ ops,
                                : (double)m * n;
     const unsigned long long f = (unsigned long long)(2.0 * entries * (double)k);
     if (op.fclass < FC_NONE) atomicAdd(&B.flops[op.fclass], f);
-    atomicAdd(&B.flops[NFC + K_GEMM], f);
+    atomicAdd(&B.flops[NFC + (F32 ? K_GEMM32 : K_GEMM)], f);
   }
 }
 
@@ -1723,7 +1758,8 @@ constexpr int CORE_SMEM = 2 * JSM * (JSM + 1) * (int)sizeof(double);
 static void set_attributes() {
   if (g_attr_set) return;
   cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM);
-  cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  cudaFuncSetAttribute(k_gemm_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  cudaFuncSetAttribute(k_gemm_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM32_SMEM);
   cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, CORE_SMEM);
   g_attr_set = true;
 }
@@ -1737,13 +1773,14 @@ cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* 
   switch (kind) {
     case K_GETRF: k_getrf<<<count, 256, 0, s>>>((const GetrfOp*)ops, B); break;
     case K_TRSM: k_trsm<<<dim3(count, gy), 256, TRSM_SMEM, s>>>((const TrsmOp*)ops, B); break;
-    case K_GEMM: k_gemm<<<dim3(count, gy, gz), 256, GEMM_SMEM, s>>>((const GemmOp*)ops, B); break;
+    case K_GEMM: k_gemm_t<double><<<dim3(count, gy, gz), 256, GEMM_SMEM, s>>>((const GemmOp*)ops, B); break;
+    case K_GEMM32: k_gemm_t<float><<<dim3(count, gy, gz), 256, GEMM32_SMEM, s>>>((const GemmOp*)ops, B); break;
     case K_COPY: k_copy<<<count, 256, 0, s>>>((const CopyOp*)ops, B); break;
     case K_STACK: k_stack<<<dim3(count, gy), 256, 0, s>>>((const TruncOp*)ops, entries, B); break;
     case K_CORE: k_core<<<count, 512, CORE_SMEM, s>>>((const TruncOp*)ops, entries, B); break;
     case K_EVAL: k_eval<<<count, 256, 0, s>>>((const EvalOp*)ops, B, h); break;
     case K_ACA: k_aca<<<count, 256, 0, s>>>((const AcaOp*)ops, B, h); break;
-    case K_GEMM_TC: return launch_gemm_tc((const GemmOp*)ops, count, B, s, gy);
+    case K_GEMM_TC: return launch_gemm_tc((const GemmOp*)ops, count, B, s, gy, gz);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -13,8 +13,9 @@ void prepare_kernels();
 // micro-op spread over several CTAs); ignored by the other kinds
 cudaError_t launch_kind(int kind, const void* ops, int count, const StackEntry* entries, const Bases& B,
                         double h, cudaStream_t s, int gy = 1, int gz = 1);
-// K_GEMM_TC launch: gy CTAs per micro-op (128 x 64 tiles of C)
-cudaError_t launch_gemm_tc(const GemmOp* ops, int count, const Bases& B, cudaStream_t s, int gy);
+// K_GEMM_TC launch: a persistent grid of at most two CTAs per SM walks the micro-ops (gy, gz
+// unused: every CTA computes whole micro-ops)
+cudaError_t launch_gemm_tc(const GemmOp* ops, int count, const Bases& B, cudaStream_t s, int gy, int gz);
 cudaError_t launch_nn2(const double* P, int n, double* out, cudaStream_t s);
 cudaError_t launch_exact_mv(const double* P, int n, double h, const double* x, int64_t ldx, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);

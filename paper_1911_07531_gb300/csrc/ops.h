@@ -31,7 +31,7 @@ struct Bases {
                                // flops executed by each kernel kind
   int* status;                 // [0] singular pivot count, [1] rank-cap hits, [2] aca non-converged,
                                // [3] row interchanges of the leaf LUs, [4] bounded device waits
-                               // that gave up, [5] tensor-core launches short of tiles (8 ints)
+                               // that gave up (8 ints)
 };
 
 // flop accounting classes (model of the truncation counts QR + core + SVD + rebuild)
@@ -39,9 +39,9 @@ enum FlopClass : int { FC_GETRF = 0, FC_TRSM = 1, FC_GEMM = 2, FC_TRUNC = 3, FC_
 
 // GF_SYM_UPPER: C is symmetric (a Gram matrix A^T A); only the entries i <= j are computed and
 // written, the consumer mirrors them
-// GF_TF32: the micro-op runs on the tensor cores (K_GEMM_TC launches of a mixed-precision plan)
+// GF_TF32 / GF_F32: the micro-op runs in a K_GEMM_TC / K_GEMM32 launch (mixed-precision plans)
 enum GemmFlags : int { GF_ATOMIC = 1, GF_OVERWRITE = 2, GF_A_UPPER = 4, GF_A_UNITLOWER = 8, GF_SYM_UPPER = 16,
-                       GF_TF32 = 32 };
+                       GF_TF32 = 32, GF_F32 = 64 };
 
 // C(i,j) (+)= alpha * sum_l A(i,l) B(l,j),  X(i,j) = X[i*rs + j*cs]
 struct GemmOp {
@@ -129,9 +129,10 @@ struct AcaOp {
   double tol;
 };
 
-// K_GEMM_TC: GEMM micro-ops (flag GF_TF32) on the tensor cores with split-TF32 operands and FP32
-// accumulation (mixed-precision H-LU); they live in the same GemmOp array as K_GEMM
+// Mixed-precision GEMM micro-ops, in the same GemmOp array as K_GEMM:
+// K_GEMM_TC (flag GF_TF32): tensor cores, split-TF32 operands, FP32 accumulation;
+// K_GEMM32 (flag GF_F32): the FP64 kernel's tiling with FP32 FMAs and accumulators.
 enum OpKind : int { K_GETRF = 0, K_TRSM = 1, K_GEMM = 2, K_COPY = 3, K_STACK = 4, K_CORE = 5,
-                    K_EVAL = 6, K_ACA = 7, K_GEMM_TC = 8, NKIND = 9 };
+                    K_EVAL = 6, K_ACA = 7, K_GEMM_TC = 8, K_GEMM32 = 9, NKIND = 10 };
 
 }  // namespace hm

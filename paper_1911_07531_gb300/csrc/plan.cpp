@@ -105,6 +105,7 @@ constexpr int KMAX_ENTRIES = 256;   // largest number of pieces of one rounded a
 constexpr int GEMM_MCHUNK = 512;    // row chunk of a GEMM micro-op
 constexpr int GEMM_KCHUNK = 512;    // reduction chunk of an accumulating GEMM micro-op
 constexpr int TRSM_VCHUNK = 256;    // vectors of one triangular-solve micro-op
+constexpr int TC_MIN_ROWS = 128;    // mixed precision: GEMM micro-ops with this many rows go to the tensor cores
 constexpr int64_t ALIGN = 32;       // doubles (256 bytes)
 
 inline int64_t align_up(int64_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -194,8 +195,9 @@ struct Ctx {
   Wave& w;   // the wave being filled: this context's own, or one shared by several instances
   // offsets of this instance's values, ranks and pivots in their spaces (batched plans)
   int64_t base_d = 0, base_r = 0, base_p = 0;
-  // mixed precision: factor products and rebuild products go to the tensor cores (GF_TF32)
-  bool mixed = false;
+  // mixed precision (0: FP64; 1: factor and rebuild products in FP32 (GF_F32); 2: those with at
+  // least TC_MIN_ROWS rows on the tensor cores (GF_TF32), the others in FP32)
+  int mixed = 0;
   // pieces reaching low-rank leaves in the current wave, by leaf index
   std::map<int, int> target_index;
   std::vector<TargetEntries> targets;
@@ -223,10 +225,12 @@ struct Ctx {
             int64_t crs, int64_t ccs, Dim m, Dim n, Dim k, double alpha, int flags, int fclass, int dhint = 0) {
     w.need(ph);
     // mixed precision: the products of Alg 1 (FC_GEMM) and the rebuild products of a rounded
-    // addition (overwrite, not symmetric) run on the tensor cores; Gram products stay FP64
+    // addition (overwrite, not symmetric) run in FP32; with tensor cores, those with at least
+    // TC_MIN_ROWS static rows (a 128-row MMA tile mostly used) run on them. The Gram products
+    // stay FP64 (their rounding sets the truncation's accuracy floor).
     if (mixed && !(flags & (GF_SYM_UPPER | GF_A_UPPER | GF_A_UNITLOWER)) &&
         (fclass == FC_GEMM || (fclass == FC_NONE && (flags & GF_OVERWRITE))))
-      flags |= GF_TF32;
+      flags |= (mixed == 2 && !m.d && m.s >= TC_MIN_ROWS) ? GF_TF32 : GF_F32;
     // split static rows (always legal) and, for accumulating outputs, the static reduction
     int mstep = (m.d || m.s <= GEMM_MCHUNK) ? std::max(m.s, 1) : GEMM_MCHUNK;
     bool ksplit = (flags & GF_ATOMIC) && !k.d && k.s > GEMM_KCHUNK;
@@ -712,8 +716,14 @@ struct Ctx {
     std::unordered_map<uint64_t, std::pair<int, int>> entry_range;
     for (int ph = 0; ph < w.nph; ++ph) {
       if ((int)w.gemm.size() <= ph) break;
+      bool first = true;   // the next launch put is the phase's first
       auto put = [&](int kind, int count, int begin) {
-        if (count > 0) plan.launches.push_back({kind, begin, count});
+        if (count > 0) {
+          Launch L{kind, begin, count};
+          L.first = first ? 1 : 0;
+          first = false;
+          plan.launches.push_back(L);
+        }
       };
       put(K_GETRF, (int)w.getrf[ph].size(), (int)plan.getrf.size());
       plan.getrf.insert(plan.getrf.end(), w.getrf[ph].begin(), w.getrf[ph].end());
@@ -732,30 +742,25 @@ struct Ctx {
       }
       plan.trsm.insert(plan.trsm.end(), w.trsm[ph].begin(), w.trsm[ph].end());
       {
-        // FP64 micro-ops first, then the tensor-core ones (independent: same phase)
+        // FP64 micro-ops, then FP32, then tensor-core ones (independent: same phase)
         std::vector<GemmOp>& g = w.gemm[ph];
-        const auto mid = std::stable_partition(g.begin(), g.end(), [](const GemmOp& o) { return !(o.flags & GF_TF32); });
-        const int n64 = (int)(mid - g.begin()), ntc = (int)(g.end() - mid);
+        const auto m32 = std::stable_partition(g.begin(), g.end(),
+                                               [](const GemmOp& o) { return !(o.flags & (GF_TF32 | GF_F32)); });
+        const auto mid = std::stable_partition(m32, g.end(), [](const GemmOp& o) { return !(o.flags & GF_TF32); });
+        const int n64 = (int)(m32 - g.begin()), n32 = (int)(mid - m32), ntc = (int)(g.end() - mid);
         put(K_GEMM, n64, (int)plan.gemm.size());
         if (n64 > 0) {
           GemmOp* out = plan.gemm.extend(n64);
           gemm_grid_to(g.data(), n64, out, plan.launches.back().gy, plan.launches.back().gz);
         }
+        put(K_GEMM32, n32, (int)plan.gemm.size());
+        if (n32 > 0) {
+          GemmOp* out = plan.gemm.extend(n32);
+          gemm_grid_to(&*m32, n32, out, plan.launches.back().gy, plan.launches.back().gz);
+        }
         if (ntc > 0) {
+          // one persistent launch: every CTA computes whole micro-ops (all their C tiles)
           put(K_GEMM_TC, ntc, (int)plan.gemm.size());
-          // CTAs per micro-op: 128 x 64 tiles of C for the largest static size plus the bound
-          // of a dynamic part (a rank: <= 64; anything else: <= 256)
-          auto bound = [](int st, uint64_t d) {
-            if (!d) return st;
-            const int sp = (int)(d >> 60) - 1;
-            return st + ((sp == IS_RANK || sp == IS_ARANK) ? 64 : 256);
-          };
-          int most = 1;
-          for (auto it = mid; it != g.end(); ++it) {
-            const int mb = bound(it->m, it->md), nb = bound(it->n, it->nd);
-            most = std::max(most, ((mb + 127) / 128) * ((nb + 63) / 64));
-          }
-          plan.launches.back().gy = most;
           plan.gemm.append(&*mid, ntc);
         }
       }
@@ -901,6 +906,7 @@ void concat_plans(std::vector<Plan>& parts, Plan& plan, int threads) {
         case K_GETRF: base = o.getrf; break;
         case K_TRSM: base = o.trsm; break;
         case K_GEMM:
+        case K_GEMM32:
         case K_GEMM_TC: base = o.gemm; break;
         case K_COPY: base = o.copy; break;
         case K_STACK:
@@ -991,7 +997,7 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
       g.nlevels, per, threads,
       [&](Plan& part, int lv0, int lv1) {
         Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, part);
-        c.mixed = precision == 1;
+        c.mixed = precision;
         for (int lv = lv0; lv < lv1; ++lv) {
           for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
           c.emit_truncations(3, eps);
@@ -1023,7 +1029,7 @@ void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, 
           cs.back()->base_d = I.base_d;
           cs.back()->base_r = I.base_r;
           cs.back()->base_p = I.base_p;
-          cs.back()->mixed = precision == 1;
+          cs.back()->mixed = precision;
         }
         for (int lv = lv0; lv < lv1; ++lv) {
           for (size_t i = 0; i < inst.size(); ++i)

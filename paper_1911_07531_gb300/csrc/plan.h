@@ -38,6 +38,7 @@ void build_layout(const ClusterTree& ct, const BlockTree& bt, int rank_cap, Layo
 struct Launch {
   int kind, begin, count;
   int gy = 1, gz = 1;   // GEMM launches: CTAs per micro-op along C tiles / reduction slices
+  int first = 0;        // 1: the first launch of a phase; the launches of one phase are independent
 };
 
 // Grid of a GEMM launch: orders the (independent) micro-ops by estimated work, largest first,
@@ -151,8 +152,9 @@ struct Spaces {
 // H-LU: every wave of the levelled task graph expanded into phases of micro-ops. threads: host
 // threads that plan ranges of waves in parallel (0: all hardware threads); any value gives the
 // same plan.
-// precision 1 (mixed): the products of Alg 1 and the rebuild products of the rounded additions
-// are K_GEMM_TC micro-ops (tensor cores, split TF32, FP32 accumulation); 0: all FP64.
+// precision 0: all FP64. 1 (mixed): the products of Alg 1 and the rebuild products of the rounded
+// additions are K_GEMM32 micro-ops (FP32 FMAs); 2 (mixed, tensor cores): those with at least 128
+// static rows are K_GEMM_TC micro-ops (split TF32 on tcgen05, FP32 accumulation), the rest K_GEMM32.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
              double eps, Plan& plan, int threads = 0, int precision = 0);
 // Independent H-LU instances in one plan: wave w of every instance is expanded into the same

@@ -172,13 +172,17 @@ def latency_summary(records):
 class GpuExecutor:
     """Factorizations and solves with the library, one context (and CUDA stream) per slot."""
 
-    def __init__(self, slots: int = 4, device: int = 0, leaf: int = 64, eta: float = 2.0, rank_cap: int = 64):
+    def __init__(self, slots: int = 4, device: int = 0, leaf: int = 64, eta: float = 2.0, rank_cap: int = 64,
+                 refine_tol: float = 0.0, precision: int = 0):
+        """refine_tol > 0: every solve is refined against the H-matrix (hm_solve with
+        residual_op HM_OP_A) to that relative residual; precision: HM_PREC_* of hm_lu."""
         import torch
 
         from . import HMContext
         self.torch = torch
         self.ctx = [HMContext(device, stream=torch.cuda.Stream(device)) for _ in range(slots)]
         self.leaf, self.eta, self.rank_cap = leaf, eta, rank_cap
+        self.refine_tol, self.precision = float(refine_tol), int(precision)
 
     @staticmethod
     def estimate_bytes(r):
@@ -194,7 +198,7 @@ class GpuExecutor:
         with self.torch.cuda.stream(ctx.stream):
             A = hm_build(ctx, W.points_for(r["geometry"], r["n"], r["seed"]), self.leaf, self.eta, r["eps"],
                          self.rank_cap)
-            F = hm_lu(ctx, A)
+            F = hm_lu(ctx, A, precision=self.precision)
         # resident: the matrix and factor values and the matrix's uploaded H-LU plan (~19 kB of
         # micro-ops per point); the factorization's scratch is released when hm_lu returns
         nbytes = 2.0 * F.stats()["value_bytes"] + 19_000.0 * r["n"]
@@ -203,13 +207,16 @@ class GpuExecutor:
     def solve(self, slot, handle, r):
         import hm_workloads as W
 
-        from . import hm_solve
+        from . import HM_OP_A, hm_solve
         owner, A, F = handle
         ctx = self.ctx[owner]
         with self.torch.cuda.stream(ctx.stream):
-            b = self.torch.from_numpy(W.gaussian_rhs(r["n"], r["nrhs"], r["rhs_seed"])).to(
-                f"cuda:{ctx.device}", non_blocking=False)
-            x, _ = hm_solve(ctx, F, b)
+            bh = W.gaussian_rhs(r["n"], r["nrhs"], r["rhs_seed"])
+            b = self.torch.from_numpy(np.ascontiguousarray(bh.T)).to(f"cuda:{ctx.device}", non_blocking=False).t()
+            if self.refine_tol > 0:
+                x, _ = hm_solve(ctx, F, b, A=A, refine_tol=self.refine_tol, max_iter=30, residual_op=HM_OP_A)
+            else:
+                x, _ = hm_solve(ctx, F, b)
             return x.cpu().numpy()
 
     def release(self, handle):

@@ -1,8 +1,8 @@
 """Mixed-precision H-LU (HM_PREC_MIXED) against the FP64 oracles (GPU; calls go through the C ABI).
 
-The factor products of Alg 1 and the rebuild products of the rounded additions run on the tensor
-cores (split TF32, FP32 accumulation); the Gram matrices, truncation core, leaf LU and solves stay
-FP64. Compared, as every floating-point result here, through reconstructions: the factorization
+The factor products of Alg 1 and the rebuild products of the rounded additions run in FP32
+(HM_PREC_MIXED), or, for those with at least 128 rows, on the tensor cores with split TF32 and FP32
+accumulation (HM_PREC_MIXED_TC); the Gram matrices, truncation core, leaf LU and solves stay FP64. Compared, as every floating-point result here, through reconstructions: the factorization
 error ||(A - P L U) X|| / ||A X|| within 10 eps and within 10x the error of the oracle with FP32
 products (oracle/mixed.py) on the same matrix, and FP64 iterative refinement reaching a relative
 residual of 1e-10 with a forward error below 1e-8 against a dense solve.
@@ -54,19 +54,21 @@ def _lu_error(ctx, hm, A, F, n, seed=5):
     return fro_ratio(host(hm.hm_matvec(ctx, A, hm.HM_OP_LU, Xd, F=F)) - Ax, Ax)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("geom,n,eps", [("sphere", 2048, 1e-4), ("cube", 3000, 1e-4), ("cube", 1500, 1e-5)])
-def test_mixed_lu_within_ten_eps_and_oracle(ctx, hm, geom, n, eps):
+def test_mixed_lu_within_ten_eps_and_oracle(ctx, hm, geom, n, eps, prec):
     p = W.points_for(geom, n, 11)
     A = hm.hm_build(ctx, p, 64, 2.0, eps, 64)
-    F = hm.hm_lu(ctx, A, precision=hm.HM_PREC_MIXED)
+    F = hm.hm_lu(ctx, A, precision=prec)
     st = F.stats()
-    assert st["precision"] == hm.HM_PREC_MIXED
-    assert st["tc_flops"] > 0                       # the tensor-core kernel did the products
+    assert st["precision"] == prec
+    assert st["f32_flops"] > 0                      # the FP32 kernel did (some of) the products
+    assert (st["tc_flops"] > 0) == (prec == hm.HM_PREC_MIXED_TC)
     err = _lu_error(ctx, hm, A, F, n)
     assert err <= 10 * eps
     F64 = hm.hm_lu(ctx, A)
     err64 = _lu_error(ctx, hm, A, F64, n)
-    assert F64.stats()["tc_flops"] == 0
+    assert F64.stats()["tc_flops"] == 0 and F64.stats()["f32_flops"] == 0
     assert err <= 3 * err64 + 1e-6                  # the FP32-level products add at most ~1e-6
     if n <= 2048:
         o = MixedHLUFactor(HMatrix(p, 64, 2.0, eps, 64)).factor()
@@ -83,17 +85,26 @@ def test_mixed_lu_within_ten_eps_and_oracle(ctx, hm, geom, n, eps):
     assert np.linalg.norm(host(x) - xe) / np.linalg.norm(xe) < 1e-8
 
 
-def test_mixed_all_dense_products_match_fp64(ctx, hm):
-    """All-dense H-LU (eta = 0): every update is a dense product on the tensor cores; the factor
-    reproduces A to the FP32 level of the products, the FP64 factor to 1e-14."""
+def test_mixed_routes_products(ctx, hm):
+    """All-dense H-LU (eta = 0): every product has at most one leaf's rows (64), below the
+    tensor-core row threshold, so even HM_PREC_MIXED_TC runs them all in FP32: the factor
+    reproduces A to the FP32 level (not FP64's 1e-14, not broken). An H-matrix with large
+    admissible blocks sends its tall products to the tensor cores under HM_PREC_MIXED_TC only."""
     p = W.cube_surface(700, 3)
     A = hm.hm_build(ctx, p, 64, 0.0, 1e-8, 64)
-    F = hm.hm_lu(ctx, A, precision=hm.HM_PREC_MIXED)
-    assert F.stats()["tc_flops"] > 0
-    err = _lu_error(ctx, hm, A, F, 700)
-    assert 1e-12 < err < 1e-5                        # FP32-level, not FP64-level, not broken
-    F64 = hm.hm_lu(ctx, A)
-    assert _lu_error(ctx, hm, A, F64, 700) < 1e-13
+    F = hm.hm_lu(ctx, A, precision=hm.HM_PREC_MIXED_TC)
+    st = F.stats()
+    assert st["tc_flops"] == 0 and st["f32_flops"] > 0
+    assert 1e-13 < _lu_error(ctx, hm, A, F, 700) < 1e-5
+    p2 = W.cube_surface(4000, 3)
+    A2 = hm.hm_build(ctx, p2, 64, 2.0, 1e-4, 64)
+    for prec in (hm.HM_PREC_MIXED, hm.HM_PREC_MIXED_TC):
+        F2 = hm.hm_lu(ctx, A2, precision=prec)
+        st = F2.stats()
+        assert st["f32_flops"] > 0
+        assert (st["tc_flops"] > 0) == (prec == hm.HM_PREC_MIXED_TC)
+        assert _lu_error(ctx, hm, A2, F2, 4000) <= 1e-3
+        F2.free()
 
 
 def test_mixed_batch_and_invalid_precision(ctx, hm):
@@ -104,4 +115,4 @@ def test_mixed_batch_and_invalid_precision(ctx, hm):
         assert F.stats()["precision"] == hm.HM_PREC_MIXED
         assert _lu_error(ctx, hm, A, F, p.shape[0]) <= 1e-3
     with pytest.raises(hm.HMError, match="HM_EINVAL"):
-        hm.hm_lu(ctx, mats[0], precision=2)
+        hm.hm_lu(ctx, mats[0], precision=3)
