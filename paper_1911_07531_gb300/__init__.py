@@ -331,7 +331,11 @@ def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0):
 
 
 def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False, precision=0):
-    """H-LU of several independent matrices whose waves share kernel launches; one factor each."""
+    """H-LU of several independent matrices whose waves share kernel launches; one factor each.
+
+    The library sizes its groups of instances by the free device memory; blocks that PyTorch's
+    caching allocator holds do not count as free, so they are returned to the driver first."""
+    ctx._torch.cuda.empty_cache()
     n = len(matrices)
     hs = (ctypes.c_void_p * n)(*[A.handle for A in matrices])
     outs = (ctypes.c_void_p * n)()

@@ -733,7 +733,9 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
         bp.push_back(bp.back() + A[i]->lay.npiv);
       }
       try {
+        const auto tp = std::chrono::steady_clock::now();
         plan_lu_batch(inst, eps, dp.host, g_host_threads.load(), precision);
+        dp.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
       } catch (const std::exception& ex) {
         return abort_all(fail(HM_EINTERNAL, std::string("hm_lu_batch: ") + ex.what()));
       }
@@ -832,6 +834,11 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
       fill_matrix_stats(A[i], &F->st);
       F->st.eps = eps;
       F->st.seconds = ms * 1e-3;
+      F->st.plan_seconds = dp.plan_seconds;         // the group's merged plan
+      F->st.plan_launches = (int64_t)P.launches.size();
+      F->st.plan_phases = P.nphases;
+      F->st.plan_truncations = P.ntrunc;
+      F->st.scratch_bytes = P.scratch_doubles * 8 + P.scratch_ints * 4;
       for (int f = 0; f < 5; ++f) F->st.flops[f] = (double)fl[f];
       F->st.singular_pivots = st[0];
       F->st.rank_cap_hits = st[1];

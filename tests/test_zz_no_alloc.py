@@ -79,3 +79,31 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(hm):
     Z = torch.zeros((8000, 130), dtype=torch.float64, device="cuda")
     with pytest.raises(hm.HMError, match="static scratch"):
         hm.hm_truncate_noalloc(W, Z, 1e-6, 64)
+
+
+def test_noalloc_writes_strided_outputs(hm):
+    """U and V written with leading dimensions larger than their row counts (column slices of
+    bigger buffers): the padding rows keep their values and the product matches hm_truncate."""
+    import ctypes
+    ctx = hm.HMContext(0)
+    m, n, r, K, eps = 300, 200, 20, 24, 1e-6
+    Wd, Zd, exact, s = _case(m, n, r, K, 5)
+    U1, V1 = hm.hm_truncate(ctx, Wd, Zd, eps, 64)
+    ldu, ldv = m + 13, n + 7
+    kc = min(64, m, n)
+    Ub = torch.full((kc, ldu), 7.0, dtype=torch.float64, device="cuda")   # column-major ldu x kc
+    Vb = torch.full((kc, ldv), -3.0, dtype=torch.float64, device="cuda")
+    k = ctypes.c_int(0)
+    st = torch.cuda.current_stream()
+    rc = hm.load_library().hm_truncate_noalloc(ctypes.c_void_p(st.cuda_stream), m, n, K, Wd.data_ptr(), m,
+                                               Zd.data_ptr(), n, eps, 64, Ub.data_ptr(), ldu, Vb.data_ptr(), ldv,
+                                               ctypes.byref(k))
+    assert rc == 0, hm.load_library().hm_last_error()
+    kk = k.value
+    assert kk == U1.shape[1]
+    Ubh, Vbh = Ub.cpu().numpy(), Vb.cpu().numpy()
+    assert (Ubh[:kk, m:] == 7.0).all() and (Vbh[:kk, n:] == -3.0).all()   # padding rows untouched
+    assert (Ubh[kk:] == 7.0).all() and (Vbh[kk:] == -3.0).all()           # columns past the rank
+    P2 = Ubh[:kk, :m].T @ Vbh[:kk, :n]
+    P1 = (U1 @ V1.t()).cpu().numpy()
+    assert np.linalg.norm(P2 - P1, 2) <= 1e-7 * s[0]
