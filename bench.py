@@ -284,7 +284,8 @@ def run_serve(args, rank):
     from paper_1911_07531_gb300.serve import GpuExecutor, Server, latency_summary
     hm.build_library()
     rq = W.serving_requests(count=args.requests, rate=200.0, seed=51)
-    srv = Server(GpuExecutor(args.slots, precision=args.precision), slots=args.slots, budget_bytes=150e9)
+    srv = Server(GpuExecutor(args.slots, precision=args.precision), slots=args.slots, budget_bytes=150e9,
+                 batch=args.serve_batch)
     t0 = time.perf_counter()
     recs = srv.run(rq)
     wall = time.perf_counter() - t0
@@ -302,8 +303,9 @@ def run_serve(args, rank):
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.requests} requests, Poisson 200/s, sphere/cube, n log-uniform in "
                                    "[2048, 131072], 1-32 RHS, eps 1e-4 / 1e-6, 50% repeat solves (seed 51)",
-                       "slots": args.slots, "budget_gb": 150},
+                       "slots": args.slots, "budget_gb": 150, "batch": args.serve_batch},
             "latency": out, "by_kind": by_kind, "wall_s": wall, "evictions": srv.evictions,
+            "factorizations_merged": int(sum(1 for r in recs if r.get("batched", 1) > 1)),
             "peak_gb": srv.peak / 1e9}
     print(json.dumps(line), flush=True)
     return 0
@@ -319,6 +321,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests of the stream")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--precision", type=int, default=0, help="batch64 / serve: HM_PREC_* of hm_lu")
+    ap.add_argument("--serve-batch", type=int, default=4,
+                    help="serve: waiting factorizations merged into one hm_lu_batch call")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solves", type=int, default=10)

@@ -8,7 +8,8 @@ solves again with a factor that an earlier request produced. The loop:
   does not;
 * runs up to `slots` requests at once, each slot with its own CUDA stream (its own library
   context), so that the small kernel launches of concurrent factorizations overlap on the
-  device;
+  device; with `batch` > 1 a slot takes several waiting factorizations of the same eps and
+  factors them in one call whose waves share kernel launches (hm_lu_batch);
 * keeps factors resident after their request, for later solves with them (a solve runs on the
   slot that owns the factor, as soon as that slot is free);
 * records arrival, start and end of every request: latency percentiles and throughput.
@@ -28,10 +29,15 @@ __all__ = ["Server", "GpuExecutor", "latency_summary"]
 
 
 class Server:
-    def __init__(self, executor, slots: int = 4, budget_bytes: float = 150e9, clock=time.perf_counter):
-        if slots < 1:
-            raise ValueError("slots must be >= 1")
+    def __init__(self, executor, slots: int = 4, budget_bytes: float = 150e9, clock=time.perf_counter,
+                 batch: int = 1):
+        """batch > 1: a slot that starts a factorization takes up to `batch` waiting
+        factorization requests of the same eps and factors them in one call of the executor's
+        factorize_batch (their waves share kernel launches: hm_lu_batch)."""
+        if slots < 1 or batch < 1:
+            raise ValueError("slots and batch must be >= 1")
         self.ex = executor
+        self.batch = int(batch)
         self.slots = int(slots)
         self.budget = float(budget_bytes)
         self.clock = clock
@@ -70,13 +76,27 @@ class Server:
         t0 = self.clock()
         pool = ThreadPoolExecutor(max_workers=self.slots)
 
-        def job(slot, r, factor):
+        def job(slot, group, factor):
+            # returns the start time and one (request, handle, bytes, result) per request
             start = self.clock() - t0
             if factor is not None:      # a solve with a resident factor (owned by this slot)
-                return start, None, 0.0, self.ex.solve(slot, factor, r)
-            handle, nbytes = self.ex.factorize(slot, r)
-            out = self.ex.solve(slot, handle, r)
-            return start, handle, nbytes, out
+                return start, [(group[0], None, 0.0, self.ex.solve(slot, factor, group[0]))]
+            if len(group) == 1:
+                made = [self.ex.factorize(slot, group[0])]
+            else:
+                made = self.ex.factorize_batch(slot, group)
+            return start, [(r, h, nb, self.ex.solve(slot, h, r)) for r, (h, nb) in zip(group, made)]
+
+        def new_factor(q):
+            """q as a factorization request (an evicted repeat is factored again), or None."""
+            if q["repeat_of"] is None:
+                return q
+            if q["repeat_of"] in self.resident:
+                return None
+            if any(x["rid"] == q["repeat_of"] for _, grp, _ in running.values() for x in grp) or \
+                    any(x["rid"] == q["repeat_of"] for x in pending):
+                return None
+            return dict(q, repeat_of=None, refactor_of=q["repeat_of"])
 
         try:
             while nxt < len(reqs) or pending or running:
@@ -86,7 +106,10 @@ class Server:
                     nxt += 1
                 # start what can start, in arrival order
                 still = []
+                taken = set()
                 for r in pending:
+                    if r["rid"] in taken:
+                        continue
                     free = [s for s in range(self.slots) if s not in busy]
                     if not free:
                         still.append(r)
@@ -94,7 +117,7 @@ class Server:
                     if r["repeat_of"] is not None:
                         src = self.resident.get(r["repeat_of"])
                         if src is None:
-                            if any(q["rid"] == r["repeat_of"] for _, q, _ in running.values()) or \
+                            if any(q["rid"] == r["repeat_of"] for _, grp, _ in running.values() for q in grp) or \
                                     any(q["rid"] == r["repeat_of"] for q in still):
                                 still.append(r)     # its factor is still being computed
                                 continue
@@ -107,17 +130,36 @@ class Server:
                                 continue
                             src["last"] = now
                             busy.add(src["slot"])
-                            running[pool.submit(job, src["slot"], r, src["handle"])] = (src["slot"], r, 0.0)
+                            running[pool.submit(job, src["slot"], [r], src["handle"])] = (src["slot"], [r], [0.0])
                             continue
                     est = float(self.ex.estimate_bytes(r))
                     if not self._make_room(est, busy):
                         still.append(r)
                         continue
+                    group, ests = [r], [est]
+                    if self.batch > 1:
+                        # later waiting factorizations of the same eps join the group while they fit
+                        for q in pending:
+                            if len(group) >= self.batch:
+                                break
+                            if q["rid"] <= r["rid"] or q["rid"] in taken:
+                                continue
+                            qf = new_factor(q)
+                            if qf is None or qf["eps"] != r["eps"]:
+                                continue
+                            e = float(self.ex.estimate_bytes(qf))
+                            if self.used + sum(ests) + e > self.budget:
+                                continue
+                            if qf.get("refactor_of") is not None:
+                                recs[qf["rid"]]["kind"] = "refactor+solve"
+                            group.append(qf)
+                            ests.append(e)
+                            taken.add(q["rid"])
                     slot = free[0]
                     busy.add(slot)
-                    self.used += est
+                    self.used += sum(ests)
                     self.peak = max(self.peak, self.used)
-                    running[pool.submit(job, slot, r, None)] = (slot, r, est)
+                    running[pool.submit(job, slot, group, None)] = (slot, group, ests)
                 pending = still
                 if running:
                     timeout = None
@@ -125,22 +167,24 @@ class Server:
                         timeout = max(0.0, reqs[nxt]["arrival"] - (self.clock() - t0))
                     done, _ = wait(list(running), timeout=timeout, return_when=FIRST_COMPLETED)
                     for f in done:
-                        slot, r, est = running.pop(f)
+                        slot, group, ests = running.pop(f)
                         busy.discard(slot)
-                        start, handle, nbytes, out = f.result()
+                        start, outs = f.result()
                         end = self.clock() - t0
-                        rec = recs[r["rid"]]
-                        rec.update(start=start, end=end, latency=end - r["arrival"], slot=slot)
-                        results[r["rid"]] = out
-                        if handle is not None:
-                            self.used += nbytes - est
-                            self.peak = max(self.peak, self.used)
-                            key = r.get("refactor_of", r["rid"])
-                            old = self.resident.pop(key, None)
-                            if old is not None:
-                                self.ex.release(old["handle"])
-                                self.used -= old["bytes"]
-                            self.resident[key] = dict(handle=handle, bytes=nbytes, slot=slot, last=end)
+                        for (r, handle, nbytes, out), est in zip(outs, ests):
+                            rec = recs[r["rid"]]
+                            rec.update(start=start, end=end, latency=end - r["arrival"], slot=slot,
+                                       batched=len(group))
+                            results[r["rid"]] = out
+                            if handle is not None:
+                                self.used += nbytes - est
+                                self.peak = max(self.peak, self.used)
+                                key = r.get("refactor_of", r["rid"])
+                                old = self.resident.pop(key, None)
+                                if old is not None:
+                                    self.ex.release(old["handle"])
+                                    self.used -= old["bytes"]
+                                self.resident[key] = dict(handle=handle, bytes=nbytes, slot=slot, last=end)
                 elif nxt < len(reqs):
                     delay = reqs[nxt]["arrival"] - (self.clock() - t0)
                     if delay > 0:
@@ -204,6 +248,20 @@ class GpuExecutor:
         nbytes = 2.0 * F.stats()["value_bytes"] + 19_000.0 * r["n"]
         return (slot, A, F), nbytes
 
+    def factorize_batch(self, slot, group):
+        """Factor several new problems in one hm_lu_batch call (same eps): their waves share the
+        kernel launches. Returns one (handle, resident bytes) per request."""
+        import hm_workloads as W
+
+        from . import hm_build, hm_lu_batch
+        ctx = self.ctx[slot]
+        with self.torch.cuda.stream(ctx.stream):
+            mats = [hm_build(ctx, W.points_for(r["geometry"], r["n"], r["seed"]), self.leaf, self.eta, r["eps"],
+                             self.rank_cap) for r in group]
+            Fs = hm_lu_batch(ctx, mats, precision=self.precision)
+        # resident: the matrix and factor values (the merged plan is released after the call)
+        return [((slot, A, F), 2.0 * F.stats()["value_bytes"]) for A, F in zip(mats, Fs)]
+
     def solve(self, slot, handle, r):
         import hm_workloads as W
 
@@ -237,9 +295,10 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--seed", type=int, default=51)
+    ap.add_argument("--batch", type=int, default=1, help="factorizations merged into one hm_lu_batch call")
     a = ap.parse_args(argv)
     rq = W.serving_requests(count=a.requests, rate=a.rate, seed=a.seed)
-    srv = Server(GpuExecutor(a.slots), slots=a.slots, budget_bytes=a.budget_gb * 1e9)
+    srv = Server(GpuExecutor(a.slots), slots=a.slots, budget_bytes=a.budget_gb * 1e9, batch=a.batch)
     recs = srv.run(rq)
     out = latency_summary(recs)
     out.update(slots=a.slots, budget_gb=a.budget_gb, offered_rate_per_s=a.rate, evictions=srv.evictions,

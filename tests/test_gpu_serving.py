@@ -26,16 +26,20 @@ def hm():
     return hm
 
 
-def test_each_result_equals_alone_and_in_the_mix(hm):
+@pytest.mark.parametrize("batch", [1, 3])
+def test_each_result_equals_alone_and_in_the_mix(hm, batch):
+    """batch 3: waiting factorizations are also merged into hm_lu_batch calls across requests."""
     from paper_1911_07531_gb300.serve import GpuExecutor, Server, latency_summary
     rq = W.serving_requests(count=30, rate=400.0, seed=7, n_min=1024, n_max=6000)
     assert any(r["repeat_of"] is not None for r in rq)
     ex = GpuExecutor(slots=3, refine_tol=1e-10)
-    srv = Server(ex, slots=3, budget_bytes=30e9)
+    srv = Server(ex, slots=3, budget_bytes=30e9, batch=batch)
     recs = srv.run(rq)
     mixed = srv.results
     srv.release_all()
     assert len(mixed) == len(rq)
+    if batch > 1:
+        assert max(r["batched"] for r in recs) > 1
     # concurrency: some request started before another one on a different slot had finished
     overlap = any(a["slot"] != b["slot"] and a["start"] < b["end"] and b["start"] < a["end"]
                   for i, a in enumerate(recs) for b in recs[i + 1:])

@@ -22,6 +22,7 @@ class SimExecutor:
         self.factors = 0
         self.released = 0
         self.solves = []
+        self.batches = []
 
     @staticmethod
     def estimate_bytes(r):
@@ -43,6 +44,12 @@ class SimExecutor:
             self.factors += 1
         self._leave()
         return (slot, r["seed"], r["n"]), 900.0 * r["n"]
+
+    def factorize_batch(self, slot, group):
+        assert len({r["eps"] for r in group}) == 1      # one accuracy per merged call
+        with self.lock:
+            self.batches.append(len(group))
+        return [self.factorize(slot, r) for r in group]
 
     def solve(self, slot, handle, r):
         owner, seed, n = handle
@@ -117,3 +124,27 @@ def test_request_larger_than_the_budget_is_reported():
     rq = [dict(rid=0, arrival=0.0, geometry="cube", n=100000, eps=1e-6, nrhs=1, seed=1, rhs_seed=2, repeat_of=None)]
     with pytest.raises(RuntimeError):
         Server(SimExecutor(), slots=1, budget_bytes=1e6).run(rq)
+
+
+def test_batched_factorizations_serve_every_request_with_its_result_alone():
+    """With batch > 1, waiting factorizations of one eps are grouped into one executor call: every
+    request is served once, groups never mix eps or exceed `batch`, the budget holds, and every
+    result equals the same request served alone."""
+    rq = _stream(160)
+    ex = SimExecutor()
+    srv = Server(ex, slots=3, budget_bytes=2e9, batch=4)
+    recs = srv.run(rq)
+    assert [r["rid"] for r in recs] == [r["rid"] for r in rq]
+    assert ex.batches and max(ex.batches) <= 4 and max(ex.batches) > 1
+    assert srv.peak <= 2e9
+    by_rid = {r["rid"]: r for r in rq}
+    for rec in recs:
+        assert rec["batched"] >= 1
+    for r in rq[:: 9]:
+        alone = Server(SimExecutor(), slots=1, budget_bytes=2e9)
+        src = [q for q in rq if q["rid"] == r["repeat_of"]] + [r]
+        alone.run(src)
+        assert np.array_equal(alone.results[r["rid"]], srv.results[r["rid"]])
+    assert len(srv.results) == len(by_rid)
+    srv.release_all()
+    assert ex.released == ex.factors
