@@ -327,6 +327,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solves", type=int, default=10)
     ap.add_argument("--no-refined", action="store_true", help="skip the eps = 1e-4 + refinement run")
+    ap.add_argument("--autotune", action="store_true",
+                    help="before timing, pick the GEMM split target with hm_autotune_gemm on the workload")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -360,6 +362,10 @@ def main():
     stream = ctx.stream
 
     A = hm.hm_build(ctx, pts, cfg["leaf"], cfg["eta"], cfg["eps"], cfg["rank_cap"])
+    tuning = None
+    if args.autotune:
+        best, times = hm.hm_autotune_gemm(ctx, A)
+        tuning = {"gemm_work": best, "seconds_by_candidate": times}
     # warm-up (the first hm_lu also builds the task graph and the wave plan on the host)
     for _ in range(max(args.warmup, 0)):
         F = hm.hm_lu(ctx, A)
@@ -545,6 +551,7 @@ def main():
                     "includes": "hm_build (points H2D, trees, ACA) + hm_lu (task graph, "
                                 "plan, execution) + hm_solve with host RHS and result"},
             "gpu_launches": launches,
+            "gemm_work": hm.hm_get_gemm_work(),
             "roofline": roofline,
             "clocks": clk.summary(),
             "dag": {"tasks": st0["dag_nodes"], "edges": st0["dag_edges"], "levels": st0["dag_levels"],
@@ -557,6 +564,8 @@ def main():
         }
         if refined is not None:
             line["refined"] = refined
+        if tuning is not None:
+            line["autotune"] = tuning
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

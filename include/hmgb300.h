@@ -257,6 +257,20 @@ int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int K, const do
                         const double* Z, int64_t ldz, double eps, int cap, double* U, int64_t ldu, double* V,
                         int64_t ldv, int* k_out);
 
+/* GEMM split tuning (process-wide): the number of FMAs that one CTA of the batched GEMM kernels
+ * aims at when a micro-op is spread over several CTAs (default 16384). Smaller values give more,
+ * shorter CTAs (more parallelism, more atomic partial sums), larger ones fewer. It changes the
+ * plans (an H-LU plan built at another value is rebuilt at the next hm_lu) and the speed, not
+ * the results beyond rounding. HM_EINVAL outside [256, 2^24]. */
+int hm_set_gemm_work(double fmas_per_cta);
+double hm_get_gemm_work(void);
+/* Autotuner of that setting for one matrix: for every candidate value, plans and factors A
+ * twice with opts (hm_lu) and keeps the device time of the second factorization; leaves the
+ * fastest candidate set and returns it in *best (seconds[q], if not NULL, receives candidate q's
+ * time). The factors are freed. Errors of hm_lu are returned (the previous setting restored). */
+int hm_autotune_gemm(hm_ctx* ctx, hm_matrix* A, const hm_lu_opts* opts, const double* candidates, int ncand,
+                     double* best, double* seconds);
+
 /* Diagnostic: y[i] = f(x[i]) for the FP64 reciprocal helpers that the serial sections of the
  * leaf LU and of the truncation core use instead of IEEE division and square root (no passage
  * of the paper: a property of this implementation). which: 0 Newton-Raphson 1/x from a

@@ -24,7 +24,7 @@ from .build import LIB, build as _build_lib
 __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_lu_batch", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
-    "hm_selftest_reciprocals",
+    "hm_selftest_reciprocals", "hm_set_gemm_work", "hm_get_gemm_work", "hm_autotune_gemm",
     "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_build_sparsified",
     "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
@@ -141,6 +141,9 @@ def load_library():
         "hm_truncate": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_truncate_noalloc": ([P, I64, I64, I, P, I64, P, I64, D, I, P, I64, P, I64, ctypes.POINTER(I)], I),
         "hm_selftest_reciprocals": ([P, I, P, P, I64], I),
+        "hm_set_gemm_work": ([D], I),
+        "hm_get_gemm_work": ([], D),
+        "hm_autotune_gemm": ([P, P, ctypes.POINTER(LuOpts), P, I, ctypes.POINTER(D), P], I),
         "hm_matrix_layout": ([P, P, P, P, P, P, P], I),
         "hm_matrix_copy_values": ([P, P, P, I], I),
         "hm_structure_build": ([P, I64, I, D, I, PP], I),
@@ -420,6 +423,27 @@ def hm_truncate_noalloc(W, Z, eps, cap=64, stream=None):
                                                   Zf.data_ptr(), n, float(eps), int(cap), U.data_ptr(), m,
                                                   V.data_ptr(), n, ctypes.byref(k)))
     return U[:, :k.value], V[:, :k.value]
+
+
+def hm_set_gemm_work(fmas_per_cta):
+    """GEMM split target (FMAs per CTA, process-wide)."""
+    _check(load_library().hm_set_gemm_work(float(fmas_per_cta)))
+
+
+def hm_get_gemm_work():
+    return load_library().hm_get_gemm_work()
+
+
+def hm_autotune_gemm(ctx, A, candidates=(4096.0, 8192.0, 16384.0, 32768.0, 65536.0), eps=0.0, precision=0):
+    """Time hm_lu of A at every candidate GEMM split target, keep the fastest set; returns
+    (best, {candidate: seconds})."""
+    c = (ctypes.c_double * len(candidates))(*[float(v) for v in candidates])
+    t = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_double()
+    o = LuOpts(float(eps), int(precision))
+    _check(load_library().hm_autotune_gemm(ctx.handle, A.handle, ctypes.byref(o), c, len(candidates),
+                                           ctypes.byref(best), t))
+    return best.value, {float(v): t[q] for q, v in enumerate(candidates)}
 
 
 def hm_selftest_reciprocals(x, which, stream=None):

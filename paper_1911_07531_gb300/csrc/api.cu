@@ -82,6 +82,7 @@ struct DevPlan {
   bool uploaded = false;
   double eps = -1.0;
   int precision = -1;
+  double gemm_work = -1.0;   // GEMM split target the plan was built with
   double plan_seconds = 0.0;
   // replay state of solve / matvec plans: persistent scratch and the captured CUDA graph
   Buf sd, si, cnt;
@@ -362,6 +363,7 @@ void fill_kind_stats(hm_stats* st, const Profile& prof, const unsigned long long
 Bases make_bases() {
   Bases B;
   std::memset(&B, 0, sizeof(B));
+  B.gemm_work = (float)gemm_min_work();
   return B;
 }
 
@@ -561,13 +563,14 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
       if (!compute_levels(A->dag)) return fail(HM_EINTERNAL, "hm_lu: task graph has a cycle");
       A->dag_built = true;
     }
-    if (A->lu_plan.eps != eps || A->lu_plan.precision != precision) {
+    if (A->lu_plan.eps != eps || A->lu_plan.precision != precision || A->lu_plan.gemm_work != gemm_min_work()) {
       free_plan(c, A->lu_plan);
       auto t0 = std::chrono::steady_clock::now();
       plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision);
       A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       A->lu_plan.eps = eps;
       A->lu_plan.precision = precision;
+      A->lu_plan.gemm_work = gemm_min_work();
     }
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_lu: ") + ex.what());
@@ -1253,6 +1256,49 @@ int hm_truncate(hm_ctx* c, int64_t m, int64_t n, int K, const double* W, int64_t
   CU(cudaStreamSynchronize(s));
   *k_out = kk;
   return done(HM_OK);
+}
+
+int hm_set_gemm_work(double fmas_per_cta) {
+  if (!(fmas_per_cta >= 256.0) || fmas_per_cta > 16777216.0)
+    return fail(HM_EINVAL, "hm_set_gemm_work: fmas_per_cta must be in [256, 2^24]");
+  set_gemm_min_work(fmas_per_cta);
+  return HM_OK;
+}
+
+double hm_get_gemm_work(void) { return gemm_min_work(); }
+
+int hm_autotune_gemm(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, const double* candidates, int ncand,
+                     double* best, double* seconds) {
+  if (!c || !A || !candidates || ncand < 1 || !best) return fail(HM_EINVAL, "hm_autotune_gemm: bad argument");
+  for (int q = 0; q < ncand; ++q)
+    if (!(candidates[q] >= 256.0) || candidates[q] > 16777216.0)
+      return fail(HM_EINVAL, "hm_autotune_gemm: candidates must be in [256, 2^24]");
+  const double before = gemm_min_work();
+  double best_s = -1.0, best_w = before;
+  for (int q = 0; q < ncand; ++q) {
+    set_gemm_min_work(candidates[q]);
+    double t = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {   // the first factorization plans at this setting
+      hm_factor* F = nullptr;
+      const int rc = hm_lu(c, A, o, &F);
+      if (F) {
+        t = F->st.seconds;
+        hm_factor_free(F);
+      }
+      if (rc != HM_OK && rc != HM_ESINGULAR) {
+        set_gemm_min_work(before);
+        return rc;
+      }
+    }
+    if (seconds) seconds[q] = t;
+    if (best_s < 0.0 || t < best_s) {
+      best_s = t;
+      best_w = candidates[q];
+    }
+  }
+  set_gemm_min_work(best_w);
+  *best = best_w;
+  return HM_OK;
 }
 
 int hm_selftest_reciprocals(void* cuda_stream, int which, const double* x, double* y, int64_t n) {

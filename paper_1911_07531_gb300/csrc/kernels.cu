@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
   // split actually used: the planner's bound, lowered to ~16k FMAs per CTA for the real sizes
   const int symax = max(1, op.split & 0xffff), szmax = atomic ? max(1, op.split >> 16) : 1;
   const double work = (double)m * n * max(k, 1);
-  const int want = min(symax * szmax, max(1, (int)ceil(work * (1.0 / 16384.0))));
+  const double per_cta = B.gemm_work > 0.f ? (double)B.gemm_work : 16384.0;
+  const int want = min(symax * szmax, max(1, (int)ceil(work / per_cta)));
   const int sy = min(min(want, symax), nrt * nct);
   const int sz = min(min((want + sy - 1) / sy, szmax), max(nslices, 1));
   if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;

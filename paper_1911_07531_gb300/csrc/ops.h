@@ -29,6 +29,7 @@ struct Bases {
   int* i[NISPACE];
   unsigned long long* flops;   // [0, NFC): model flops per class; [NFC, NFC+NKIND): algorithmic
                                // flops executed by each kernel kind
+  float gemm_work;             // GEMM split: FMAs per CTA the kernels aim at (0: 16384)
   int* status;                 // [0] singular pivot count, [1] rank-cap hits, [2] aca non-converged,
                                // [3] row interchanges of the leaf LUs, [4] bounded device waits
                                // that gave up (8 ints)

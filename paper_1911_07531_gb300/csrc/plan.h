@@ -46,6 +46,10 @@ struct Launch {
 // C along y, reduction slices of accumulating micro-ops along z, recorded in GemmOp::split);
 // gy, gz are the launch's maxima.
 void gemm_grid(GemmOp* ops, int count, int& gy, int& gz);
+// FMAs per CTA that the GEMM split aims at (process-wide; default 16384): the planner's split
+// bound and, through Bases::gemm_work, the kernels' own lowering of it.
+void set_gemm_min_work(double fmas_per_cta);
+double gemm_min_work();
 // The same, writing the ordered micro-ops with their splits to out (count entries, not
 // overlapping ops).
 void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz);

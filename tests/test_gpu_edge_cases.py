@@ -344,3 +344,27 @@ def test_lu_batch_matches_solo_factors(ctx, hm):
         Fs[i].free()
     for A in mats:
         A.free()
+
+
+# ------------------------------------------------------------------ GEMM split autotuner
+def test_autotune_gemm_split(ctx, hm):
+    """The autotuner times hm_lu at every candidate split target, keeps the fastest set; the
+    factorization stays within 10 eps at every setting."""
+    p = W.fibonacci_sphere(4096, 3)
+    A = hm.hm_build(ctx, p, 64, 2.0, 1e-6, 64)
+    before = hm.hm_get_gemm_work()
+    try:
+        best, times = hm.hm_autotune_gemm(ctx, A, candidates=(4096.0, 16384.0, 65536.0))
+        assert best in times and all(t > 0 for t in times.values())
+        assert times[best] == min(times.values())
+        assert hm.hm_get_gemm_work() == best
+        for w in (4096.0, 65536.0):
+            hm.hm_set_gemm_work(w)
+            F = hm.hm_lu(ctx, A)
+            X = np.random.default_rng(5).standard_normal((4096, 4))
+            Xd = dev(X)
+            Ax = host(hm.hm_matvec(ctx, A, hm.HM_OP_EXACT, Xd))
+            assert fro_ratio(host(hm.hm_matvec(ctx, A, hm.HM_OP_LU, Xd, F=F)) - Ax, Ax) <= 1e-5
+            F.free()
+    finally:
+        hm.hm_set_gemm_work(before)

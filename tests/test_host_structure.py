@@ -220,3 +220,26 @@ def test_no_cpu_fallback_without_a_device(lib):
     assert lib.hm_ctx_create(0, None, hm.ALLOC_FN(), hm.FREE_FN(), None, ctypes.byref(h)) == -3
     assert h.value is None
     assert b"no CUDA device" in lib.hm_last_error()
+
+
+def test_gemm_split_tuning_changes_the_plan_not_its_operations():
+    """The GEMM split target is a process-wide tuning value: a larger FMAs-per-CTA target gives
+    GEMM micro-ops no larger splits and the same operations; out-of-range values are refused."""
+    import paper_1911_07531_gb300 as hm
+    p = W.points_for("cube", 3000, 4)
+    S = hm.hm_structure_build(p, 64, 2.0)
+    before = hm.hm_get_gemm_work()
+    try:
+        with pytest.raises(hm.HMError):
+            hm.hm_set_gemm_work(0.0)
+        hm.hm_set_gemm_work(4096.0)
+        g_small = S.plan(0, 1e-6, 64, 1, 1)["gemm"].copy()
+        hm.hm_set_gemm_work(262144.0)
+        g_large = S.plan(0, 1e-6, 64, 1, 1)["gemm"].copy()
+    finally:
+        hm.hm_set_gemm_work(before)
+    assert len(g_small) == len(g_large)
+    sp = lambda g: (g["split"] & 0xffff) * np.maximum(1, g["split"] >> 16)
+    assert sp(g_large).sum() < sp(g_small).sum()
+    key = lambda g: np.sort(g[["A", "B", "C", "m", "n", "k"]], order=["A", "B", "C", "m", "n", "k"])
+    assert (key(g_small) == key(g_large)).all()
