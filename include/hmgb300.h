@@ -129,7 +129,7 @@ typedef struct {
   int64_t dag_nodes, dag_edges, dag_levels;   /* task graph (0 before the first hm_lu)  */
   double dag_seconds;           /* host time of the task graph construction (Alg 11)     */
   int64_t plan_launches, plan_phases, plan_truncations;
-  int64_t scratch_bytes;        /* device scratch of the H-LU plan                       */
+  int64_t scratch_bytes;        /* device scratch of the H-LU plan (both spaces with overlap) */
   double plan_seconds;          /* host time of wave planning                            */
   double seconds;               /* device time of the last hm_build / hm_lu (CUDA events) */
   double flops[5];              /* model flops of the last hm_lu: getrf, trsm, gemm,
@@ -150,6 +150,8 @@ typedef struct {
   double f32_ms;                /* the FP32 GEMM kind (mixed precision): the same three    */
   int64_t f32_launches;
   double f32_flops;
+  int64_t plan_deferred;        /* rounded additions of the H-LU plan that overlap the next
+                                   wave on the side stream (hm_set_overlap)               */
 } hm_stats;
 
 /* Last error message of the calling thread ("" if none). */
@@ -270,6 +272,16 @@ double hm_get_gemm_work(void);
  * time). The factors are freed. Errors of hm_lu are returned (the previous setting restored). */
 int hm_autotune_gemm(hm_ctx* ctx, hm_matrix* A, const hm_lu_opts* opts, const double* candidates, int ncand,
                      double* best, double* seconds);
+/* Wave overlap (process-wide, default 1): a rounded addition (Alg 10) whose target leaf no task
+ * of the next level of the task graph reads or updates is issued on a second stream of the
+ * context and overlaps that next wave; the waves after it wait for it through CUDA events
+ * before they reuse its scratch (two scratch spaces, alternating by wave, so an H-LU with
+ * overlap needs twice the scratch memory). 0: every micro-op in wave order on one stream.
+ * Profiled factorizations (hm_ctx_set_profiling) run without overlap. Changes the plans (an
+ * H-LU plan built with the other setting is rebuilt at the next hm_lu) and the speed, not the
+ * results: the same micro-ops run on the same operands. HM_EINVAL unless on is 0 or 1. */
+int hm_set_overlap(int on);
+int hm_get_overlap(void);
 
 /* Diagnostic: y[i] = f(x[i]) for the FP64 reciprocal helpers that the serial sections of the
  * leaf LU and of the truncation core use instead of IEEE division and square root (no passage
@@ -322,17 +334,22 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
  * HM_OP_L, HM_OP_U, HM_OP_LU) on a work buffer of four n x nrhs_max blocks (x, y, two
  * temporaries); which = 6: the assembly plan of hm_build at accuracy eps (dense leaves by
  * kernel evaluation, admissible leaves by ACA + rounded truncation, into the matrix-value space
- * 3 from the permuted points, space 4, n x 3 row-major). rank_cap: 1..64, the capacity of the
+ * 3 from the permuted points, space 4, n x 3 row-major); which = 7: the H-LU plan of which = 0
+ * with wave overlap (hm_set_overlap): deferred rounded additions are side launches, and the
+ * odd waves address the second scratch spaces (doubles 5, ints 4). rank_cap: 1..64, the capacity of the
  * low-rank leaves. threads: host threads of the H-LU planner (0: the hm_set_host_threads
  * setting; the plan does not depend on it). Replaces an earlier plan of S. HM_EINVAL on bad arguments or an
  * accumulator task graph, HM_EINTERNAL if the planner fails. */
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads);
 
 enum {
-  HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz, first} int32 records, in execution
-                            order; kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack, 5 core,
-                            6 eval, 7 aca, 8 tensor-core gemm, 9 FP32 gemm (mixed precision); first = 1
-                            starts a phase (the launches of a phase are independent)          */
+  HM_PLAN_LAUNCHES = 0,  /* {kind, begin, count, gy, gz, first, wave, side} int32 records, in
+                            execution order; kind: 0 getrf, 1 trsm, 2 gemm, 3 copy, 4 stack,
+                            5 core, 6 eval, 7 aca, 8 tensor-core gemm, 9 FP32 gemm (mixed
+                            precision); first = 1 starts a phase (the launches of a phase are
+                            independent); wave: the task-graph level of an H-LU launch (-1 in
+                            the other plans); side = 1: a deferred rounded addition, which may run
+                            at any time after the wave's other launches and before wave + 2 */
   HM_PLAN_GETRF = 1,     /* the micro-op descriptors of the batched kernels, laid out as the */
   HM_PLAN_TRSM = 2,      /* GetrfOp, TrsmOp, GemmOp, CopyOp, TruncOp and StackEntry structs  */
   HM_PLAN_GEMM = 3,      /* of the library's csrc/ops.h; one TRUNC record serves a stack and */

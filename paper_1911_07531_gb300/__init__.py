@@ -25,6 +25,7 @@ __all__ = [
     "HMError", "load_library", "build_library", "HMContext", "HMatrix", "HFactor",
     "hm_ctx_create", "hm_build", "hm_lu", "hm_lu_batch", "hm_solve", "hm_matvec", "hm_truncate", "hm_truncate_noalloc",
     "hm_selftest_reciprocals", "hm_set_gemm_work", "hm_get_gemm_work", "hm_autotune_gemm",
+    "hm_set_overlap", "hm_get_overlap",
     "hm_structure_build", "hm_structure_build_accumulator", "hm_structure_build_sparsified",
     "hm_structure_plan_lu_batch", "hm_set_host_threads",
     "header_functions",
@@ -78,7 +79,8 @@ class Stats(ctypes.Structure):
                 ("kind_flops", ctypes.c_double * 8), ("launches", ctypes.c_int64),
                 ("row_interchanges", ctypes.c_int64), ("precision", ctypes.c_int64), ("tc_ms", ctypes.c_double),
                 ("tc_launches", ctypes.c_int64), ("tc_flops", ctypes.c_double), ("f32_ms", ctypes.c_double),
-                ("f32_launches", ctypes.c_int64), ("f32_flops", ctypes.c_double)]
+                ("f32_launches", ctypes.c_int64), ("f32_flops", ctypes.c_double),
+                ("plan_deferred", ctypes.c_int64)]
 
     def to_dict(self):
         d = {}
@@ -143,6 +145,8 @@ def load_library():
         "hm_selftest_reciprocals": ([P, I, P, P, I64], I),
         "hm_set_gemm_work": ([D], I),
         "hm_get_gemm_work": ([], D),
+        "hm_set_overlap": ([I], I),
+        "hm_get_overlap": ([], I),
         "hm_autotune_gemm": ([P, P, ctypes.POINTER(LuOpts), P, I, ctypes.POINTER(D), P], I),
         "hm_matrix_layout": ([P, P, P, P, P, P, P], I),
         "hm_matrix_copy_values": ([P, P, P, I], I),
@@ -434,6 +438,15 @@ def hm_get_gemm_work():
     return load_library().hm_get_gemm_work()
 
 
+def hm_set_overlap(on):
+    """Wave overlap of deferred rounded additions on a side stream (process-wide, 0 or 1)."""
+    _check(load_library().hm_set_overlap(int(on)))
+
+
+def hm_get_overlap():
+    return load_library().hm_get_overlap()
+
+
 def hm_autotune_gemm(ctx, A, candidates=(4096.0, 8192.0, 16384.0, 32768.0, 65536.0), eps=0.0, precision=0):
     """Time hm_lu of A at every candidate GEMM split target, keep the fastest set; returns
     (best, {candidate: seconds})."""
@@ -467,7 +480,8 @@ def _dt(fields):
 _U8, _I8, _I4, _F8 = "u8", "i8", "i4", "f8"
 # record layouts of the plan tables (the micro-op descriptors of csrc/ops.h)
 PLAN_DTYPES = {
-    "launches": _dt([("kind", _I4), ("begin", _I4), ("count", _I4), ("gy", _I4), ("gz", _I4), ("first", _I4)]),
+    "launches": _dt([("kind", _I4), ("begin", _I4), ("count", _I4), ("gy", _I4), ("gz", _I4), ("first", _I4), ("wave", _I4),
+                      ("side", _I4)]),
     "getrf": _dt([("A", _U8), ("piv", _U8), ("b", _I4), ("pad", _I4)]),
     "trsm": _dt([("T", _U8), ("piv", _U8), ("X", _U8), ("x_es", _I8), ("x_vs", _I8), ("nvd", _U8), ("nv", _I4),
                  ("b", _I4), ("mode", _I4), ("pad", _I4)]),
@@ -498,13 +512,13 @@ PLAN_TABLES = ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", 
 class Structure:
     """Host-only cluster tree, block tree and H-LU task graph (no GPU needed)."""
 
-    def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1, threads=0):
+    def plan(self, which=0, eps=1e-6, rank_cap=64, nrhs_max=1, threads=0, names=PLAN_TABLES):
         """Host plan (which 0: H-LU at eps, 1: solve for nrhs_max right-hand sides, 2..5: matvec,
-        6: assembly) as a dict of numpy record arrays, one per table of ``PLAN_TABLES``; threads:
-        host threads of the H-LU planner (0: all)."""
+        6: assembly, 7: H-LU with wave overlap) as a dict of numpy record arrays, one per table of
+        ``PLAN_TABLES`` named in `names`; threads: host threads of the H-LU planner (0: all)."""
         _check(load_library().hm_structure_plan(self.handle, int(which), float(eps), int(rank_cap), int(nrhs_max),
                                                 int(threads)))
-        return self.plan_tables()
+        return self.plan_tables(names)
 
     def plan_tables(self, names=PLAN_TABLES):
         """The tables (by name, see ``PLAN_TABLES``) of the structure's last plan."""

@@ -24,6 +24,8 @@ using namespace hm;
 namespace {
 
 thread_local std::string g_err;
+// rounded additions not touched by the next wave overlap it on a side stream (hm_set_overlap)
+std::atomic<int> g_overlap{1};
 // host threads of task-graph construction and planning (0: all hardware threads)
 std::atomic<int> g_host_threads{0};
 
@@ -46,6 +48,18 @@ struct hm_ctx {
   hm_free_fn ff = nullptr;
   void* user = nullptr;
   bool profiling = false;
+  // side stream of the deferred rounded additions and its events (created on first use)
+  bool side_ready = false;
+  cudaStream_t side = nullptr;
+  cudaEvent_t main_done[2] = {nullptr, nullptr}, side_done[2] = {nullptr, nullptr};
+  ~hm_ctx() {
+    if (!side_ready) return;
+    cudaStreamDestroy(side);
+    for (int q = 0; q < 2; ++q) {
+      cudaEventDestroy(main_done[q]);
+      cudaEventDestroy(side_done[q]);
+    }
+  }
 };
 
 namespace {
@@ -83,6 +97,7 @@ struct DevPlan {
   double eps = -1.0;
   int precision = -1;
   double gemm_work = -1.0;   // GEMM split target the plan was built with
+  int overlap = -1;          // deferred rounded additions on a side stream (plan built with)
   double plan_seconds = 0.0;
   // replay state of solve / matvec plans: persistent scratch and the captured CUDA graph
   Buf sd, si, cnt;
@@ -157,9 +172,64 @@ struct Profile {
   int64_t launches[NKIND] = {0};
 };
 
+bool ensure_side(hm_ctx* c) {
+  if (c->side_ready) return true;
+  bool ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+  for (int q = 0; q < 2 && ok; ++q)
+    ok = cudaEventCreateWithFlags(&c->main_done[q], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->side_done[q], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return false;
+  }
+  c->side_ready = true;
+  return true;
+}
+
+// A plan with side launches (deferred rounded additions): wave w's side launches run on the side
+// stream after an event that marks the end of w's other launches, and overlap wave w + 1 (which
+// does not touch their targets, and works in the other scratch space); wave w + 2 waits for them
+// before it reuses their scratch. Without profiling only; a profiled run is sequential.
+int run_plan_overlapped(hm_ctx* c, DevPlan& dp, const Bases& B, double h, cudaStream_t stream) {
+  const std::vector<Launch>& Ls = dp.host.launches;
+  bool pending[2] = {false, false};
+  int cur = -1;
+  for (size_t i = 0; i < Ls.size(); ++i) {
+    const Launch& L = Ls[i];
+    const int par = L.wave & 1;
+    if (!L.side && L.wave != cur) {
+      cur = L.wave;
+      if (pending[par]) {   // wave - 2's side launches used this scratch space
+        CU(cudaStreamWaitEvent(stream, c->side_done[par], 0));
+        pending[par] = false;
+      }
+    }
+    cudaStream_t st = stream;
+    if (L.side) {
+      if (i == 0 || !Ls[i - 1].side || Ls[i - 1].wave != L.wave) {
+        CU(cudaEventRecord(c->main_done[par], stream));
+        CU(cudaStreamWaitEvent(c->side, c->main_done[par], 0));
+      }
+      st = c->side;
+    }
+    const int buf = L.kind == K_CORE ? K_STACK : ((L.kind == K_GEMM_TC || L.kind == K_GEMM32) ? K_GEMM : L.kind);
+    const void* ops = (const char*)dp.ops[buf].p + (size_t)L.begin * op_size(L.kind);
+    cudaError_t e = launch_kind(L.kind, ops, L.count, (const StackEntry*)dp.entries.p, B, h, st, L.gy, L.gz);
+    if (e != cudaSuccess) return fail(HM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (L.side && (i + 1 == Ls.size() || !Ls[i + 1].side || Ls[i + 1].wave != L.wave)) {
+      CU(cudaEventRecord(c->side_done[par], c->side));
+      pending[par] = true;
+    }
+  }
+  for (int q = 0; q < 2; ++q)
+    if (pending[q]) CU(cudaStreamWaitEvent(stream, c->side_done[q], 0));
+  return HM_OK;
+}
+
 int run_plan(hm_ctx* c, DevPlan& dp, const Bases& B, double h, Profile* prof, cudaStream_t stream_override = nullptr,
              bool use_override = false) {
   const cudaStream_t stream = use_override ? stream_override : c->stream;
+  if (!prof && dp.host.deferred_truncations > 0 && ensure_side(c)) return run_plan_overlapped(c, dp, B, h, stream);
   std::vector<cudaEvent_t> ev;
   std::vector<int> evkind;
   // with the launch log on, the kind's FLOP counter is copied after every launch (pinned host
@@ -301,7 +371,9 @@ void fill_matrix_stats(const hm_matrix* A, hm_stats* s) {
   s->plan_launches = (int64_t)A->lu_plan.host.launches.size();
   s->plan_phases = A->lu_plan.host.nphases;
   s->plan_truncations = A->lu_plan.host.ntrunc;
-  s->scratch_bytes = A->lu_plan.host.scratch_doubles * 8 + A->lu_plan.host.scratch_ints * 4;
+  s->scratch_bytes = (A->lu_plan.host.scratch_doubles * 8 + A->lu_plan.host.scratch_ints * 4) *
+                     (A->lu_plan.host.two_scratch ? 2 : 1);
+  s->plan_deferred = A->lu_plan.host.deferred_truncations;
   s->plan_seconds = A->lu_plan.plan_seconds;
   s->seconds = A->build_seconds;
   s->aca_unconverged = A->aca_unconverged;
@@ -563,14 +635,17 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
       if (!compute_levels(A->dag)) return fail(HM_EINTERNAL, "hm_lu: task graph has a cycle");
       A->dag_built = true;
     }
-    if (A->lu_plan.eps != eps || A->lu_plan.precision != precision || A->lu_plan.gemm_work != gemm_min_work()) {
+    const int ov = g_overlap.load();
+    if (A->lu_plan.eps != eps || A->lu_plan.precision != precision || A->lu_plan.gemm_work != gemm_min_work() ||
+        A->lu_plan.overlap != ov) {
       free_plan(c, A->lu_plan);
       auto t0 = std::chrono::steady_clock::now();
-      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision);
+      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision, ov != 0);
       A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       A->lu_plan.eps = eps;
       A->lu_plan.precision = precision;
       A->lu_plan.gemm_work = gemm_min_work();
+      A->lu_plan.overlap = ov;
     }
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_lu: ") + ex.what());
@@ -581,11 +656,13 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   F->ctx = c;
   F->A = A;
   F->eps = eps;
-  Buf sd, si;
+  Buf sd, si, sd2, si2;
   Counters k;
   auto cleanup = [&](int r) {
     dfree(c, sd);
     dfree(c, si);
+    dfree(c, sd2);
+    dfree(c, si2);
     dfree(c, k.b);
     dfree(c, F->vals);
     dfree(c, F->ranks);
@@ -596,7 +673,9 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   if (!dalloc(c, F->vals, A->lay.nvalues * 8) || !dalloc(c, F->ranks, std::max(1, A->lay.nranks) * 4) ||
       !dalloc(c, F->piv, std::max<int64_t>(1, A->lay.npiv) * 4) ||
       !dalloc(c, sd, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
-      !dalloc(c, si, std::max<int64_t>(1, P.scratch_ints) * 4))
+      !dalloc(c, si, std::max<int64_t>(1, P.scratch_ints) * 4) ||
+      (P.two_scratch && (!dalloc(c, sd2, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
+                         !dalloc(c, si2, std::max<int64_t>(1, P.scratch_ints) * 4))))
     return cleanup(fail(HM_ENOMEM, "hm_lu: allocator returned NULL"));
   if ((rc = counters_init(c, k))) return cleanup(rc);
   cudaStream_t s = c->stream;
@@ -614,11 +693,13 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   Bases B = make_bases();
   B.d[SP_F] = (double*)F->vals.p;
   B.d[SP_S] = (double*)sd.p;
+  B.d[SP_S2] = (double*)sd2.p;
   B.d[SP_A] = (double*)A->vals.p;
   B.d[SP_P] = (double*)A->pts.p;
   B.i[IS_RANK] = (int*)F->ranks.p;
   B.i[IS_PIV] = (int*)F->piv.p;
   B.i[IS_S] = (int*)si.p;
+  B.i[IS_S2] = (int*)si2.p;
   B.i[IS_ARANK] = (int*)A->ranks.p;
   B.flops = k.flops();
   B.status = k.status();
@@ -655,6 +736,8 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   if ((rc = read_ranks(c, F->ranks, A->lay.nranks, &F->st.max_rank, &F->st.sum_rank))) return cleanup(rc);
   dfree(c, sd);
   dfree(c, si);
+  dfree(c, sd2);
+  dfree(c, si2);
   dfree(c, k.b);
   hm_factor* f = F.release();
   *out = f;
@@ -842,6 +925,7 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
       F->st.plan_phases = P.nphases;
       F->st.plan_truncations = P.ntrunc;
       F->st.scratch_bytes = P.scratch_doubles * 8 + P.scratch_ints * 4;
+      F->st.plan_deferred = 0;
       for (int f = 0; f < 5; ++f) F->st.flops[f] = (double)fl[f];
       F->st.singular_pivots = st[0];
       F->st.rank_cap_hits = st[1];
@@ -1267,6 +1351,14 @@ int hm_set_gemm_work(double fmas_per_cta) {
 
 double hm_get_gemm_work(void) { return gemm_min_work(); }
 
+int hm_set_overlap(int on) {
+  if (on != 0 && on != 1) return fail(HM_EINVAL, "hm_set_overlap: on must be 0 or 1");
+  g_overlap.store(on);
+  return HM_OK;
+}
+
+int hm_get_overlap(void) { return g_overlap.load(); }
+
 int hm_autotune_gemm(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, const double* candidates, int ncand,
                      double* best, double* seconds) {
   if (!c || !A || !candidates || ncand < 1 || !best) return fail(HM_EINVAL, "hm_autotune_gemm: bad argument");
@@ -1417,17 +1509,17 @@ int hm_set_host_threads(int threads) {
 
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
-  if (which < 0 || which > 6) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..6");
+  if (which < 0 || which > 7) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..7");
   if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan: rank_cap must be in 1..64");
-  if ((which == 0 || which == 6) && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
+  if ((which == 0 || which >= 6) && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
   if (which >= 1 && which <= 5 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
   if (threads < 0) return fail(HM_EINVAL, "hm_structure_plan: threads must be >= 0");
   for (const Task& t : S->g.nodes)
     if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan: the structure holds an accumulator task graph");
   try {
     build_layout(S->ct, S->bt, rank_cap, S->lay);
-    if (which == 0)
-      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads ? threads : g_host_threads.load());
+    if (which == 0 || which == 7)
+      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads ? threads : g_host_threads.load(), 0, which == 7);
     else if (which == 1)
       plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
     else if (which <= 5)

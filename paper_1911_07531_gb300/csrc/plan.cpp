@@ -206,6 +206,11 @@ struct Ctx {
   // mixed precision (0: FP64; 1: factor and rebuild products in FP32 (GF_F32); 2: those with at
   // least TC_MIN_ROWS rows on the tensor cores (GF_TF32), the others in FP32)
   int mixed = 0;
+  // scratch spaces of the current wave (the odd waves of a plan with deferred rounded additions
+  // use the second pair), the wave's level, and the first phase of its side launches
+  int ss = SP_S, sis = IS_S;
+  int level = -1;
+  int side_from = 1 << 30;
   // pieces reaching low-rank leaves in the current wave, by leaf index
   std::map<int, int> target_index;
   std::vector<TargetEntries> targets;
@@ -225,7 +230,7 @@ struct Ctx {
   uint64_t dref(int64_t off) const { return mkref(sp.d, off + base_d); }
   uint64_t rref(const LeafStore& L) const { return mkref(sp.r, L.rank_idx + base_r); }
   uint64_t pref(const LeafStore& L) const { return mkref(IS_PIV, L.piv_off + base_p); }
-  uint64_t sref(int64_t off) const { return mkref(SP_S, off); }
+  uint64_t sref(int64_t off) const { return mkref(ss, off); }
 
   // ---------------------------------------------------------------- micro-op emitters
   // dhint: expected value of the dynamic sizes (a rank or a stacked rank), for the grid split
@@ -617,6 +622,17 @@ struct Ctx {
     apply_pieces(Cn, pieces);
   }
 
+  // the targets whose rounded addition can wait for the side stream (defer(leaf) true) are
+  // moved out of `targets` into `out`
+  template <class F>
+  void take_deferred(F defer, std::vector<TargetEntries>& out) {
+    std::vector<TargetEntries> keep;
+    for (TargetEntries& T : targets) (defer(T.leaf) ? out : keep).push_back(std::move(T));
+    targets.swap(keep);
+    target_index.clear();
+    for (size_t q = 0; q < targets.size(); ++q) target_index[targets[q].leaf] = (int)q;
+  }
+
   // rounded additions of all pieces that reached low-rank leaves in this wave. A target whose
   // pieces exceed KMAX_STACK columns is updated in rounds (chunk r+1 after chunk r). The
   // truncations of one round run in batches whose scratch fits `budget`; every batch reuses
@@ -686,7 +702,7 @@ struct Ctx {
         op.Tw = sref(w.alloc_d((int64_t)Kc * L.cap));
         op.Tz = sref(w.alloc_d((int64_t)Kc * L.cap));
         op.work = sref(w.alloc_d(2 * (int64_t)Kc * Kc));
-        op.Kd = mkref(IS_S, w.alloc_i(1));
+        op.Kd = mkref(sis, w.alloc_i(1));
         op.eps = eps;
         peak = std::max(peak, w.sd);
         std::vector<StackEntry> es;
@@ -729,6 +745,8 @@ struct Ctx {
         if (count > 0) {
           Launch L{kind, begin, count};
           L.first = first ? 1 : 0;
+          L.wave = level;
+          L.side = ph >= side_from ? 1 : 0;
           first = false;
           plan.launches.push_back(L);
         }
@@ -804,6 +822,7 @@ struct Ctx {
       plan.trunc.insert(plan.trunc.end(), w.core[ph].begin(), w.core[ph].end());
     }
     plan.nphases += w.nph;
+    side_from = 1 << 30;
     plan.scratch_doubles = std::max(plan.scratch_doubles, w.sd);
     plan.scratch_ints = std::max(plan.scratch_ints, w.si);
     plan.nwaves++;
@@ -941,6 +960,7 @@ void concat_plans(std::vector<Plan>& parts, Plan& plan, int threads) {
     plan.nphases += q.nphases;
     plan.ntasks += q.ntasks;
     plan.ntrunc += q.ntrunc;
+    plan.deferred_truncations += q.deferred_truncations;
   }
 }
 
@@ -995,24 +1015,82 @@ void plan_wave_ranges(int nlev, const std::vector<size_t>& tasks_per_wave, int t
 }
 }  // namespace
 
+// For every leaf block, the sorted levels of the tasks that touch it: the block a triangular
+// solve or a leaf LU works on, and the two operands and the target of a product.
+std::vector<std::vector<int>> touch_levels(const BlockTree& bt, const Layout& lay, const TaskGraph& g) {
+  std::vector<std::vector<int>> out(lay.leaf.size());
+  std::vector<int> leaves;
+  auto mark = [&](int r, int c, int lv) {
+    const int id = bt.find(r, c);
+    if (id < 0) return;
+    leaves.clear();
+    collect_leaves(bt, id, leaves);
+    for (int lid : leaves) out[bt.nodes[lid].leaf].push_back(lv);
+  };
+  for (size_t i = 0; i < g.nodes.size(); ++i) {
+    const Task& t = g.nodes[i];
+    const int lv = g.level[i];
+    switch (t.type) {
+      case T_LU: mark(t.a, t.a, lv); break;
+      case T_TRSL: mark(t.a, t.b, lv); break;
+      case T_TRSU: mark(t.b, t.a, lv); break;
+      case T_SHIFT:
+      case T_APPLY: mark(t.a, t.b, lv); break;
+      default:
+        mark(t.a, t.b, lv);
+        mark(t.b, t.c, lv);
+        mark(t.a, t.c, lv);
+        break;
+    }
+  }
+  for (auto& v : out) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  return out;
+}
+
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
-             Plan& plan, int threads, int precision) {
+             Plan& plan, int threads, int precision, bool defer) {
   plan = Plan();
   const auto byl = by_level(g);
   std::vector<size_t> per(g.nlevels);
   for (int lv = 0; lv < g.nlevels; ++lv) per[lv] = byl[lv].size();
+  std::vector<std::vector<int>> touched;
+  if (defer) touched = touch_levels(bt, lay, g);
   plan_wave_ranges(
       g.nlevels, per, threads,
       [&](Plan& part, int lv0, int lv1) {
         Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, part);
         c.mixed = precision;
         for (int lv = lv0; lv < lv1; ++lv) {
+          c.level = lv;
+          if (defer) {
+            c.ss = (lv & 1) ? SP_S2 : SP_S;
+            c.sis = (lv & 1) ? IS_S2 : IS_S;
+          }
           for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
+          std::vector<TargetEntries> later;
+          if (defer)   // not touched by the next wave: its rounded addition can overlap that wave
+            c.take_deferred(
+                [&](int leaf) {
+                  const auto& v = touched[leaf];
+                  return !std::binary_search(v.begin(), v.end(), lv + 1);
+                },
+                later);
           c.emit_truncations(3, eps);
+          if (!later.empty()) {
+            c.targets.swap(later);
+            for (size_t q = 0; q < c.targets.size(); ++q) c.target_index[c.targets[q].leaf] = (int)q;
+            c.side_from = c.w.nph;
+            part.deferred_truncations += (int64_t)c.targets.size();
+            c.emit_truncations(c.side_from, eps);
+          }
           c.flush();
         }
       },
       plan);
+  plan.two_scratch = defer;
 }
 
 void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads, int precision) {
@@ -1045,6 +1123,7 @@ void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, 
               for (int ti : byl[i][lv]) expand_task(*cs[i], inst[i].g->nodes[ti]);
           // every instance's rounded additions of this wave share the phases after the products
           for (auto& c : cs) c->emit_truncations(3, eps);
+          cs[0]->level = lv;
           cs[0]->flush();
         }
       },

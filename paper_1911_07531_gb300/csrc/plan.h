@@ -39,6 +39,9 @@ struct Launch {
   int kind, begin, count;
   int gy = 1, gz = 1;   // GEMM launches: CTAs per micro-op along C tiles / reduction slices
   int first = 0;        // 1: the first launch of a phase; the launches of one phase are independent
+  int wave = -1;        // H-LU plans: the wave (task-graph level) the launch belongs to
+  int side = 0;         // 1: a deferred rounded addition of `wave`, run on a side stream after the
+                        // wave's other launches and before wave + 2 (its scratch is reused there)
 };
 
 // Grid of a GEMM launch: orders the (independent) micro-ops by estimated work, largest first,
@@ -145,6 +148,8 @@ struct Plan {
   int64_t ntrunc = 0;
   int64_t scratch_products_max = 0;   // largest product / solve scratch of one wave (doubles)
   int64_t scratch_trunc_max = 0;      // largest truncation scratch of one wave (doubles)
+  bool two_scratch = false;           // odd waves use SP_S2 / IS_S2 (deferred rounded additions)
+  int64_t deferred_truncations = 0;   // rounded additions on the side stream
 };
 
 // Memory spaces the planner addresses (factor vs. matrix storage).
@@ -159,8 +164,11 @@ struct Spaces {
 // precision 0: all FP64. 1 (mixed): the products of Alg 1 and the rebuild products of the rounded
 // additions are K_GEMM32 micro-ops (FP32 FMAs); 2 (mixed, tensor cores): those with at least 128
 // static rows are K_GEMM_TC micro-ops (split TF32 on tcgen05, FP32 accumulation), the rest K_GEMM32.
+// defer: rounded additions whose target leaf is not touched by the next wave (no task of the
+// next level reads it, no product of the next level updates it) become side launches of their
+// wave (Launch::side), overlapping the next wave; odd waves then use the second scratch space.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
-             double eps, Plan& plan, int threads = 0, int precision = 0);
+             double eps, Plan& plan, int threads = 0, int precision = 0, bool defer = false);
 // Independent H-LU instances in one plan: wave w of every instance is expanded into the same
 // phases, so that one launch per kind and phase serves all of them (their task graphs have no
 // edges between each other). Instance i addresses its values, ranks and pivots at the given

@@ -5,6 +5,9 @@
       and runs one hm_lu with HM_PREC_* = PRECISION; prints the device seconds.
   python -m paper_1911_07531_gb300.run_case xmv N
       the cube matrix at eps 1e-6 and two exact-kernel matvecs (HM_OP_EXACT) of one vector.
+  python -m paper_1911_07531_gb300.run_case overlap WORKLOAD EPS REPEATS
+      hm_lu of a workload with the wave overlap off and on (hm_set_overlap), alternating, after
+      a warm-up of each; prints the device seconds of every factorization as JSON lines.
   python -m paper_1911_07531_gb300.run_case kinds WORKLOAD EPS
       one hm_lu per precision (FP64, MIXED, MIXED_TC) of a workload of `hm_workloads.WORKLOADS`
       after a warm-up, then a profiled one (CUDA events around every launch); prints the device
@@ -79,12 +82,36 @@ def _kinds(workload, eps):
         F.free()
 
 
+def _overlap(workload, eps, repeats):
+    import hm_workloads as W
+
+    from . import HMContext, build_library, hm_build, hm_lu, hm_set_overlap
+    build_library()
+    w = W.WORKLOADS[workload]
+    ctx = HMContext(0)
+    A = hm_build(ctx, W.points_for(w["geometry"], w["n"], w["seed"]), w["leaf"], w["eta"], w["eps"], w["rank_cap"])
+    for on in (0, 1):
+        hm_set_overlap(on)
+        hm_lu(ctx, A, eps=eps).free()
+    for r in range(repeats):
+        for on in (0, 1):
+            hm_set_overlap(on)
+            F = hm_lu(ctx, A, eps=eps)
+            st = F.stats()
+            F.free()
+            print(json.dumps({"overlap": on, "repeat": r, "seconds": st["seconds"],
+                              "plan_truncations": st["plan_truncations"],
+                              "plan_deferred": st["plan_deferred"]}), flush=True)
+
+
 def main(argv=None):
     a = sys.argv[1:] if argv is None else argv
     if a and a[0] == "lu" and len(a) == 5:
         _lu(a[1], int(a[2]), float(a[3]), int(a[4]))
     elif a and a[0] == "xmv" and len(a) == 2:
         _xmv(int(a[1]))
+    elif a and a[0] == "overlap" and len(a) == 4:
+        _overlap(a[1], float(a[2]), int(a[3]))
     elif a and a[0] == "kinds" and len(a) == 3:
         _kinds(a[1], float(a[2]))
     else:

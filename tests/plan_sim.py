@@ -34,19 +34,21 @@ from numpy.lib.stride_tricks import as_strided
 MASK = (1 << 60) - 1
 K_GETRF, K_TRSM, K_GEMM, K_COPY, K_STACK, K_CORE, K_EVAL, K_ACA = range(8)
 GF_ATOMIC, GF_OVERWRITE, GF_A_UPPER, GF_A_UNITLOWER, GF_SYM_UPPER = 1, 2, 4, 8, 16
-SP_F, SP_S, SP_X, SP_A, SP_P = 0, 1, 2, 3, 4
-IS_RANK, IS_PIV, IS_S, IS_ARANK = 0, 1, 2, 3
+SP_F, SP_S, SP_X, SP_A, SP_P, SP_S2 = 0, 1, 2, 3, 4, 5
+IS_RANK, IS_PIV, IS_S, IS_ARANK, IS_S2 = 0, 1, 2, 3, 4
 KMAX_ENTRIES = 256
 
 
 class PlanSim:
     def __init__(self, sizes, nrhs_space=0):
         self.d = {SP_F: np.zeros(int(sizes["nvalues"])), SP_S: np.zeros(int(sizes["scratch_doubles"])),
-                  SP_X: np.zeros(int(nrhs_space))}
+                  SP_X: np.zeros(int(nrhs_space)), SP_S2: np.zeros(int(sizes["scratch_doubles"]))}
         self.i = {IS_RANK: np.zeros(int(sizes["nranks"]), np.int64), IS_PIV: np.zeros(int(sizes["npiv"]), np.int64),
-                  IS_S: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64)}
+                  IS_S: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64),
+                  IS_S2: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64)}
         self.cap_hits = 0
         self.singular = 0
+        self.trace = None   # a list: every access is recorded as (table, space, element offsets)
         self.h = None   # kernel regularisation (assembly plans)
 
     # -- addressing ------------------------------------------------------------------------------
@@ -63,16 +65,25 @@ class PlanSim:
         if m and n:
             last = off + (m - 1) * rs + (n - 1) * cs
             assert 0 <= off and last < arr.size, f"access [{off}, {last}] outside a space of {arr.size}"
+            if self.trace is not None:
+                self.trace.append(("d", (int(ref) >> 60) - 1,
+                                   (off + rs * np.arange(m)[:, None] + cs * np.arange(n)[None, :]).ravel()))
         return as_strided(arr[off:], shape=(m, n), strides=(rs * 8, cs * 8))
+
+    def _itrace(self, ref, off):
+        if self.trace is not None:
+            self.trace.append(("i", (int(ref) >> 60) - 1, np.array([off])))
 
     def ival(self, ref):
         arr, off = self._space(ref, self.i)
         assert off < arr.size
+        self._itrace(ref, off)
         return int(arr[off])
 
     def iset(self, ref, v):
         arr, off = self._space(ref, self.i)
         assert off < arr.size
+        self._itrace(ref, off)
         arr[off] = v
 
     def dim(self, s, d):
@@ -240,16 +251,61 @@ class PlanSim:
         self.iset(op["kd"], k)
 
     # -- plans -------------------------------------------------------------------------------------
-    def run(self, P):
+    @staticmethod
+    def latest_order(launches):
+        """The launches of an H-LU plan with side launches in the latest order the library's
+        streams allow: the side launches of wave w after every other launch of wave w + 1, just
+        before wave w + 2 starts (the sequential plan order is the earliest one)."""
+        out, held = [], {}
+        cur = None
+        for ln in launches:
+            w = int(ln["wave"])
+            if int(ln["side"]):
+                held.setdefault(w, []).append(ln)
+                continue
+            if w != cur:
+                cur = w
+                out.extend(held.pop(w - 2, []))
+            out.append(ln)
+        for w in sorted(held):
+            out.extend(held[w])
+        return out
+
+    def run_launch(self, P, ln):
         tables = {K_GETRF: P["getrf"], K_TRSM: P["trsm"], K_GEMM: P["gemm"], K_COPY: P["copy"],
                   K_STACK: P["trunc"], K_CORE: P["trunc"], K_EVAL: P.get("eval"), K_ACA: P.get("aca")}
         fns = {K_GETRF: self.getrf, K_TRSM: self.trsm, K_GEMM: self.gemm, K_COPY: self.copy,
                K_STACK: lambda op: self.stack(op, P["entries"]), K_CORE: self.core, K_EVAL: self.eval,
                K_ACA: self.aca}
-        for ln in P["launches"]:
-            kind, b, c = int(ln["kind"]), int(ln["begin"]), int(ln["count"])
-            ops = tables[kind]
-            assert b + c <= len(ops)
-            for op in ops[b:b + c]:
-                fns[kind](op)
+        kind, b, c = int(ln["kind"]), int(ln["begin"]), int(ln["count"])
+        ops = tables[kind]
+        assert b + c <= len(ops)
+        for op in ops[b:b + c]:
+            fns[kind](op)
+
+    def footprint(self, P, ln):
+        """Runs one launch and returns what it accessed and what it changed: two dicts
+        {(table, space): sorted element offsets}, table "d" (doubles) or "i" (integers)."""
+        snap = {("d", k): v.copy() for k, v in self.d.items()}
+        snap.update({("i", k): v.copy() for k, v in self.i.items()})
+        self.trace = []
+        try:
+            self.run_launch(P, ln)
+        finally:
+            tr, self.trace = self.trace, None
+        acc = {}
+        for t, sp, offs in tr:
+            acc.setdefault((t, sp), []).append(offs)
+        acc = {k: np.unique(np.concatenate(v)) for k, v in acc.items()}
+        wr = {}
+        for (t, sp), before in snap.items():
+            now = (self.d if t == "d" else self.i)[sp]
+            ch = np.flatnonzero(before != now)
+            if ch.size:
+                wr[(t, sp)] = ch
+        return acc, wr
+
+    def run(self, P, order=None):
+        for ln in (P["launches"] if order is None else order):
+            self.run_launch(P, ln)
         return self

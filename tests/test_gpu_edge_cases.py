@@ -10,7 +10,9 @@
 * numerically singular leaves (duplicate points) report HM_ESINGULAR with the factor returned;
 * an allocator that fails at any one of its calls gives HM_ENOMEM, leaks nothing, and the
   next calls succeed;
-* the FP64 reciprocal helpers of the serial sections against IEEE division / square root.
+* the FP64 reciprocal helpers of the serial sections against IEEE division / square root;
+* batching across instances, the GEMM split autotuner, and the wave overlap of deferred
+  rounded additions against the sequential schedule.
 """
 import numpy as np
 import pytest
@@ -368,3 +370,37 @@ def test_autotune_gemm_split(ctx, hm):
             F.free()
     finally:
         hm.hm_set_gemm_work(before)
+
+
+# ------------------------------------------------------------------ wave overlap
+def test_wave_overlap_matches_sequential(ctx, hm):
+    """Rounded additions deferred to the side stream (hm_set_overlap(1)) give the factors of
+    the sequential schedule (hm_set_overlap(0)) up to the order of atomic accumulations, and
+    a profiled factorization (sequential by construction) agrees too: all within 10 eps of the
+    exact kernel and within eps of each other."""
+    n, eps = 8192, 1e-6
+    p = W.cube_surface(n, 31)
+    A = hm.hm_build(ctx, p, 64, 2.0, eps, 64)
+    X = np.random.default_rng(7).standard_normal((n, 4))
+    Xd = dev(X)
+    Ax = host(hm.hm_matvec(ctx, A, hm.HM_OP_EXACT, Xd))
+    before = hm.hm_get_overlap()
+    out = {}
+    try:
+        for on, prof in ((1, False), (0, False), (1, True)):
+            hm.hm_set_overlap(on)
+            assert hm.hm_get_overlap() == on
+            ctx.set_profiling(prof)
+            F = hm.hm_lu(ctx, A)
+            ctx.set_profiling(False)
+            out[(on, prof)] = host(hm.hm_matvec(ctx, A, hm.HM_OP_LU, Xd, F=F))
+            assert fro_ratio(out[(on, prof)] - Ax, Ax) <= 10 * eps
+            F.free()
+        with pytest.raises(hm.HMError, match="HM_EINVAL"):
+            hm.hm_set_overlap(2)
+    finally:
+        ctx.set_profiling(False)
+        hm.hm_set_overlap(before)
+    ref = out[(0, False)]   # rank decisions near eps may differ with the accumulation order
+    assert fro_ratio(out[(1, False)] - ref, Ax) <= eps
+    assert fro_ratio(out[(1, True)] - ref, Ax) <= eps
