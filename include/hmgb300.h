@@ -103,6 +103,13 @@ typedef struct {
                         matrix's eps; else in [HM_EPS_MIN, 1)); the rank cap is the
                         matrix's                                                          */
   int precision;     /* HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC                   */
+  int accumulate;    /* 0: the H-LU of Alg 2 (every update rounded into its leaf in the wave
+                        that forms it). 1: the accumulator H-LU of §2.3 (Alg 4-8): the update
+                        pieces of a low-rank leaf are collected (add_upd; shift_upd restricts a
+                        block's pieces to its sons) and added in one rounded addition before
+                        the leaf is used (apply_upd), in the wave of its last update; pieces
+                        that outlive their wave are held in a device arena (stats arena_bytes).
+                        Not available in hm_lu_batch.                                     */
 } hm_lu_opts;
 
 typedef struct {
@@ -152,6 +159,9 @@ typedef struct {
   double f32_flops;
   int64_t plan_deferred;        /* rounded additions of the H-LU plan that overlap the next
                                    wave on the side stream (hm_set_overlap)               */
+  int64_t accumulate;           /* 1: the last hm_lu was the accumulator H-LU             */
+  int64_t arena_bytes;          /*   its accumulator arena (held update pieces)           */
+  int64_t accumulated_pieces;   /*   update pieces held past the wave that formed them    */
 } hm_stats;
 
 /* Last error message of the calling thread ("" if none). */
@@ -336,7 +346,9 @@ int hm_structure_info_get(const hm_structure* S, hm_structure_info* out);
  * kernel evaluation, admissible leaves by ACA + rounded truncation, into the matrix-value space
  * 3 from the permuted points, space 4, n x 3 row-major); which = 7: the H-LU plan of which = 0
  * with wave overlap (hm_set_overlap): deferred rounded additions are side launches, and the
- * odd waves address the second scratch spaces (doubles 5, ints 4). rank_cap: 1..64, the capacity of the
+ * odd waves address the second scratch spaces (doubles 5, ints 4); which = 8: the accumulator
+ * H-LU plan (hm_lu_opts.accumulate = 1; held pieces in the arena, doubles space 6), which = 9:
+ * the same with wave overlap. rank_cap: 1..64, the capacity of the
  * low-rank leaves. threads: host threads of the H-LU planner (0: the hm_set_host_threads
  * setting; the plan does not depend on it). Replaces an earlier plan of S. HM_EINVAL on bad arguments or an
  * accumulator task graph, HM_EINTERNAL if the planner fails. */
@@ -360,8 +372,9 @@ enum {
   HM_PLAN_LEAVES = 7,    /* per block-tree leaf, 10 int64: row cluster, col cluster, m, n,
                             low-rank (0/1), rank capacity, value offset (dense D or U, ld m),
                             V offset (ld n), rank index, pivot offset (-1: none)             */
-  HM_PLAN_SIZES = 8,     /* one record of 8 int64: scratch doubles, scratch ints, value
-                            doubles, ranks, pivots, rounded additions, waves, phases          */
+  HM_PLAN_SIZES = 8,     /* one record of 9 int64: scratch doubles, scratch ints, value
+                            doubles, ranks, pivots, rounded additions, waves, phases, arena
+                            doubles (accumulator H-LU plans, else 0)                         */
   HM_PLAN_INSTANCES = 9, /* per instance, 5 int64: first leaf record, leaf records, value,
                             rank and pivot offsets (one instance unless batched)              */
   HM_PLAN_EVAL = 10,     /* EvalOp and AcaOp records of the assembly plan (kinds 6 and 7)     */

@@ -52,7 +52,7 @@ class BuildOpts(ctypes.Structure):
 
 
 class LuOpts(ctypes.Structure):
-    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int)]
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("accumulate", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -80,7 +80,8 @@ class Stats(ctypes.Structure):
                 ("row_interchanges", ctypes.c_int64), ("precision", ctypes.c_int64), ("tc_ms", ctypes.c_double),
                 ("tc_launches", ctypes.c_int64), ("tc_flops", ctypes.c_double), ("f32_ms", ctypes.c_double),
                 ("f32_launches", ctypes.c_int64), ("f32_flops", ctypes.c_double),
-                ("plan_deferred", ctypes.c_int64)]
+                ("plan_deferred", ctypes.c_int64), ("accumulate", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("accumulated_pieces", ctypes.c_int64)]
 
     def to_dict(self):
         d = {}
@@ -324,9 +325,10 @@ def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h
     return HMatrix(ctx, h, p.shape[0])
 
 
-def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0):
-    """H-LU of A (precision: HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC)."""
-    o = LuOpts(float(eps), int(precision))
+def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0, accumulate=False):
+    """H-LU of A (precision: HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC; accumulate: the
+    accumulator H-LU of Alg 4-8)."""
+    o = LuOpts(float(eps), int(precision), int(bool(accumulate)))
     h = ctypes.c_void_p()
     rc = load_library().hm_lu(ctx.handle, A.handle, ctypes.byref(o), ctypes.byref(h))
     F = HFactor(ctx, h, A) if h.value else None
@@ -337,7 +339,7 @@ def hm_lu(ctx, A, eps=0.0, allow_singular=False, precision=0):
     return F
 
 
-def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False, precision=0):
+def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False, precision=0, accumulate=False):
     """H-LU of several independent matrices whose waves share kernel launches; one factor each.
 
     The library sizes its groups of instances by the free device memory; blocks that PyTorch's
@@ -346,7 +348,7 @@ def hm_lu_batch(ctx, matrices, eps=0.0, allow_singular=False, precision=0):
     n = len(matrices)
     hs = (ctypes.c_void_p * n)(*[A.handle for A in matrices])
     outs = (ctypes.c_void_p * n)()
-    o = LuOpts(float(eps), int(precision))
+    o = LuOpts(float(eps), int(precision), int(bool(accumulate)))
     rc = load_library().hm_lu_batch(ctx.handle, hs, n, ctypes.byref(o), outs)
     Fs = [HFactor(ctx, ctypes.c_void_p(outs[i]), A) if outs[i] else None for i, A in enumerate(matrices)]
     if rc != 0 and not (rc == -4 and allow_singular and all(F is not None for F in Fs)):
@@ -499,7 +501,7 @@ PLAN_DTYPES = {
     "leaves": _dt([(f, _I8) for f in ("row", "col", "m", "n", "lr", "cap", "off", "voff", "rank_idx",
                                       "piv_off")]),
     "sizes": _dt([(f, _I8) for f in ("scratch_doubles", "scratch_ints", "nvalues", "nranks", "npiv", "ntrunc",
-                                     "nwaves", "nphases")]),
+                                     "nwaves", "nphases", "arena_doubles")]),
     "instances": _dt([(f, _I8) for f in ("first_leaf", "nleaves", "base_d", "base_r", "base_p")]),
     "eval": _dt([("D", _U8), ("r0", _I4), ("c0", _I4), ("m", _I4), ("n", _I4)]),
     "aca": _dt([("r0", _I4), ("c0", _I4), ("m", _I4), ("n", _I4), ("U", _U8), ("V", _U8), ("used", _U8),

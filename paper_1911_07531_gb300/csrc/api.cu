@@ -98,6 +98,7 @@ struct DevPlan {
   int precision = -1;
   double gemm_work = -1.0;   // GEMM split target the plan was built with
   int overlap = -1;          // deferred rounded additions on a side stream (plan built with)
+  int accumulate = -1;       // accumulator H-LU (plan built with)
   double plan_seconds = 0.0;
   // replay state of solve / matvec plans: persistent scratch and the captured CUDA graph
   Buf sd, si, cnt;
@@ -374,6 +375,9 @@ void fill_matrix_stats(const hm_matrix* A, hm_stats* s) {
   s->scratch_bytes = (A->lu_plan.host.scratch_doubles * 8 + A->lu_plan.host.scratch_ints * 4) *
                      (A->lu_plan.host.two_scratch ? 2 : 1);
   s->plan_deferred = A->lu_plan.host.deferred_truncations;
+  s->accumulate = A->lu_plan.accumulate > 0 ? 1 : 0;
+  s->arena_bytes = A->lu_plan.host.arena_doubles * 8;
+  s->accumulated_pieces = A->lu_plan.host.accumulated_pieces;
   s->plan_seconds = A->lu_plan.plan_seconds;
   s->seconds = A->build_seconds;
   s->aca_unconverged = A->aca_unconverged;
@@ -628,6 +632,8 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   const int precision = o ? o->precision : HM_PREC_FP64;
   if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED && precision != HM_PREC_MIXED_TC)
     return fail(HM_EINVAL, "hm_lu: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");
+  const int accumulate = o ? o->accumulate : 0;
+  if (accumulate != 0 && accumulate != 1) return fail(HM_EINVAL, "hm_lu: accumulate must be 0 or 1");
   CU(cudaSetDevice(c->device));
   try {
     if (!A->dag_built) {
@@ -637,15 +643,17 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
     }
     const int ov = g_overlap.load();
     if (A->lu_plan.eps != eps || A->lu_plan.precision != precision || A->lu_plan.gemm_work != gemm_min_work() ||
-        A->lu_plan.overlap != ov) {
+        A->lu_plan.overlap != ov || A->lu_plan.accumulate != accumulate) {
       free_plan(c, A->lu_plan);
       auto t0 = std::chrono::steady_clock::now();
-      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision, ov != 0);
+      plan_lu(A->ct, A->bt, A->lay, A->dag, eps, A->lu_plan.host, g_host_threads.load(), precision, ov != 0,
+              accumulate != 0);
       A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       A->lu_plan.eps = eps;
       A->lu_plan.precision = precision;
       A->lu_plan.gemm_work = gemm_min_work();
       A->lu_plan.overlap = ov;
+      A->lu_plan.accumulate = accumulate;
     }
   } catch (const std::exception& ex) {
     return fail(HM_EINTERNAL, std::string("hm_lu: ") + ex.what());
@@ -656,13 +664,14 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   F->ctx = c;
   F->A = A;
   F->eps = eps;
-  Buf sd, si, sd2, si2;
+  Buf sd, si, sd2, si2, acc;
   Counters k;
   auto cleanup = [&](int r) {
     dfree(c, sd);
     dfree(c, si);
     dfree(c, sd2);
     dfree(c, si2);
+    dfree(c, acc);
     dfree(c, k.b);
     dfree(c, F->vals);
     dfree(c, F->ranks);
@@ -675,7 +684,8 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
       !dalloc(c, sd, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
       !dalloc(c, si, std::max<int64_t>(1, P.scratch_ints) * 4) ||
       (P.two_scratch && (!dalloc(c, sd2, std::max<int64_t>(1, P.scratch_doubles) * 8) ||
-                         !dalloc(c, si2, std::max<int64_t>(1, P.scratch_ints) * 4))))
+                         !dalloc(c, si2, std::max<int64_t>(1, P.scratch_ints) * 4))) ||
+      (P.arena_doubles > 0 && !dalloc(c, acc, P.arena_doubles * 8)))
     return cleanup(fail(HM_ENOMEM, "hm_lu: allocator returned NULL"));
   if ((rc = counters_init(c, k))) return cleanup(rc);
   cudaStream_t s = c->stream;
@@ -694,6 +704,7 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   B.d[SP_F] = (double*)F->vals.p;
   B.d[SP_S] = (double*)sd.p;
   B.d[SP_S2] = (double*)sd2.p;
+  B.d[SP_ACC] = (double*)acc.p;
   B.d[SP_A] = (double*)A->vals.p;
   B.d[SP_P] = (double*)A->pts.p;
   B.i[IS_RANK] = (int*)F->ranks.p;
@@ -738,6 +749,7 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
   dfree(c, si);
   dfree(c, sd2);
   dfree(c, si2);
+  dfree(c, acc);
   dfree(c, k.b);
   hm_factor* f = F.release();
   *out = f;
@@ -775,6 +787,7 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
   const int precision = o ? o->precision : HM_PREC_FP64;
   if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED && precision != HM_PREC_MIXED_TC)
     return fail(HM_EINVAL, "hm_lu_batch: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");
+  if (o && o->accumulate) return fail(HM_EINVAL, "hm_lu_batch: the accumulator H-LU is not batched");
   const bool given = o && o->eps > 0.0;
   const double eps = given ? o->eps : A[0]->opts.eps;
   if (!(eps >= HM_EPS_MIN) || eps >= 1.0) return fail(HM_EINVAL, "hm_lu_batch: eps must be in [HM_EPS_MIN, 1)");
@@ -926,6 +939,9 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
       F->st.plan_truncations = P.ntrunc;
       F->st.scratch_bytes = P.scratch_doubles * 8 + P.scratch_ints * 4;
       F->st.plan_deferred = 0;
+      F->st.accumulate = 0;
+      F->st.arena_bytes = 0;
+      F->st.accumulated_pieces = 0;
       for (int f = 0; f < 5; ++f) F->st.flops[f] = (double)fl[f];
       F->st.singular_pivots = st[0];
       F->st.rank_cap_hits = st[1];
@@ -1509,7 +1525,7 @@ int hm_set_host_threads(int threads) {
 
 int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int nrhs_max, int threads) {
   if (!S) return fail(HM_EINVAL, "hm_structure_plan: NULL structure");
-  if (which < 0 || which > 7) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..7");
+  if (which < 0 || which > 9) return fail(HM_EINVAL, "hm_structure_plan: which must be in 0..9");
   if (rank_cap < 1 || rank_cap > 64) return fail(HM_EINVAL, "hm_structure_plan: rank_cap must be in 1..64");
   if ((which == 0 || which >= 6) && !(eps > 0.0)) return fail(HM_EINVAL, "hm_structure_plan: eps must be > 0");
   if (which >= 1 && which <= 5 && nrhs_max < 1) return fail(HM_EINVAL, "hm_structure_plan: nrhs_max must be >= 1");
@@ -1518,8 +1534,9 @@ int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int 
     if (t.type > T_TRSU) return fail(HM_EINVAL, "hm_structure_plan: the structure holds an accumulator task graph");
   try {
     build_layout(S->ct, S->bt, rank_cap, S->lay);
-    if (which == 0 || which == 7)
-      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads ? threads : g_host_threads.load(), 0, which == 7);
+    if (which == 0 || which >= 7)
+      plan_lu(S->ct, S->bt, S->lay, S->g, eps, S->plan, threads ? threads : g_host_threads.load(), 0,
+              which == 7 || which == 9, which >= 8);
     else if (which == 1)
       plan_solve(S->ct, S->bt, S->lay, nrhs_max, S->plan);
     else if (which <= 5)
@@ -1535,7 +1552,7 @@ int hm_structure_plan(hm_structure* S, int which, double eps, int rank_cap, int 
   append_leaf_table(S->lay, 0, 0, 0, S->leaf_table);
   const Plan& P = S->plan;
   S->sizes = {P.scratch_doubles, P.scratch_ints, S->lay.nvalues, S->lay.nranks, S->lay.npiv,
-              P.ntrunc,          P.nwaves,       P.nphases};
+              P.ntrunc,          P.nwaves,       P.nphases,         P.arena_doubles};
   S->instances = {0, (int64_t)S->lay.leaf.size(), 0, 0, 0};
   return HM_OK;
 }
@@ -1576,7 +1593,7 @@ int hm_structure_plan_lu_batch(hm_structure* const* S, int count, double eps, in
   H->leaf_table.swap(table);
   H->instances.swap(insts);
   const Plan& P = H->plan;
-  H->sizes = {P.scratch_doubles, P.scratch_ints, bd, br, bp, P.ntrunc, P.nwaves, P.nphases};
+  H->sizes = {P.scratch_doubles, P.scratch_ints, bd, br, bp, P.ntrunc, P.nwaves, P.nphases, 0};
   return HM_OK;
 }
 

@@ -16,10 +16,11 @@
 
 namespace hm {
 
-enum DSpace : int { SP_F = 0, SP_S = 1, SP_X = 2, SP_A = 3, SP_P = 4, SP_S2 = 5, NDSPACE = 6 };
+enum DSpace : int { SP_F = 0, SP_S = 1, SP_X = 2, SP_A = 3, SP_P = 4, SP_S2 = 5, SP_ACC = 6, NDSPACE = 7 };
 // SP_F factor values, SP_S scratch, SP_X right-hand-side work buffer,
 // SP_A matrix values, SP_P permuted points (n x 3, row-major), SP_S2 the scratch of the odd waves
-// of an H-LU plan whose truncations overlap the next wave (same size as SP_S)
+// of an H-LU plan whose truncations overlap the next wave (same size as SP_S), SP_ACC the
+// accumulator arena of an accumulator H-LU plan (update pieces kept across waves)
 enum ISpace : int { IS_RANK = 0, IS_PIV = 1, IS_S = 2, IS_ARANK = 3, IS_S2 = 4, NISPACE = 5 };
 
 constexpr uint64_t REF_MASK = (1ull << 60) - 1;

@@ -22,8 +22,10 @@
 #include <unordered_map>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
+#include <set>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -193,6 +195,67 @@ struct Wave {
   }
 };
 
+// Accumulator arena of an accumulator H-LU plan: blocks of doubles that live from the wave that
+// allocates them to a release wave fixed at allocation (best fit among the free blocks, which
+// coalesce; the top grows when none fits).
+struct Arena {
+  std::map<int64_t, int64_t> by_off;              // free blocks: offset -> size
+  std::set<std::pair<int64_t, int64_t>> by_size;  // free blocks: (size, offset)
+  std::multimap<int, std::pair<int64_t, int64_t>> later;   // release wave -> (offset, size)
+  int64_t top = 0;
+  int64_t alloc(int64_t n, int release_wave) {
+    n = align_up(n);
+    int64_t off;
+    auto it = by_size.lower_bound({n, INT64_MIN});
+    if (it != by_size.end()) {
+      const int64_t sz = it->first;
+      off = it->second;
+      by_size.erase(it);
+      by_off.erase(off);
+      if (sz > n) {
+        by_off[off + n] = sz - n;
+        by_size.insert({sz - n, off + n});
+      }
+    } else {
+      off = top;
+      top += n;
+    }
+    later.insert({release_wave, {off, n}});
+    return off;
+  }
+  void give_back(int64_t off, int64_t n) {
+    auto nx = by_off.lower_bound(off);
+    if (nx != by_off.end() && off + n == nx->first) {   // merge with the next free block
+      n += nx->second;
+      by_size.erase({nx->second, nx->first});
+      nx = by_off.erase(nx);
+    }
+    if (nx != by_off.begin()) {   // merge with the previous one
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        by_size.erase({pv->second, pv->first});
+        off = pv->first;
+        n += pv->second;
+        by_off.erase(pv);
+      }
+    }
+    by_off[off] = n;
+    by_size.insert({n, off});
+  }
+  // the blocks whose release wave is <= wave become free
+  void release_until(int wave) {
+    while (!later.empty() && later.begin()->first <= wave) {
+      give_back(later.begin()->second.first, later.begin()->second.second);
+      later.erase(later.begin());
+    }
+  }
+};
+
+// For every leaf block, its events in the task graph sorted by level: (level, 1) where a task
+// reads it (the leaf LU, a triangular solve, an operand of a product) and (level, 0) where a
+// product updates it.
+using LeafEvents = std::vector<std::vector<std::pair<int, int>>>;
+
 struct Ctx {
   const ClusterTree& ct;
   const BlockTree& bt;
@@ -214,6 +277,12 @@ struct Ctx {
   // pieces reaching low-rank leaves in the current wave, by leaf index
   std::map<int, int> target_index;
   std::vector<TargetEntries> targets;
+  // accumulator H-LU: the leaves' events, the arena, the pieces held for each leaf until its
+  // rounded addition, and the release wave of the pieces being formed (-1: wave scratch)
+  const LeafEvents* events = nullptr;
+  Arena* arena = nullptr;
+  std::map<int, std::vector<std::pair<StackEntry, int>>> pending;
+  int piece_release = -1;
   Ctx(const ClusterTree& c, const BlockTree& b, const Layout& l, Spaces s, Plan& p)
       : ct(c), bt(b), lay(l), sp(s), plan(p), w(own) {}
   Ctx(const ClusterTree& c, const BlockTree& b, const Layout& l, Spaces s, Plan& p, Wave& shared)
@@ -231,6 +300,41 @@ struct Ctx {
   uint64_t rref(const LeafStore& L) const { return mkref(sp.r, L.rank_idx + base_r); }
   uint64_t pref(const LeafStore& L) const { return mkref(IS_PIV, L.piv_off + base_p); }
   uint64_t sref(int64_t off) const { return mkref(ss, off); }
+  // memory of an update piece: the wave's scratch, or the arena when the piece is held
+  uint64_t palloc(int64_t n) {
+    return piece_release >= 0 ? mkref(SP_ACC, arena->alloc(n, piece_release)) : sref(w.alloc_d(n));
+  }
+  // accumulator H-LU: the wave of the rounded addition of the pieces that an update at level lv
+  // brings to leaf `leaf`: the last update level before the leaf's next read
+  int flush_level(int leaf, int lv) const {
+    const auto& ev = (*events)[leaf];
+    auto it = std::upper_bound(ev.begin(), ev.end(), std::make_pair(lv, 1));
+    int f = lv;
+    for (; it != ev.end() && it->second == 0; ++it) f = it->first;
+    return f;
+  }
+  // accumulator H-LU: the targets of this wave whose rounded addition comes later hand their
+  // pieces to `pending`; the others take the pieces held for them (in arrival order) first
+  void hold_pending(int lv) {
+    std::vector<TargetEntries> keep;
+    for (TargetEntries& T : targets) {
+      if (flush_level(T.leaf, lv) > lv) {
+        auto& P = pending[T.leaf];
+        P.insert(P.end(), T.e.begin(), T.e.end());
+        plan.accumulated_pieces += (int64_t)T.e.size();
+        continue;
+      }
+      auto it = pending.find(T.leaf);
+      if (it != pending.end()) {
+        T.e.insert(T.e.begin(), it->second.begin(), it->second.end());
+        pending.erase(it);
+      }
+      keep.push_back(std::move(T));
+    }
+    targets.swap(keep);
+    target_index.clear();
+    for (size_t q = 0; q < targets.size(); ++q) target_index[targets[q].leaf] = (int)q;
+  }
 
   // ---------------------------------------------------------------- micro-op emitters
   // dhint: expected value of the dynamic sizes (a rank or a stacked rank), for the grid split
@@ -434,9 +538,9 @@ struct Ctx {
       utsolve(0, t, View{dref(M.off), M.m, 1}, Dim{M.m, 0}, M.m);
   }
 
-  int64_t identity(int k) {
-    const int64_t I = w.alloc_d((int64_t)k * k);
-    copy(0, CM_IDENTITY, 0, 0, 0, sref(I), 1, k, {k, 0}, {k, 0});
+  uint64_t identity(int k) {
+    const uint64_t I = palloc((int64_t)k * k);
+    copy(0, CM_IDENTITY, 0, 0, 0, I, 1, k, {k, 0}, {k, 0});
     return I;
   }
 
@@ -449,18 +553,18 @@ struct Ctx {
     const bool Aleaf = A.is_leaf(), Bleaf = B.is_leaf();
     if (Aleaf && leaf_of(An).lr) {
       const LeafStore& LA = leaf_of(An);
-      const int64_t Z = w.alloc_d((int64_t)mc * LA.cap);
-      copy(0, CM_ZERO, 0, 0, 0, sref(Z), 1, mc, {mc, 0}, {LA.cap, 0});
-      block_mv(0, Bn, View{dref(LA.voff), 1, mb}, View{sref(Z), 1, mc}, 1.0, true, {0, rref(LA)}, LA.cap);
-      out.push_back({View{dref(LA.off), 1, ma}, View{sref(Z), 1, mc}, {0, rref(LA)}, LA.cap, ro, ma, co, mc, -1.0});
+      const uint64_t Z = palloc((int64_t)mc * LA.cap);
+      copy(0, CM_ZERO, 0, 0, 0, Z, 1, mc, {mc, 0}, {LA.cap, 0});
+      block_mv(0, Bn, View{dref(LA.voff), 1, mb}, View{Z, 1, mc}, 1.0, true, {0, rref(LA)}, LA.cap);
+      out.push_back({View{dref(LA.off), 1, ma}, View{Z, 1, mc}, {0, rref(LA)}, LA.cap, ro, ma, co, mc, -1.0});
       return;
     }
     if (Bleaf && leaf_of(Bn).lr) {
       const LeafStore& LB = leaf_of(Bn);
-      const int64_t W = w.alloc_d((int64_t)ma * LB.cap);
-      copy(0, CM_ZERO, 0, 0, 0, sref(W), 1, ma, {ma, 0}, {LB.cap, 0});
-      block_mv(0, An, View{dref(LB.off), 1, mb}, View{sref(W), 1, ma}, 1.0, false, {0, rref(LB)}, LB.cap);
-      out.push_back({View{sref(W), 1, ma}, View{dref(LB.voff), 1, mc}, {0, rref(LB)}, LB.cap, ro, ma, co, mc, -1.0});
+      const uint64_t W = palloc((int64_t)ma * LB.cap);
+      copy(0, CM_ZERO, 0, 0, 0, W, 1, ma, {ma, 0}, {LB.cap, 0});
+      block_mv(0, An, View{dref(LB.off), 1, mb}, View{W, 1, ma}, 1.0, false, {0, rref(LB)}, LB.cap);
+      out.push_back({View{W, 1, ma}, View{dref(LB.voff), 1, mc}, {0, rref(LB)}, LB.cap, ro, ma, co, mc, -1.0});
       return;
     }
     if (Aleaf && Bleaf) {
@@ -470,35 +574,35 @@ struct Ctx {
         out.push_back({View{dref(LA.off), 1, ma}, View{dref(LB.off), mb, 1}, {mb, 0}, mb, ro, ma, co, mc, -1.0});
         return;
       }
-      const int64_t P = w.alloc_d((int64_t)ma * mc);
-      copy(0, CM_ZERO, 0, 0, 0, sref(P), 1, ma, {ma, 0}, {mc, 0});
-      gemm(1, dref(LA.off), 1, ma, dref(LB.off), 1, mb, sref(P), 1, ma, {ma, 0}, {mc, 0}, {mb, 0}, 1.0, GF_ATOMIC,
+      const uint64_t P = palloc((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, P, 1, ma, {ma, 0}, {mc, 0});
+      gemm(1, dref(LA.off), 1, ma, dref(LB.off), 1, mb, P, 1, ma, {ma, 0}, {mc, 0}, {mb, 0}, 1.0, GF_ATOMIC,
            FC_GEMM);
       if (ma <= mc) {
-        const int64_t I = identity(ma);
-        out.push_back({View{sref(I), 1, ma}, View{sref(P), ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
+        const uint64_t I = identity(ma);
+        out.push_back({View{I, 1, ma}, View{P, ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
       } else {
-        const int64_t I = identity(mc);
-        out.push_back({View{sref(P), 1, ma}, View{sref(I), 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
+        const uint64_t I = identity(mc);
+        out.push_back({View{P, 1, ma}, View{I, 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
       }
       return;
     }
     if (Aleaf) {   // A dense with a leaf row cluster, B structured: (I, B^T A^T)
       const LeafStore& LA = leaf_of(An);
-      const int64_t S = w.alloc_d((int64_t)ma * mc);
-      copy(0, CM_ZERO, 0, 0, 0, sref(S), 1, ma, {ma, 0}, {mc, 0});
-      block_mv(0, Bn, View{dref(LA.off), ma, 1}, View{sref(S), ma, 1}, 1.0, true, {ma, 0}, ma);
-      const int64_t I = identity(ma);
-      out.push_back({View{sref(I), 1, ma}, View{sref(S), ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
+      const uint64_t S = palloc((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, S, 1, ma, {ma, 0}, {mc, 0});
+      block_mv(0, Bn, View{dref(LA.off), ma, 1}, View{S, ma, 1}, 1.0, true, {ma, 0}, ma);
+      const uint64_t I = identity(ma);
+      out.push_back({View{I, 1, ma}, View{S, ma, 1}, {ma, 0}, ma, ro, ma, co, mc, -1.0});
       return;
     }
     if (Bleaf) {   // B dense with a leaf column cluster, A structured: (A B, I)
       const LeafStore& LB = leaf_of(Bn);
-      const int64_t S = w.alloc_d((int64_t)ma * mc);
-      copy(0, CM_ZERO, 0, 0, 0, sref(S), 1, ma, {ma, 0}, {mc, 0});
-      block_mv(0, An, View{dref(LB.off), 1, mb}, View{sref(S), 1, ma}, 1.0, false, {mc, 0}, mc);
-      const int64_t I = identity(mc);
-      out.push_back({View{sref(S), 1, ma}, View{sref(I), 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
+      const uint64_t S = palloc((int64_t)ma * mc);
+      copy(0, CM_ZERO, 0, 0, 0, S, 1, ma, {ma, 0}, {mc, 0});
+      block_mv(0, An, View{dref(LB.off), 1, mb}, View{S, 1, ma}, 1.0, false, {mc, 0}, mc);
+      const uint64_t I = identity(mc);
+      out.push_back({View{S, 1, ma}, View{I, 1, mc}, {mc, 0}, mc, ro, ma, co, mc, -1.0});
       return;
     }
     const Cluster& Ca = cl(a);
@@ -618,7 +722,20 @@ struct Ctx {
       return;
     }
     std::vector<Piece> pieces;
+    piece_release = -1;
+    if (events) {   // accumulator H-LU: pieces held past this wave live in the arena
+      std::vector<int> leaves;
+      collect_leaves(bt, Cn, leaves);
+      for (int lid : leaves) {
+        const int leaf = bt.nodes[lid].leaf;
+        if (!lay.leaf[leaf].lr) continue;
+        const int f = flush_level(leaf, level);
+        // the rounded addition of wave f may run beside wave f + 1: free from wave f + 2 on
+        if (f > level) piece_release = std::max(piece_release, f + 2);
+      }
+    }
     product_pieces(An, Bn, 0, 0, pieces);
+    piece_release = -1;
     apply_pieces(Cn, pieces);
   }
 
@@ -1015,31 +1132,29 @@ void plan_wave_ranges(int nlev, const std::vector<size_t>& tasks_per_wave, int t
 }
 }  // namespace
 
-// For every leaf block, the sorted levels of the tasks that touch it: the block a triangular
-// solve or a leaf LU works on, and the two operands and the target of a product.
-std::vector<std::vector<int>> touch_levels(const BlockTree& bt, const Layout& lay, const TaskGraph& g) {
-  std::vector<std::vector<int>> out(lay.leaf.size());
+static LeafEvents leaf_events(const BlockTree& bt, const Layout& lay, const TaskGraph& g) {
+  LeafEvents out(lay.leaf.size());
   std::vector<int> leaves;
-  auto mark = [&](int r, int c, int lv) {
+  auto mark = [&](int r, int c, int lv, int read) {
     const int id = bt.find(r, c);
     if (id < 0) return;
     leaves.clear();
     collect_leaves(bt, id, leaves);
-    for (int lid : leaves) out[bt.nodes[lid].leaf].push_back(lv);
+    for (int lid : leaves) out[bt.nodes[lid].leaf].push_back({lv, read});
   };
   for (size_t i = 0; i < g.nodes.size(); ++i) {
     const Task& t = g.nodes[i];
     const int lv = g.level[i];
     switch (t.type) {
-      case T_LU: mark(t.a, t.a, lv); break;
-      case T_TRSL: mark(t.a, t.b, lv); break;
-      case T_TRSU: mark(t.b, t.a, lv); break;
+      case T_LU: mark(t.a, t.a, lv, 1); break;
+      case T_TRSL: mark(t.a, t.b, lv, 1); break;
+      case T_TRSU: mark(t.b, t.a, lv, 1); break;
       case T_SHIFT:
-      case T_APPLY: mark(t.a, t.b, lv); break;
+      case T_APPLY: mark(t.a, t.b, lv, 1); break;
       default:
-        mark(t.a, t.b, lv);
-        mark(t.b, t.c, lv);
-        mark(t.a, t.c, lv);
+        mark(t.a, t.b, lv, 1);
+        mark(t.b, t.c, lv, 1);
+        mark(t.a, t.c, lv, 0);
         break;
     }
   }
@@ -1051,33 +1166,41 @@ std::vector<std::vector<int>> touch_levels(const BlockTree& bt, const Layout& la
 }
 
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g, double eps,
-             Plan& plan, int threads, int precision, bool defer) {
+             Plan& plan, int threads, int precision, bool defer, bool accumulate) {
   plan = Plan();
   const auto byl = by_level(g);
   std::vector<size_t> per(g.nlevels);
   for (int lv = 0; lv < g.nlevels; ++lv) per[lv] = byl[lv].size();
-  std::vector<std::vector<int>> touched;
-  if (defer) touched = touch_levels(bt, lay, g);
+  LeafEvents events;
+  if (defer || accumulate) events = leaf_events(bt, lay, g);
+  // a leaf is touched at a level when any task of that level reads or updates it
+  auto touched_at = [&](int leaf, int lv) {
+    const auto& v = events[leaf];
+    auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(lv, 0));
+    return it != v.end() && it->first == lv;
+  };
+  Arena arena;
   plan_wave_ranges(
-      g.nlevels, per, threads,
+      g.nlevels, per, accumulate ? 1 : threads,
       [&](Plan& part, int lv0, int lv1) {
         Ctx c(ct, bt, lay, Spaces{SP_F, IS_RANK}, part);
         c.mixed = precision;
+        if (accumulate) {
+          c.events = &events;
+          c.arena = &arena;
+        }
         for (int lv = lv0; lv < lv1; ++lv) {
           c.level = lv;
           if (defer) {
             c.ss = (lv & 1) ? SP_S2 : SP_S;
             c.sis = (lv & 1) ? IS_S2 : IS_S;
           }
+          if (accumulate) arena.release_until(lv);
           for (int ti : byl[lv]) expand_task(c, g.nodes[ti]);
+          if (accumulate) c.hold_pending(lv);
           std::vector<TargetEntries> later;
           if (defer)   // not touched by the next wave: its rounded addition can overlap that wave
-            c.take_deferred(
-                [&](int leaf) {
-                  const auto& v = touched[leaf];
-                  return !std::binary_search(v.begin(), v.end(), lv + 1);
-                },
-                later);
+            c.take_deferred([&](int leaf) { return !touched_at(leaf, lv + 1); }, later);
           c.emit_truncations(3, eps);
           if (!later.empty()) {
             c.targets.swap(later);
@@ -1088,9 +1211,11 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
           }
           c.flush();
         }
+        if (!c.pending.empty()) throw std::runtime_error("planner: accumulated updates never reached their leaf");
       },
       plan);
   plan.two_scratch = defer;
+  plan.arena_doubles = arena.top;
 }
 
 void plan_lu_batch(const std::vector<LuInstance>& inst, double eps, Plan& plan, int threads, int precision) {

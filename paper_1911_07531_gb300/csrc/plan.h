@@ -150,6 +150,8 @@ struct Plan {
   int64_t scratch_trunc_max = 0;      // largest truncation scratch of one wave (doubles)
   bool two_scratch = false;           // odd waves use SP_S2 / IS_S2 (deferred rounded additions)
   int64_t deferred_truncations = 0;   // rounded additions on the side stream
+  int64_t arena_doubles = 0;          // accumulator arena (SP_ACC) of an accumulator H-LU plan
+  int64_t accumulated_pieces = 0;     // update pieces kept in the arena across waves
 };
 
 // Memory spaces the planner addresses (factor vs. matrix storage).
@@ -167,8 +169,14 @@ struct Spaces {
 // defer: rounded additions whose target leaf is not touched by the next wave (no task of the
 // next level reads it, no product of the next level updates it) become side launches of their
 // wave (Launch::side), overlapping the next wave; odd waves then use the second scratch space.
+// accumulate: the accumulator H-LU of §2.3 (Alg 4-8) with its accumulators held as lists of
+// pieces: the product pieces that reach a low-rank leaf are not truncated in the wave that forms
+// them but kept (in the arena SP_ACC when they outlive their wave) and added in one rounded
+// addition in the wave of the leaf's last update before the leaf is read (apply_upd before the
+// solve, the leaf LU or a product that uses it). Planned on one thread.
 void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, const TaskGraph& g,
-             double eps, Plan& plan, int threads = 0, int precision = 0, bool defer = false);
+             double eps, Plan& plan, int threads = 0, int precision = 0, bool defer = false,
+             bool accumulate = false);
 // Independent H-LU instances in one plan: wave w of every instance is expanded into the same
 // phases, so that one launch per kind and phase serves all of them (their task graphs have no
 // edges between each other). Instance i addresses its values, ranks and pivots at the given

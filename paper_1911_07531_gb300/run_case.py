@@ -8,6 +8,9 @@
   python -m paper_1911_07531_gb300.run_case overlap WORKLOAD EPS REPEATS
       hm_lu of a workload with the wave overlap off and on (hm_set_overlap), alternating, after
       a warm-up of each; prints the device seconds of every factorization as JSON lines.
+  python -m paper_1911_07531_gb300.run_case accumulate WORKLOAD EPS REPEATS
+      hm_lu of a workload as the H-LU of Alg 2 and as the accumulator H-LU, alternating, after a
+      warm-up of each; prints device seconds, rounded additions and the arena size as JSON lines.
   python -m paper_1911_07531_gb300.run_case kinds WORKLOAD EPS
       one hm_lu per precision (FP64, MIXED, MIXED_TC) of a workload of `hm_workloads.WORKLOADS`
       after a warm-up, then a profiled one (CUDA events around every launch); prints the device
@@ -104,6 +107,28 @@ def _overlap(workload, eps, repeats):
                               "plan_deferred": st["plan_deferred"]}), flush=True)
 
 
+def _accumulate(workload, eps, repeats):
+    import hm_workloads as W
+
+    from . import HMContext, build_library, hm_build, hm_lu
+    build_library()
+    w = W.WORKLOADS[workload]
+    ctx = HMContext(0)
+    A = hm_build(ctx, W.points_for(w["geometry"], w["n"], w["seed"]), w["leaf"], w["eta"], w["eps"], w["rank_cap"])
+    for acc in (False, True):
+        hm_lu(ctx, A, eps=eps, accumulate=acc).free()
+    for r in range(repeats):
+        for acc in (False, True):
+            F = hm_lu(ctx, A, eps=eps, accumulate=acc)
+            st = F.stats()
+            F.free()
+            print(json.dumps({"accumulate": acc, "repeat": r, "seconds": st["seconds"],
+                              "plan_seconds": st["plan_seconds"], "plan_launches": st["plan_launches"],
+                              "plan_truncations": st["plan_truncations"], "arena_gb": st["arena_bytes"] / 1e9,
+                              "accumulated_pieces": st["accumulated_pieces"],
+                              "scratch_gb": st["scratch_bytes"] / 1e9}), flush=True)
+
+
 def main(argv=None):
     a = sys.argv[1:] if argv is None else argv
     if a and a[0] == "lu" and len(a) == 5:
@@ -112,6 +137,8 @@ def main(argv=None):
         _xmv(int(a[1]))
     elif a and a[0] == "overlap" and len(a) == 4:
         _overlap(a[1], float(a[2]), int(a[3]))
+    elif a and a[0] == "accumulate" and len(a) == 4:
+        _accumulate(a[1], float(a[2]), int(a[3]))
     elif a and a[0] == "kinds" and len(a) == 3:
         _kinds(a[1], float(a[2]))
     else:

@@ -34,7 +34,7 @@ from numpy.lib.stride_tricks import as_strided
 MASK = (1 << 60) - 1
 K_GETRF, K_TRSM, K_GEMM, K_COPY, K_STACK, K_CORE, K_EVAL, K_ACA = range(8)
 GF_ATOMIC, GF_OVERWRITE, GF_A_UPPER, GF_A_UNITLOWER, GF_SYM_UPPER = 1, 2, 4, 8, 16
-SP_F, SP_S, SP_X, SP_A, SP_P, SP_S2 = 0, 1, 2, 3, 4, 5
+SP_F, SP_S, SP_X, SP_A, SP_P, SP_S2, SP_ACC = 0, 1, 2, 3, 4, 5, 6
 IS_RANK, IS_PIV, IS_S, IS_ARANK, IS_S2 = 0, 1, 2, 3, 4
 KMAX_ENTRIES = 256
 
@@ -42,7 +42,8 @@ KMAX_ENTRIES = 256
 class PlanSim:
     def __init__(self, sizes, nrhs_space=0):
         self.d = {SP_F: np.zeros(int(sizes["nvalues"])), SP_S: np.zeros(int(sizes["scratch_doubles"])),
-                  SP_X: np.zeros(int(nrhs_space)), SP_S2: np.zeros(int(sizes["scratch_doubles"]))}
+                  SP_X: np.zeros(int(nrhs_space)), SP_S2: np.zeros(int(sizes["scratch_doubles"])),
+                  SP_ACC: np.zeros(int(sizes["arena_doubles"]))}
         self.i = {IS_RANK: np.zeros(int(sizes["nranks"]), np.int64), IS_PIV: np.zeros(int(sizes["npiv"]), np.int64),
                   IS_S: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64),
                   IS_S2: np.zeros(max(int(sizes["scratch_ints"]), 1), np.int64)}

@@ -121,7 +121,7 @@ def test_plan_builds_on_host(lib):
 
 def test_plan_export_errors(lib):
     S = hm.hm_structure_build(W.fibonacci_sphere(512, 3), 64, 2.0)
-    for args in ((9, 1e-6, 64, 1), (0, 0.0, 64, 1), (0, 1e-6, 65, 1), (1, 0.0, 64, 0)):
+    for args in ((10, 1e-6, 64, 1), (0, 0.0, 64, 1), (8, 0.0, 64, 1), (0, 1e-6, 65, 1), (1, 0.0, 64, 0)):
         with pytest.raises(hm.HMError):
             S.plan(*args)
     acc = hm.hm_structure_build_accumulator(W.fibonacci_sphere(512, 3), 64, 2.0)

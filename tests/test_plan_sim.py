@@ -325,23 +325,26 @@ def _merge(fps):
     return acc, wr
 
 
-def test_overlap_plan_on_the_host(lib):
+@pytest.mark.parametrize("which", [7, 9])
+def test_overlap_plan_on_the_host(lib, which):
     """The H-LU plan with wave overlap (rounded additions deferred to side launches): the side
     launches of a wave are its last launches and are stack / Gram / core / rebuild launches;
     executed at the latest time the streams allow (after the next wave) they give the same
     factors as in plan order, and the same as the plan without overlap; and no side launch of
     wave w changes memory that a launch of wave w + 1 accesses, or the other way round (the
     two run concurrently on the device). In these task graphs no rounded-addition target of
-    wave w is touched by wave w + 1, so every rounded addition is deferred."""
+    wave w is touched by wave w + 1, so every rounded addition is deferred. which = 7: the H-LU
+    of Alg 2, 9: the accumulator H-LU (held pieces in the arena)."""
     geom, n, eps = "cube", 700, 1e-6
     pts = W.points_for(geom, n, 21)
     hmat = HMatrix(pts, 64, 2.0, eps, 64)
     S = hm.hm_structure_build(pts, 64, 2.0)
-    P0 = S.plan(0, eps, 64)
-    P = S.plan(7, eps, 64)
+    P0 = S.plan(0 if which == 7 else 8, eps, 64)
+    P = S.plan(which, eps, 64)
     L = P["launches"]
     side = L[L["side"] == 1]
     assert side.size > 0 and P["sizes"]["ntrunc"] == P0["sizes"]["ntrunc"]
+    assert (P["sizes"]["arena_doubles"] > 0) == (which == 9)
     assert np.all(np.diff(L["wave"]) >= 0)
     assert set(np.unique(side["kind"]).tolist()) <= {4, 5, 2}   # stack, core, gemm
     for w in np.unique(side["wave"]):
@@ -395,3 +398,61 @@ def test_overlap_plan_on_the_host(lib):
     # the check sees real dependences: wave w + 2 reuses the scratch of wave w's side launches
     # and updates some of their targets again, which is why it waits for them
     assert checked > 0 and later > 0
+
+
+class _CountingAccu:
+    """The oracle's accumulator H-LU (piece lists), recording how many pieces every low-rank
+    leaf receives in its one rounded addition."""
+
+    @staticmethod
+    def run(hmat):
+        from oracle.accu import AccuHLUFactor
+
+        class Rec(AccuHLUFactor):
+            def apply_to_leaf(self, leaf, alpha, pieces, base_row, base_col):
+                lr0, lr1 = leaf.row.lo - base_row, leaf.row.hi - base_row
+                lc0, lc1 = leaf.col.lo - base_col, leaf.col.hi - base_col
+                k = sum(1 for (r0, c0, Wp, Zp) in pieces
+                        if max(r0, lr0) < min(r0 + Wp.shape[0], lr1) and max(c0, lc0) < min(c0 + Zp.shape[0], lc1))
+                if k and not isinstance(self.M[leaf.key], Dense):
+                    self.counts[(leaf.row.lo, leaf.col.lo)] = self.counts.get((leaf.row.lo, leaf.col.lo), 0) + k
+                return super().apply_to_leaf(leaf, alpha, pieces, base_row, base_col)
+
+        R = Rec(hmat)
+        R.counts = {}
+        return R.factor()
+
+
+@pytest.mark.parametrize("geom,n,eps", [("sphere", 1024, 1e-6), ("cube", 1500, 1e-4)])
+def test_accumulator_plan_on_the_host(lib, geom, n, eps):
+    """The accumulator H-LU plan (Alg 4-8, piece lists): every low-rank leaf receives in its
+    rounded additions exactly the pieces that the oracle's accumulator H-LU hands to it in one
+    apply_upd (counted per leaf), fewer rounded additions than the H-LU of Alg 2, and factors
+    within 10 eps of the exact kernel and within eps of the oracle's accumulator factors."""
+    pts = W.points_for(geom, n, 21)
+    hmat = HMatrix(pts, 64, 2.0, eps, 64)
+    S = hm.hm_structure_build(pts, 64, 2.0)
+    P0 = S.plan(0, eps, 64)
+    P = S.plan(8, eps, 64)
+    assert P["sizes"]["arena_doubles"] > 0
+    assert P["sizes"]["ntrunc"] < P0["sizes"]["ntrunc"]
+    R = _CountingAccu.run(hmat)
+    cl = S.export()["clusters"]
+    key = {int(lf["off"]): (int(cl[lf["row"], 0]), int(cl[lf["col"], 0])) for lf in P["leaves"] if lf["lr"]}
+    counts = {}
+    L = P["launches"]
+    for ln in L[L["kind"] == 4]:
+        for op in P["trunc"][ln["begin"]:ln["begin"] + ln["count"]]:
+            k = key[int(op["U"]) & ((1 << 60) - 1)]
+            counts[k] = counts.get(k, 0) + int(op["n_entries"])
+    assert counts == R.counts
+    sim = PlanSim(P["sizes"])
+    _load(sim, P["leaves"], hmat.store)
+    sim.run(P)
+    assert sim.singular == 0
+    f = _factor(hmat, sim, P["leaves"])
+    A = hmat.exact_dense()
+    X = np.random.default_rng(3).standard_normal((n, 4))
+    AX = A @ X
+    assert np.linalg.norm(AX - f.apply_lu(X)) / np.linalg.norm(AX) <= 10 * eps
+    assert np.linalg.norm(f.apply_lu(X) - R.apply_lu(X)) / np.linalg.norm(AX) <= eps
