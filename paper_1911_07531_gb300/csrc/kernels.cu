@@ -166,9 +166,10 @@ __device__ __forceinline__ unsigned pivot_key(double v, int i) {
 // elements of a tile, and for tiles of fewer than 128 elements G = 2..8 threads split the
 // reduction of one element (partial sums combined in shared memory). Slices of GKS reduction
 // steps of both operands are staged in shared memory through two buffers: the next slice is
-// fetched with cp.async while the current one is multiplied. Tiles of one micro-op are spread
-// over blockIdx.y and, for accumulating (atomic) micro-ops, reduction slices over blockIdx.z
-// (per micro-op counts in GemmOp::split), so that a large micro-op does not sit on one SM.
+// fetched with cp.async while the current one is multiplied. A micro-op has a budget of CTAs
+// along blockIdx.y (GemmOp::split), which the kernel divides between its C tiles and, for
+// accumulating (atomic) micro-ops, reduction slices, from the actual sizes, so that a large
+// micro-op does not sit on one SM.
 constexpr int KMAX_ENTRIES = 256;   // largest number of pieces of one rounded addition (planner)
 constexpr int GE = 1024;      // largest C tile (elements)
 constexpr int GTM = 128;      // largest C tile side
@@ -244,15 +245,18 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
   const int nslices = (k + GKS - 1) / GKS;
   int mt, nt, nrt, nct;
   gemm_tile_shape(m, n, mt, nt, nrt, nct);
-  // split actually used: the planner's bound, lowered to ~16k FMAs per CTA for the real sizes
-  const int symax = max(1, op.split & 0xffff), szmax = atomic ? max(1, op.split >> 16) : 1;
+  // CTAs of this micro-op: the planner's budget (at most gridDim.y), lowered to the tuned work
+  // per CTA for the actual sizes and factored here into C tiles (sy) times reduction slices (sz,
+  // atomic micro-ops only), sy * sz <= budget. The factoring follows the actual sizes, so a Gram
+  // product whose dynamic K x K output fits in a few tiles spreads its rows over the slices.
+  const int budget = max(1, op.split & 0xffff) * max(1, op.split >> 16);
   const double work = (double)m * n * max(k, 1);
   const double per_cta = B.gemm_work > 0.f ? (double)B.gemm_work : 16384.0;
-  const int want = min(symax * szmax, max(1, (int)ceil(work / per_cta)));
-  const int sy = min(min(want, symax), nrt * nct);
-  const int sz = min(min((want + sy - 1) / sy, szmax), max(nslices, 1));
-  if ((int)blockIdx.y >= sy || (int)blockIdx.z >= sz) return;
-  const int z0 = blockIdx.z, zs = sz;
+  const int want = min(budget, max(1, (int)ceil(work / per_cta)));
+  const int sy = min(want, nrt * nct);
+  const int sz = atomic ? max(1, min(want / sy, max(nslices, 1))) : 1;
+  if ((int)blockIdx.y >= sy * sz) return;
+  const int ty = (int)blockIdx.y % sy, z0 = (int)blockIdx.y / sy, zs = sz;
   extern __shared__ double gsm[];             // buffer b: A slice [GKS][GTM + 1], B slice [GKS][GTM + 1]
   double* red = gsm + 2 * GBUF;               // [256]
   float* fsl = (float*)(red + 256);           // FP32 copy of the current slice (F32 only)
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
   const bool b_j_fast = op.b_cs <= op.b_rs;
   const bool upper = op.flags & GF_A_UPPER, unitlower = op.flags & GF_A_UNITLOWER;
   const bool sym = op.flags & GF_SYM_UPPER;
-  for (int tile = blockIdx.y; tile < nrt * nct; tile += sy) {
+  for (int tile = ty; tile < nrt * nct; tile += sy) {
     const int i0 = (tile % nrt) * mt, j0 = (tile / nrt) * nt;
     const int mi = min(mt, m - i0), nj = min(nt, n - j0);
     const int c0 = j0 - i0 + 1;
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
       }
     }
   }
-  if (threadIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+  if (threadIdx.x == 0 && blockIdx.y == 0) {
     // a symmetric product computes only the entries i <= j: sum_j min(j + 1, m) of them
     const double entries = sym ? (n <= m ? 0.5 * n * (n + 1.0) : 0.5 * m * (m + 1.0) + (double)(n - m) * m)
                                : (double)m * n;

@@ -55,7 +55,8 @@ struct GemmOp {
   int flags;
   double alpha;
   int fclass;
-  int split;   // CTAs of this micro-op: (split & 0xffff) along C tiles, (split >> 16) along reduction
+  int split;   // CTA budget of this micro-op: (split & 0xffff) * max(1, split >> 16); the kernel
+               // divides it between C tiles and (atomic micro-ops) reduction slices
                // slices (0 = one CTA); CTAs of the launch grid beyond them exit
 };
 

@@ -63,7 +63,8 @@ void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz) {
   // `split` (0: 16). A CTA should get at least the tuned work (default ~16k FMAs, 8k cycles of
   // one SM's FP64 pipe; set_gemm_min_work) and
   // about the launch's average work per CTA slot (three resident CTAs per SM). The split stored
-  // is an upper bound; the kernel lowers it from the actual sizes.
+  // is a budget of CTAs (grid y = the largest budget, z = 1); the kernel lowers it from the
+  // actual sizes and divides it between C tiles and reduction slices.
   const double kMinWork = g_gemm_min_work.load();
   constexpr int kSlots = 3 * 152, kMaxSplit = 32, kTile = 1024, kSlice = 16;
   thread_local std::vector<double> w;
@@ -94,12 +95,11 @@ void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz) {
     const int want = std::min(kMaxSplit, std::max(1, (int)std::ceil(w[idx[t]] / target)));
     const int tiles = std::max(1, (int)((m * n + kTile - 1) / kTile));
     const int slices = (src.flags & GF_ATOMIC) ? std::max(1, (int)((k + kSlice - 1) / kSlice)) : 1;
-    const int sy = std::max(1, std::min(want, tiles));
-    const int sz = std::max(1, std::min((want + sy - 1) / sy, slices));
+    // a CTA budget: the kernel factors it into C tiles and reduction slices of the actual sizes
+    const int budget = std::max(1, std::min(want, tiles * slices));
     out[t] = src;
-    out[t].split = sy | (sz << 16);
-    gy = std::max(gy, sy);
-    gz = std::max(gz, sz);
+    out[t].split = budget;
+    gy = std::max(gy, budget);
   }
 }
 
