@@ -270,7 +270,7 @@ int hm_truncate_noalloc(void* cuda_stream, int64_t m, int64_t n, int K, const do
                         int64_t ldv, int* k_out);
 
 /* GEMM split tuning (process-wide): the number of FMAs that one CTA of the batched GEMM kernels
- * aims at when a micro-op is spread over several CTAs (default 16384). Smaller values give more,
+ * aims at when a micro-op is spread over several CTAs (default 4096). Smaller values give more,
  * shorter CTAs (more parallelism, more atomic partial sums), larger ones fewer. It changes the
  * plans (an H-LU plan built at another value is rebuilt at the next hm_lu) and the speed, not
  * the results beyond rounding. HM_EINVAL outside [256, 2^24]. */

@@ -449,7 +449,7 @@ def hm_get_overlap():
     return load_library().hm_get_overlap()
 
 
-def hm_autotune_gemm(ctx, A, candidates=(4096.0, 8192.0, 16384.0, 32768.0, 65536.0), eps=0.0, precision=0):
+def hm_autotune_gemm(ctx, A, candidates=(2048.0, 4096.0, 8192.0, 16384.0, 32768.0), eps=0.0, precision=0):
     """Time hm_lu of A at every candidate GEMM split target, keep the fastest set; returns
     (best, {candidate: seconds})."""
     c = (ctypes.c_double * len(candidates))(*[float(v) for v in candidates])

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
   // product whose dynamic K x K output fits in a few tiles spreads its rows over the slices.
   const int budget = max(1, op.split & 0xffff) * max(1, op.split >> 16);
   const double work = (double)m * n * max(k, 1);
-  const double per_cta = B.gemm_work > 0.f ? (double)B.gemm_work : 16384.0;
+  const double per_cta = B.gemm_work > 0.f ? (double)B.gemm_work : 4096.0;
   const int want = min(budget, max(1, (int)ceil(work / per_cta)));
   const int sy = min(want, nrt * nct);
   const int sz = atomic ? max(1, min(want / sy, max(nslices, 1))) : 1;

@@ -52,21 +52,21 @@ void run_workers(int threads, F worker) {
 }  // namespace
 
 namespace {
-std::atomic<double> g_gemm_min_work{16384.0};
+std::atomic<double> g_gemm_min_work{4096.0};
 }  // namespace
 
-void set_gemm_min_work(double w) { g_gemm_min_work.store(w > 0.0 ? w : 16384.0); }
+void set_gemm_min_work(double w) { g_gemm_min_work.store(w > 0.0 ? w : 4096.0); }
 double gemm_min_work() { return g_gemm_min_work.load(); }
 
 void gemm_grid_to(const GemmOp* ops, int count, GemmOp* out, int& gy, int& gz) {
   // Dynamic sizes (ranks) are not known here: each micro-op carries an expected value in
-  // `split` (0: 16). A CTA should get at least the tuned work (default ~16k FMAs, 8k cycles of
+  // `split` (0: 16). A CTA should get at least the tuned work (default 4096 FMAs, ~2k cycles of
   // one SM's FP64 pipe; set_gemm_min_work) and
   // about the launch's average work per CTA slot (three resident CTAs per SM). The split stored
   // is a budget of CTAs (grid y = the largest budget, z = 1); the kernel lowers it from the
   // actual sizes and divides it between C tiles and reduction slices.
   const double kMinWork = g_gemm_min_work.load();
-  constexpr int kSlots = 3 * 152, kMaxSplit = 32, kTile = 1024, kSlice = 16;
+  constexpr int kSlots = 3 * 152, kMaxSplit = 128, kTile = 1024, kSlice = 16;
   thread_local std::vector<double> w;
   thread_local std::vector<int> idx;
   w.resize(count);
