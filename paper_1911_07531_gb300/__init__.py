@@ -494,7 +494,8 @@ PLAN_DTYPES = {
                  ("md", _U8), ("nd", _U8), ("m", _I4), ("n", _I4), ("mode", _I4), ("pad", _I4), ("alpha", _F8)]),
     "trunc": _dt([("U", _U8), ("V", _U8), ("rank", _U8), ("m", _I4), ("n", _I4), ("cap", _I4), ("Kcap", _I4),
                   ("first_entry", _I4), ("n_entries", _I4), ("Wst", _U8), ("Zst", _U8), ("Gw", _U8), ("Gz", _U8),
-                  ("Tw", _U8), ("Tz", _U8), ("work", _U8), ("Kd", _U8), ("eps", _F8)]),
+                  ("Tw", _U8), ("Tz", _U8), ("work", _U8), ("Kd", _U8), ("eps", _F8), ("flags", _I4),
+                  ("pad2", _I4)]),
     "entries": _dt([("W", _U8), ("w_rs", _I8), ("w_cs", _I8), ("Z", _U8), ("z_rs", _I8), ("z_cs", _I8),
                     ("kd", _U8), ("k", _I4), ("row_off", _I4), ("nrows", _I4), ("col_off", _I4), ("ncols", _I4),
                     ("pad", _I4), ("alpha", _F8)]),

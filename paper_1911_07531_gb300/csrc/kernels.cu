@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
   // publishes the stacked rank and clears the Gram matrices.
   const TruncOp op = ops[blockIdx.x];
   const int m = op.m, n = op.n, Kc = op.Kcap, tid = threadIdx.x;
-  const int kself = *iptr(B, op.rank);
+  const int kself = (op.flags & TF_NOSELF) ? 0 : *iptr(B, op.rank);
   const int ne = min(op.n_entries, KMAX_ENTRIES);
   __shared__ int s_ke[KMAX_ENTRIES], s_col[KMAX_ENTRIES], s_K;
   for (int e = tid; e < ne; e += blockDim.x) {

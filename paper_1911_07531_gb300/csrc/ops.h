@@ -115,7 +115,10 @@ struct TruncOp {
   uint64_t work;       // 2 * Kcap * Kcap doubles (Gw and Gz are reused by the core)
   uint64_t Kd;         // int ref: stacked rank
   double eps;
+  int flags;           // TF_NOSELF: the stack leaves out U, V (a temporary sum: its rank is not read)
+  int pad_;
 };
+enum TruncFlags : int { TF_NOSELF = 1 };
 
 // dense leaf assembly: D(i,j) = 1 / (4 pi (|p_{r0+i} - p_{c0+j}| + h)), permuted points
 struct EvalOp {

@@ -751,50 +751,144 @@ struct Ctx {
   }
 
   // rounded additions of all pieces that reached low-rank leaves in this wave. A target whose
-  // pieces exceed KMAX_STACK columns is updated in rounds (chunk r+1 after chunk r). The
-  // truncations of one round run in batches whose scratch fits `budget`; every batch reuses
-  // the same scratch region (they are sequential phases), so a wave's scratch is its product
-  // temporaries plus one batch.
+  // pieces and own factors fit one stack (KMAX_STACK columns by static rank bounds) is one
+  // rounded addition. A larger one is either updated in sequential rounds (chunk r + 1 stacked
+  // on the result of chunk r) or, when that takes more levels, as a tree: stacks of pieces are
+  // rounded in parallel into temporary low-rank sums (groups: stacks without the target's own
+  // factors, TF_NOSELF), those are combined the same way level by level, and the last level adds
+  // the target's own factors and at most the remaining sums; rounded additions of one level are
+  // independent. The rounded additions of one level run in batches whose scratch fits `budget`;
+  // every batch reuses the same scratch region (they are sequential phases), so a wave's scratch
+  // is its product temporaries, the groups' sums and one batch.
   void emit_truncations(int ph0, double eps, bool target_rank_zero = false, int64_t budget = (int64_t)1 << 29) {
-    const int64_t base = w.sd;
-    plan.scratch_products_max = std::max(plan.scratch_products_max, base);
-    // chunking of every target
-    struct Chunk {
-      int target;
-      size_t e0, e1;
-      int Kc;
-      bool zero_self;
+    plan.scratch_products_max = std::max(plan.scratch_products_max, w.sd);
+    struct Group {
+      uint64_t U, V, rank;   // the temporary sum (ld m and n, cap columns) and its rank
     };
-    std::vector<std::vector<Chunk>> rounds;
+    struct Job {
+      int target;            // index into targets: the leaf whose shape the stack has
+      bool self;             // the stack starts with the output's own factors
+      int out;               // -1: the leaf; else a group
+      std::vector<std::pair<StackEntry, int>> e;   // pieces with static rank bounds
+      int sum;               // static stacked rank
+    };
+    std::vector<Group> groups;
+    std::vector<std::vector<Job>> levels;
+    auto level = [&](size_t lv) -> std::vector<Job>& {
+      if (levels.size() <= lv) levels.resize(lv + 1);
+      return levels[lv];
+    };
+    // greedy chunks of es with static sums <= room and at most KMAX_ENTRIES pieces
+    auto chunks = [&](const std::vector<std::pair<StackEntry, int>>& es, int room) {
+      std::vector<std::pair<size_t, size_t>> out;
+      size_t e0 = 0;
+      while (e0 < es.size()) {
+        int sum = 0;
+        size_t e1 = e0;
+        while (e1 < es.size() && e1 - e0 < (size_t)KMAX_ENTRIES && (e1 == e0 || sum + es[e1].second <= room)) {
+          sum += es[e1].second;
+          ++e1;
+        }
+        if (sum > room) throw std::runtime_error("planner: piece rank exceeds the stack limit");
+        out.push_back({e0, e1});
+        e0 = e1;
+      }
+      return out;
+    };
+    // a temporary sum as a piece of the next level's stacks
+    auto group_entry = [&](const Group& g, const LeafStore& L) {
+      StackEntry e;
+      std::memset(&e, 0, sizeof(e));
+      e.W = g.U;
+      e.w_rs = 1;
+      e.w_cs = L.m;
+      e.Z = g.V;
+      e.z_rs = 1;
+      e.z_cs = L.n;
+      e.k = 0;
+      e.kd = g.rank;
+      e.row_off = 0;
+      e.nrows = L.m;
+      e.col_off = 0;
+      e.ncols = L.n;
+      e.alpha = 1.0;
+      return std::make_pair(e, L.cap);
+    };
     for (size_t ti = 0; ti < targets.size(); ++ti) {
       const TargetEntries& T = targets[ti];
       const LeafStore& L = lay.leaf[T.leaf];
-      size_t e0 = 0;
-      int round = 0;
-      while (e0 < T.e.size()) {
-        const int selfmax = (target_rank_zero && round == 0) ? 0 : L.cap;
-        int sum = selfmax;
-        size_t e1 = e0;
-        while (e1 < T.e.size() && e1 - e0 < (size_t)KMAX_ENTRIES &&
-               (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
-          sum += T.e[e1].second;
-          ++e1;
+      // sequential rounds: the first with the target's static rank (0 for an empty target)
+      std::vector<std::pair<size_t, size_t>> seq;
+      std::vector<int> seq_sum;
+      {
+        size_t e0 = 0;
+        for (int round = 0; e0 < T.e.size(); ++round) {
+          const int selfmax = (target_rank_zero && round == 0) ? 0 : L.cap;
+          int sum = selfmax;
+          size_t e1 = e0;
+          while (e1 < T.e.size() && e1 - e0 < (size_t)KMAX_ENTRIES &&
+                 (e1 == e0 || sum + T.e[e1].second <= KMAX_STACK)) {
+            sum += T.e[e1].second;
+            ++e1;
+          }
+          if (sum > KMAX_STACK) throw std::runtime_error("planner: piece rank exceeds the stack limit");
+          seq.push_back({e0, e1});
+          seq_sum.push_back(sum);
+          e0 = e1;
         }
-        if (sum > KMAX_STACK) throw std::runtime_error("planner: piece rank exceeds the stack limit");
-        if ((int)rounds.size() <= round) rounds.resize(round + 1);
-        rounds[round].push_back({(int)ti, e0, e1, std::max(2, (sum + 1) / 2 * 2), selfmax == 0});
-        e0 = e1;
-        ++round;
       }
+      // tree: the groups of the pieces, the levels that combine sums, the last stack
+      const int capk = std::max(1, L.cap);
+      const int per = std::max(1, std::min(KMAX_ENTRIES, KMAX_STACK / capk));
+      const int last = std::max(0, (KMAX_STACK - (target_rank_zero ? 0 : L.cap)) / capk);
+      int tree = 2;
+      {
+        int r = (int)chunks(T.e, KMAX_STACK).size();
+        while (r > last) {
+          r = (r + per - 1) / per;
+          ++tree;
+        }
+      }
+      if ((int)seq.size() <= tree || last < 1) {
+        for (size_t q = 0; q < seq.size(); ++q) {
+          Job j{(int)ti, true, -1, {T.e.begin() + seq[q].first, T.e.begin() + seq[q].second}, seq_sum[q]};
+          level(q).push_back(std::move(j));
+        }
+        continue;
+      }
+      std::vector<std::pair<StackEntry, int>> cur = T.e;
+      size_t lv = 0;
+      for (;;) {
+        const auto ch = chunks(cur, KMAX_STACK);
+        std::vector<std::pair<StackEntry, int>> next;
+        for (const auto& c : ch) {
+          Group g;
+          g.U = sref(w.alloc_d((int64_t)L.m * L.cap));
+          g.V = sref(w.alloc_d((int64_t)L.n * L.cap));
+          g.rank = mkref(sis, w.alloc_i(1));
+          Job j{(int)ti, false, (int)groups.size(), {cur.begin() + c.first, cur.begin() + c.second}, 0};
+          for (const auto& pe : j.e) j.sum += pe.second;
+          groups.push_back(g);
+          level(lv).push_back(std::move(j));
+          next.push_back(group_entry(groups.back(), L));
+        }
+        cur.swap(next);
+        ++lv;
+        if ((int)cur.size() <= last) break;
+      }
+      Job j{(int)ti, true, -1, cur, target_rank_zero ? 0 : L.cap};
+      for (const auto& pe : cur) j.sum += pe.second;
+      level(lv).push_back(std::move(j));
     }
+    const int64_t base = w.sd;   // after the groups' sums, which live through all levels
     int batch = 0;
     int64_t peak = 0;
-    for (const auto& rd : rounds) {
+    for (const auto& rd : levels) {
       w.sd = base;
       bool opened = false;
-      for (const Chunk& ch : rd) {
-        const LeafStore& L = lay.leaf[targets[ch.target].leaf];
-        const int Kc = ch.Kc;
+      for (const Job& jb : rd) {
+        const LeafStore& L = lay.leaf[targets[jb.target].leaf];
+        const int Kc = std::max(2, (jb.sum + 1) / 2 * 2);
         const int64_t need = (int64_t)(L.m + L.n) * Kc + 4 * (int64_t)Kc * Kc + 2 * (int64_t)Kc * L.cap + 8 * ALIGN;
         if (opened && w.sd + need - base > budget) {
           ++batch;
@@ -805,9 +899,16 @@ struct Ctx {
         w.need(ph + 3);
         TruncOp op;
         std::memset(&op, 0, sizeof(op));
-        op.U = dref(L.off);
-        op.V = dref(L.voff);
-        op.rank = rref(L);
+        if (jb.out < 0) {
+          op.U = dref(L.off);
+          op.V = dref(L.voff);
+          op.rank = rref(L);
+        } else {
+          op.U = groups[jb.out].U;
+          op.V = groups[jb.out].V;
+          op.rank = groups[jb.out].rank;
+          op.flags = TF_NOSELF;
+        }
         op.m = L.m;
         op.n = L.n;
         op.cap = L.cap;
@@ -823,8 +924,7 @@ struct Ctx {
         op.eps = eps;
         peak = std::max(peak, w.sd);
         std::vector<StackEntry> es;
-        const TargetEntries& T = targets[ch.target];
-        for (size_t q = ch.e0; q < ch.e1; ++q) es.push_back(T.e[q].first);
+        for (const auto& pe : jb.e) es.push_back(pe.first);
         w.stack[ph].push_back(op);
         w.stack_entries[ph].push_back(es);
         const Dim Kd{0, op.Kd};

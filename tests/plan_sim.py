@@ -11,8 +11,9 @@ checked against the oracle without a GPU:
   gemm   C (+)= alpha A B on strided operands with dynamic dimension adders; flags select
          accumulate / overwrite, an upper or unit-lower A, and an upper-triangle-only C;
   copy   zero / identity / alpha-scaled copy / alpha-scaled add of a strided block;
-  stack  W = [U, a_1 W_1, ...], Z = [V, Z_1, ...] with zero rows outside each piece, the
-         stacked rank K, and zeroed K x K Gram matrices;
+  stack  W = [U, a_1 W_1, ...], Z = [V, Z_1, ...] with zero rows outside each piece (without U,
+         V for a temporary sum of a tree of rounded additions), the stacked rank K, and zeroed
+         K x K Gram matrices;
   core   from the Gram matrices of W and Z (upper triangles): coefficient matrices T_W, T_Z
          with W T_W = U_k S_k, Z T_Z = V_k for the singular values above eps s_1 (at most
          the cap), and the new rank k. Computed here by symmetric eigendecompositions of the
@@ -37,6 +38,7 @@ GF_ATOMIC, GF_OVERWRITE, GF_A_UPPER, GF_A_UNITLOWER, GF_SYM_UPPER = 1, 2, 4, 8, 
 SP_F, SP_S, SP_X, SP_A, SP_P, SP_S2, SP_ACC = 0, 1, 2, 3, 4, 5, 6
 IS_RANK, IS_PIV, IS_S, IS_ARANK, IS_S2 = 0, 1, 2, 3, 4
 KMAX_ENTRIES = 256
+TF_NOSELF = 1   # a stack without the output's own factors (a temporary sum of a tree of rounded additions)
 
 
 class PlanSim:
@@ -175,7 +177,7 @@ class PlanSim:
 
     def stack(self, op, entries):
         m, n, Kc = int(op["m"]), int(op["n"]), int(op["Kcap"])
-        kself = self.ival(op["rank"])
+        kself = 0 if int(op["flags"]) & TF_NOSELF else self.ival(op["rank"])
         ent = entries[int(op["first_entry"]):int(op["first_entry"]) + min(int(op["n_entries"]), KMAX_ENTRIES)]
         ke = [max(self.dim(e["k"], e["kd"]), 0) for e in ent]
         K = min(kself + sum(ke), Kc)

@@ -427,8 +427,9 @@ class _CountingAccu:
 def test_accumulator_plan_on_the_host(lib, geom, n, eps):
     """The accumulator H-LU plan (Alg 4-8, piece lists): every low-rank leaf receives in its
     rounded additions exactly the pieces that the oracle's accumulator H-LU hands to it in one
-    apply_upd (counted per leaf), fewer rounded additions than the H-LU of Alg 2, and factors
-    within 10 eps of the exact kernel and within eps of the oracle's accumulator factors."""
+    apply_upd (counted per leaf, through the trees of rounded additions that large stacks
+    take), fewer rounded additions than the H-LU of Alg 2, and factors within 10 eps of the
+    exact kernel and within eps of the oracle's accumulator factors."""
     pts = W.points_for(geom, n, 21)
     hmat = HMatrix(pts, 64, 2.0, eps, 64)
     S = hm.hm_structure_build(pts, 64, 2.0)
@@ -439,12 +440,23 @@ def test_accumulator_plan_on_the_host(lib, geom, n, eps):
     R = _CountingAccu.run(hmat)
     cl = S.export()["clusters"]
     key = {int(lf["off"]): (int(cl[lf["row"], 0]), int(cl[lf["col"], 0])) for lf in P["leaves"] if lf["lr"]}
-    counts = {}
+    # the pieces of every rounded addition, followed through the temporary sums of the trees of
+    # rounded additions (a stack without self writes a sum that a later stack takes as an entry;
+    # scratch addresses repeat from wave to wave, so a sum is identified by wave and address)
     L = P["launches"]
-    for ln in L[L["kind"] == 4]:
-        for op in P["trunc"][ln["begin"]:ln["begin"] + ln["count"]]:
-            k = key[int(op["U"]) & ((1 << 60) - 1)]
-            counts[k] = counts.get(k, 0) + int(op["n_entries"])
+    ops = [(int(ln["wave"]), op) for ln in L[L["kind"] == 4]
+           for op in P["trunc"][ln["begin"]:ln["begin"] + ln["count"]]]
+    ents = lambda op: P["entries"][int(op["first_entry"]):int(op["first_entry"]) + int(op["n_entries"])]
+    sums = {(w, int(op["U"])) for w, op in ops if int(op["flags"]) & 1}
+    assert sums, "no tree of rounded additions in this plan"
+    consumer = {(w, int(e["W"])): q for q, (w, op) in enumerate(ops) for e in ents(op) if (w, int(e["W"])) in sums}
+    counts = {}
+    for w, op in ops:
+        out = op
+        while int(out["flags"]) & 1:
+            out = ops[consumer[(w, int(out["U"]))]][1]
+        k = key[int(out["U"]) & ((1 << 60) - 1)]
+        counts[k] = counts.get(k, 0) + sum(1 for e in ents(op) if (w, int(e["W"])) not in sums)
     assert counts == R.counts
     sim = PlanSim(P["sizes"])
     _load(sim, P["leaves"], hmat.store)
