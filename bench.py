@@ -33,11 +33,12 @@ import numpy as np  # noqa: E402
 import hm_workloads as W  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07       # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# DRAM bytes (read + write) per counted FLOP of a launch, from ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum) of one H-LU step of the n = 32768 sphere: the largest k_gemm launch
-# (8906 micro-ops: 405.4 MB + 20.4 MB for 2.2317 GFLOP) and a k_core launch (6 cores: 285.7 kB for
-# 9.0379 MFLOP). A launch's traffic is taken as this ratio times its FLOPs.
-PROFILED_BYTES_PER_FLOP = {"gemm": (405.352192e6 + 20.44544e6) / 2231684434.0,
+# DRAM bytes (read + write) per counted FLOP, from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum): k_gemm, every launch of one H-LU of the n = 8192 cube (1425 launches,
+# 7279.3 MB + 466.9 MB for 26.04 GFLOP; profiles/k_gemm_dram_cube8192.md); k_core, two launches of
+# the n = 32768 sphere step (6 cores: 285.7 kB for 9.0379 MFLOP). A launch's traffic is taken as
+# this ratio times its FLOPs.
+PROFILED_BYTES_PER_FLOP = {"gemm": (7279340800.0 + 466858496.0) / 26040271168.0,
                            "core": 285696.0 / 9037896.0}
 KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 METRIC = "H-LU factorization seconds at {w}"
@@ -429,8 +430,9 @@ def main():
         traffic = PROFILED_BYTES_PER_FLOP[dom] * kind_fl[dom] / kind_n[dom]
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "traffic_basis": "bytes per launch: ncu DRAM bytes/FLOP of a captured launch (n = 32768 "
-                                 "sphere) x this kernel's average FLOPs per launch",
+                "traffic_basis": "bytes per launch: ncu DRAM bytes/FLOP summed over the kernel's launches "
+                                 "in one H-LU of the n = 8192 cube (k_gemm; k_core: two launches of the "
+                                 "n = 32768 sphere) x this kernel's average FLOPs per launch",
                 "peak_basis": "derived FP64 DFMA peak: 152 SM x 2 FMA/clk x 2 x 2.07 GHz",
                 "launches_per_step": kind_n[dom],
                 "share": kind_ms[dom] / max(sum(kind_ms.values()), 1e-9),

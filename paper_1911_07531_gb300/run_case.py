@@ -2,7 +2,8 @@
 
   python -m paper_1911_07531_gb300.run_case lu GEOMETRY N EPS PRECISION
       builds the H-matrix of the points of `hm_workloads` (seed 31, leaf 64, eta 2, rank cap 64)
-      and runs one hm_lu with HM_PREC_* = PRECISION; prints the device seconds.
+      and runs one hm_lu with HM_PREC_* = PRECISION inside the NVTX range "hm_lu"; prints its
+      device seconds, launches and FLOPs per kernel kind as a JSON line.
   python -m paper_1911_07531_gb300.run_case xmv N
       the cube matrix at eps 1e-6 and two exact-kernel matvecs (HM_OP_EXACT) of one vector.
   python -m paper_1911_07531_gb300.run_case overlap WORKLOAD EPS REPEATS
@@ -31,14 +32,22 @@ KINDS = ("getrf", "trsm", "gemm", "copy", "stack", "core", "eval", "aca")
 
 
 def _lu(geom, n, eps, prec):
+    import torch
+
     import hm_workloads as W
 
     from . import HMContext, build_library, hm_build, hm_lu
     build_library()
     ctx = HMContext(0)
     A = hm_build(ctx, W.points_for(geom, n, 31), 64, 2.0, eps, 64)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("hm_lu")   # profilers can select the factorization's launches
     F = hm_lu(ctx, A, precision=prec)
-    print("ok", F.stats()["seconds"])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    st = F.stats()
+    print(json.dumps({"seconds": st["seconds"], "launches": st["launches"],
+                      "kind_flops": dict(zip(KINDS, st["kind_flops"]))}), flush=True)
 
 
 def _xmv(n):
