@@ -19,6 +19,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <array>
 #include <unordered_map>
 #include <atomic>
 #include <cmath>
@@ -1232,31 +1233,51 @@ void plan_wave_ranges(int nlev, const std::vector<size_t>& tasks_per_wave, int t
 }
 }  // namespace
 
-static LeafEvents leaf_events(const BlockTree& bt, const Layout& lay, const TaskGraph& g) {
-  LeafEvents out(lay.leaf.size());
-  std::vector<int> leaves;
-  auto mark = [&](int r, int c, int lv, int read) {
-    const int id = bt.find(r, c);
-    if (id < 0) return;
-    leaves.clear();
-    collect_leaves(bt, id, leaves);
-    for (int lid : leaves) out[bt.nodes[lid].leaf].push_back({lv, read});
-  };
-  for (size_t i = 0; i < g.nodes.size(); ++i) {
-    const Task& t = g.nodes[i];
-    const int lv = g.level[i];
-    switch (t.type) {
-      case T_LU: mark(t.a, t.a, lv, 1); break;
-      case T_TRSL: mark(t.a, t.b, lv, 1); break;
-      case T_TRSU: mark(t.b, t.a, lv, 1); break;
-      case T_SHIFT:
-      case T_APPLY: mark(t.a, t.b, lv, 1); break;
-      default:
-        mark(t.a, t.b, lv, 1);
-        mark(t.b, t.c, lv, 1);
-        mark(t.a, t.c, lv, 0);
-        break;
+static LeafEvents leaf_events(const BlockTree& bt, const Layout& lay, const TaskGraph& g, int threads) {
+  // ranges of tasks on the host threads, each into its own (leaf, level, read) list; the lists
+  // are then gathered per leaf and sorted (the result does not depend on the thread count)
+  const int nt = plan_threads(threads);
+  const size_t N = g.nodes.size();
+  const int nchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nt * 4, N / 2048 + 1));
+  std::vector<std::vector<std::array<int, 3>>> part(nchunk);
+  std::atomic<int> next{0};
+  run_workers(std::min(nt, nchunk), [&]() {
+    std::vector<int> leaves;
+    for (int k; (k = next.fetch_add(1)) < nchunk;) {
+      auto& out = part[k];
+      auto mark = [&](int r, int c, int lv, int read) {
+        const int id = bt.find(r, c);
+        if (id < 0) return;
+        leaves.clear();
+        collect_leaves(bt, id, leaves);
+        for (int lid : leaves) out.push_back({bt.nodes[lid].leaf, lv, read});
+      };
+      for (size_t i = N * k / nchunk; i < N * (k + 1) / nchunk; ++i) {
+        const Task& t = g.nodes[i];
+        const int lv = g.level[i];
+        switch (t.type) {
+          case T_LU: mark(t.a, t.a, lv, 1); break;
+          case T_TRSL: mark(t.a, t.b, lv, 1); break;
+          case T_TRSU: mark(t.b, t.a, lv, 1); break;
+          case T_SHIFT:
+          case T_APPLY: mark(t.a, t.b, lv, 1); break;
+          default:
+            mark(t.a, t.b, lv, 1);
+            mark(t.b, t.c, lv, 1);
+            mark(t.a, t.c, lv, 0);
+            break;
+        }
+      }
     }
+  });
+  LeafEvents out(lay.leaf.size());
+  {
+    std::vector<size_t> cnt(lay.leaf.size(), 0);
+    for (const auto& p : part)
+      for (const auto& e : p) ++cnt[e[0]];
+    for (size_t l = 0; l < out.size(); ++l) out[l].reserve(cnt[l]);
+    for (const auto& p : part)
+      for (const auto& e : p) out[e[0]].push_back({e[1], e[2]});
   }
   for (auto& v : out) {
     std::sort(v.begin(), v.end());
@@ -1272,7 +1293,7 @@ void plan_lu(const ClusterTree& ct, const BlockTree& bt, const Layout& lay, cons
   std::vector<size_t> per(g.nlevels);
   for (int lv = 0; lv < g.nlevels; ++lv) per[lv] = byl[lv].size();
   LeafEvents events;
-  if (defer || accumulate) events = leaf_events(bt, lay, g);
+  if (defer || accumulate) events = leaf_events(bt, lay, g, threads);
   // a leaf is touched at a level when any task of that level reads or updates it
   auto touched_at = [&](int leaf, int lv) {
     const auto& v = events[leaf];

@@ -135,15 +135,17 @@ def test_plan_export_errors(lib):
 
 def test_parallel_planner_equals_sequential(lib):
     """Ranges of waves planned on several host threads and concatenated give the sequential plan
-    byte for byte (launch list, every micro-op table, sizes)."""
+    byte for byte (launch list, every micro-op table, sizes), with and without the wave overlap
+    (whose leaf-event analysis also runs on the host threads)."""
     S = hm.hm_structure_build(W.fibonacci_sphere(8192, 21), 64, 2.0)
-    ref = S.plan(0, 1e-6, 64, threads=1)
-    assert ref["sizes"]["nwaves"] >= 64
-    for t in (3, 8):
-        P = S.plan(0, 1e-6, 64, threads=t)
-        for name in ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves"):
-            assert P[name].tobytes() == ref[name].tobytes(), (t, name)
-        assert P["sizes"].tobytes() == ref["sizes"].tobytes()
+    for which in (0, 7):
+        ref = S.plan(which, 1e-6, 64, threads=1)
+        assert ref["sizes"]["nwaves"] >= 64
+        for t in (3, 8):
+            P = S.plan(which, 1e-6, 64, threads=t)
+            for name in ("launches", "getrf", "trsm", "gemm", "copy", "trunc", "entries", "leaves"):
+                assert P[name].tobytes() == ref[name].tobytes(), (which, t, name)
+            assert P["sizes"].tobytes() == ref["sizes"].tobytes()
 
 
 def test_parallel_task_graph_equals_serial(lib):
