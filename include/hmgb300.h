@@ -81,6 +81,12 @@ typedef struct {
                         [HM_EPS_MIN, 1) (default 1e-6)                                  */
   int rank_cap;      /* maximal rank of a low-rank block, 1..64 (default 64)            */
   double kernel_h;   /* regularisation h of 1/(4 pi (r + h)); <= 0: mean NN spacing     */
+  int prepare_lu;    /* 1: while the device assembles the matrix, a host thread builds the
+                        task graph (Alg 11) and the H-LU plan for hm_lu's defaults (the
+                        matrix's eps, FP64, no accumulators, the current hm_set_overlap and
+                        GEMM settings), so that a following hm_lu starts launching at once;
+                        any later call on the matrix waits for that thread. 0 (default):
+                        hm_lu builds them.                                                */
 } hm_build_opts;
 
 /* Arithmetic of hm_lu (hm_lu_opts.precision).

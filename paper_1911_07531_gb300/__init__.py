@@ -48,7 +48,7 @@ class HMError(RuntimeError):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("eta", ctypes.c_double), ("eps", ctypes.c_double),
-                ("rank_cap", ctypes.c_int), ("kernel_h", ctypes.c_double)]
+                ("rank_cap", ctypes.c_int), ("kernel_h", ctypes.c_double), ("prepare_lu", ctypes.c_int)]
 
 
 class LuOpts(ctypes.Structure):
@@ -314,12 +314,13 @@ class HFactor:
             pass
 
 
-def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h=-1.0):
-    """H-matrix of a_ij = 1/(4 pi (|x_i - x_j| + h)) for host points (n x 3 float64)."""
+def hm_build(ctx, points, leaf_size=64, eta=2.0, eps=1e-6, rank_cap=64, kernel_h=-1.0, prepare_lu=False):
+    """H-matrix of a_ij = 1/(4 pi (|x_i - x_j| + h)) for host points (n x 3 float64);
+    prepare_lu: plan the H-LU on a host thread while the device assembles the matrix."""
     p = np.ascontiguousarray(points, dtype=np.float64)
     if p.ndim != 2 or p.shape[1] != 3:
         raise ValueError("points must be n x 3")
-    o = BuildOpts(int(leaf_size), float(eta), float(eps), int(rank_cap), float(kernel_h))
+    o = BuildOpts(int(leaf_size), float(eta), float(eps), int(rank_cap), float(kernel_h), int(bool(prepare_lu)))
     h = ctypes.c_void_p()
     _check(load_library().hm_build(ctx.handle, p.ctypes.data, p.shape[0], ctypes.byref(o), ctypes.byref(h)))
     return HMatrix(ctx, h, p.shape[0])

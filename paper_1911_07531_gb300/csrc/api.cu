@@ -12,6 +12,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hmgb300.h"
@@ -326,6 +327,10 @@ struct hm_matrix {
   Buf mv_work;
   double build_seconds = 0.0;
   int64_t aca_unconverged = 0;
+  // host preparation of the H-LU started by hm_build (task graph and plan at the matrix's eps,
+  // FP64, the current overlap and GEMM settings) while the device assembles the matrix; every
+  // reader of dag / lu_plan joins it first
+  std::thread prep;
 };
 
 // One allocation of factor values, ranks and pivots shared by the factors of a batch
@@ -351,7 +356,35 @@ namespace {
 
 constexpr int SOLVE_CHUNK = 32;
 
+// task graph and H-LU plan of A for the defaults of hm_lu (the matrix's eps, FP64, no
+// accumulators), on the host; on any failure nothing is kept and hm_lu plans (and reports) itself
+void prep_lu(hm_matrix* A, int ov) {
+  try {
+    build_task_graph(A->ct, A->bt, A->dag, false, g_host_threads.load());
+    if (!compute_levels(A->dag)) return;
+    A->dag_built = true;
+    auto t0 = std::chrono::steady_clock::now();
+    plan_lu(A->ct, A->bt, A->lay, A->dag, A->opts.eps, A->lu_plan.host, g_host_threads.load(), HM_PREC_FP64,
+            ov != 0, false);
+    A->lu_plan.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    A->lu_plan.eps = A->opts.eps;
+    A->lu_plan.precision = HM_PREC_FP64;
+    A->lu_plan.gemm_work = gemm_min_work();
+    A->lu_plan.overlap = ov;
+    A->lu_plan.accumulate = 0;
+  } catch (...) {
+    A->lu_plan.host = Plan();
+    A->lu_plan.eps = -1.0;
+  }
+}
+
+void prep_join(const hm_matrix* A) {
+  hm_matrix* M = const_cast<hm_matrix*>(A);
+  if (M->prep.joinable()) M->prep.join();
+}
+
 void fill_matrix_stats(const hm_matrix* A, hm_stats* s) {
+  prep_join(A);
   std::memset(s, 0, sizeof(*s));
   s->n = A->n;
   s->nclusters = (int64_t)A->ct.cl.size();
@@ -480,7 +513,7 @@ int hm_ctx_set_profiling(hm_ctx* c, int enable) {
 int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm_matrix** out) {
   if (!c || !pts || !out) return fail(HM_EINVAL, "hm_build: NULL argument");
   if (n < 1 || n > (int64_t)1 << 30) return fail(HM_EINVAL, "hm_build: n out of range");
-  hm_build_opts opts{64, 2.0, 1e-6, 64, -1.0};
+  hm_build_opts opts{64, 2.0, 1e-6, 64, -1.0, 0};
   if (o) opts = *o;
   if (opts.leaf_size < 1 || opts.leaf_size > 64) return fail(HM_EINVAL, "hm_build: leaf_size must be in 1..64");
   if (!(opts.eta >= 0.0)) return fail(HM_EINVAL, "hm_build: eta must be >= 0");
@@ -500,6 +533,7 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
     return fail(HM_EINTERNAL, std::string("hm_build: ") + ex.what());
   }
   auto cleanup = [&](int rc) {
+    prep_join(A.get());
     dfree(c, A->perm);
     dfree(c, A->pts);
     dfree(c, A->pts_orig);
@@ -511,6 +545,14 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
       !dalloc(c, A->pts_orig, n * 3 * sizeof(double)) || !dalloc(c, A->vals, A->lay.nvalues * sizeof(double)) ||
       !dalloc(c, A->ranks, std::max(1, A->lay.nranks) * sizeof(int)))
     return cleanup(fail(HM_ENOMEM, "hm_build: allocator returned NULL"));
+  // the H-LU's host preparation needs only the trees and the layout: it runs beside the assembly
+  if (opts.prepare_lu) {
+    try {
+      A->prep = std::thread(prep_lu, A.get(), g_overlap.load());
+    } catch (...) {
+      // no thread: hm_lu plans itself
+    }
+  }
   cudaStream_t s = c->stream;
   int rc = HM_OK;
   cudaEvent_t e0, e1;
@@ -612,6 +654,7 @@ int hm_build(hm_ctx* c, const double* pts, int64_t n, const hm_build_opts* o, hm
 
 void hm_matrix_free(hm_matrix* A) {
   if (!A) return;
+  prep_join(A);
   hm_ctx* c = A->ctx;
   free_plan(c, A->lu_plan);
   free_plan(c, A->mv_plan);
@@ -634,6 +677,7 @@ int hm_lu(hm_ctx* c, hm_matrix* A, const hm_lu_opts* o, hm_factor** out) {
     return fail(HM_EINVAL, "hm_lu: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");
   const int accumulate = o ? o->accumulate : 0;
   if (accumulate != 0 && accumulate != 1) return fail(HM_EINVAL, "hm_lu: accumulate must be 0 or 1");
+  prep_join(A);
   CU(cudaSetDevice(c->device));
   try {
     if (!A->dag_built) {
@@ -784,6 +828,7 @@ int hm_lu_batch(hm_ctx* c, hm_matrix* const* A, int count, const hm_lu_opts* o, 
     if (!A[i]) return fail(HM_EINVAL, "hm_lu_batch: NULL matrix");
     out[i] = nullptr;
   }
+  for (int i = 0; i < count; ++i) prep_join(A[i]);
   const int precision = o ? o->precision : HM_PREC_FP64;
   if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED && precision != HM_PREC_MIXED_TC)
     return fail(HM_EINVAL, "hm_lu_batch: precision must be HM_PREC_FP64, HM_PREC_MIXED or HM_PREC_MIXED_TC");

@@ -404,3 +404,34 @@ def test_wave_overlap_matches_sequential(ctx, hm):
     ref = out[(0, False)]   # rank decisions near eps may differ with the accumulation order
     assert fro_ratio(out[(1, False)] - ref, Ax) <= eps
     assert fro_ratio(out[(1, True)] - ref, Ax) <= eps
+
+
+# ------------------------------------------------------------------ H-LU prepared during the build
+def test_prepare_lu_during_build(ctx, hm):
+    """hm_build with prepare_lu plans the H-LU on a host thread during the assembly: hm_lu then
+    factors with that plan (no planning left: its plan time is the thread's), the factor equals
+    one planned by hm_lu itself within rounding of the atomic accumulations, a different eps
+    re-plans, and freeing the matrix without factoring it waits for the thread."""
+    n, eps = 4096, 1e-6
+    p = W.fibonacci_sphere(n, 9)
+    X = np.random.default_rng(8).standard_normal((n, 3))
+    A0 = hm.hm_build(ctx, p, 64, 2.0, eps, 64)
+    A1 = hm.hm_build(ctx, p, 64, 2.0, eps, 64, prepare_lu=True)
+    s1 = A1.stats()   # waits for the preparation
+    assert s1["dag_levels"] > 0 and s1["plan_launches"] > 0
+    F0, F1 = hm.hm_lu(ctx, A0), hm.hm_lu(ctx, A1)
+    assert F1.stats()["plan_launches"] == F0.stats()["plan_launches"]
+    Xd = dev(X)
+    Ax = host(hm.hm_matvec(ctx, A0, hm.HM_OP_EXACT, Xd))
+    y0 = host(hm.hm_matvec(ctx, A0, hm.HM_OP_LU, Xd, F=F0))
+    y1 = host(hm.hm_matvec(ctx, A1, hm.HM_OP_LU, Xd, F=F1))
+    assert fro_ratio(y1 - Ax, Ax) <= 10 * eps
+    assert fro_ratio(y1 - y0, Ax) <= eps
+    F2 = hm.hm_lu(ctx, A1, eps=1e-4)   # another eps: planned again
+    assert fro_ratio(host(hm.hm_matvec(ctx, A1, hm.HM_OP_LU, Xd, F=F2)) - Ax, Ax) <= 1e-3
+    for F in (F0, F1, F2):
+        F.free()
+    A0.free()
+    A1.free()
+    A3 = hm.hm_build(ctx, p, 64, 2.0, eps, 64, prepare_lu=True)
+    A3.free()   # joins the preparation thread
