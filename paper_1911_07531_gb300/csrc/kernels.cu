@@ -998,8 +998,12 @@ __device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol
 // more accurate than QR", 1992). Round-robin pairing; one half-warp (16 lanes) handles one pair
 // of a round, so a block of 512 threads runs all pairs of a round concurrently for cols <= 64,
 // and a round costs one block barrier.
-__device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
-                                    int max_sweeps) {
+// NR: entries per lane of a column (rows <= 16 NR). A lane keeps its entries of the pair's two
+// columns in registers from the dot products to the rotation: one load pass per round, and no
+// store waits for a later load (the arithmetic is that of a load-compute-store pass).
+template <int NR>
+__device__ void onesided_jacobi_f32_t(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
+                                      int max_sweeps) {
   const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
   const unsigned hmask = 0xffffu << (threadIdx.x & 16);
   const int half = cols / 2;
@@ -1023,12 +1027,19 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
         const int a = min(x, y), b = max(x, y);
         float* ga = G + a * ldg;
         float* gb = G + b * ldg;
+        float u[NR], v[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          const int l = hl + 16 * k;
+          u[k] = l < rows ? ga[l] : 0.f;
+          v[k] = l < rows ? gb[l] : 0.f;
+        }
         float al = 0.f, be = 0.f, ga_b = 0.f;
-        for (int l = hl; l < rows; l += 16) {
-          const float u = ga[l], v = gb[l];
-          al = fmaf(u, u, al);
-          be = fmaf(v, v, be);
-          ga_b = fmaf(u, v, ga_b);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          al = fmaf(u[k], u[k], al);
+          be = fmaf(v[k], v[k], be);
+          ga_b = fmaf(u[k], v[k], ga_b);
         }
         for (int o = 8; o > 0; o >>= 1) {
           al += __shfl_xor_sync(hmask, al, o);
@@ -1052,18 +1063,21 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
           }
           const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
           if (s != 0.f) {
-            for (int l = hl; l < rows; l += 16) {
-              const float u = ga[l], v = gb[l];
-              ga[l] = c * u - s * v;
-              gb[l] = s * u + c * v;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+              const int l = hl + 16 * k;
+              if (l < rows) {
+                ga[l] = c * u[k] - s * v[k];
+                gb[l] = s * u[k] + c * v[k];
+              }
             }
             if (V) {
               float* va = V + a * ldv;
               float* vb = V + b * ldv;
               for (int l = hl; l < cols; l += 16) {
-                const float u = va[l], v = vb[l];
-                va[l] = c * u - s * v;
-                vb[l] = s * u + c * v;
+                const float p0 = va[l], p1 = vb[l];
+                va[l] = c * p0 - s * p1;
+                vb[l] = s * p0 + c * p1;
               }
             }
             if (hl == 0 && fabsf(gn) > tol_next) *flag = 1;
@@ -1078,6 +1092,87 @@ __device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float
 #ifdef HM_CORE_TIMING
   if (threadIdx.x == 0) g_core_stamp[15] = sweep;
 #endif
+}
+
+// NR = 0: columns of any length, loaded again for the rotation (no register copy)
+template <>
+__device__ void onesided_jacobi_f32_t<0>(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
+                                         int max_sweeps) {
+  const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
+  const unsigned hmask = 0xffffu << (threadIdx.x & 16);
+  const int half = cols / 2;
+  const float tol = fmaxf(1e-6f, 6e-8f * (float)rows);
+  const float tol_next = sqrtf(tol);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int r = 0; r < cols - 1; ++r) {
+      for (int q = hw; q < half; q += nh) {
+        int x = q - 1 + r, y = cols - 2 - q + r;
+        x = x >= cols - 1 ? x - (cols - 1) : x;
+        y = y >= cols - 1 ? y - (cols - 1) : y;
+        x = q == 0 ? 0 : 1 + x;
+        y = 1 + y;
+        const int a = min(x, y), b = max(x, y);
+        float* ga = G + a * ldg;
+        float* gb = G + b * ldg;
+        float al = 0.f, be = 0.f, ga_b = 0.f;
+        for (int l = hl; l < rows; l += 16) {
+          const float u = ga[l], v = gb[l];
+          al = fmaf(u, u, al);
+          be = fmaf(v, v, be);
+          ga_b = fmaf(u, v, ga_b);
+        }
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(hmask, al, o);
+          be += __shfl_xor_sync(hmask, be, o);
+          ga_b += __shfl_xor_sync(hmask, ga_b, o);
+        }
+        const float rab = (al > 0.f && be > 0.f) ? rsqrtf(al) * rsqrtf(be) : 0.f;
+        const float gn = ga_b * rab, dn = (be - al) * rab;
+        if (fabsf(gn) > tol) {
+          const float th = __fdividef(dn, 2.0f * gn);
+          float t;
+          if (!(fabsf(th) < 1e18f)) t = 0.0f;
+          else {
+            const float h = fmaf(th, th, 1.0f);
+            t = copysignf(__fdividef(1.0f, fabsf(th) + h * rsqrtf(h)), th);
+          }
+          const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+          if (s != 0.f) {
+            for (int l = hl; l < rows; l += 16) {
+              const float u = ga[l], v = gb[l];
+              ga[l] = c * u - s * v;
+              gb[l] = s * u + c * v;
+            }
+            if (V) {
+              float* va = V + a * ldv;
+              float* vb = V + b * ldv;
+              for (int l = hl; l < cols; l += 16) {
+                const float p0 = va[l], p1 = vb[l];
+                va[l] = c * p0 - s * p1;
+                vb[l] = s * p0 + c * p1;
+              }
+            }
+            if (hl == 0 && fabsf(gn) > tol_next) *flag = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (*flag == 0) break;
+    __syncthreads();
+  }
+#ifdef HM_CORE_TIMING
+  if (threadIdx.x == 0) g_core_stamp[15] = sweep;
+#endif
+}
+
+__device__ void onesided_jacobi_f32(float* G, int ldg, int rows, int cols, float* V, int ldv, int* flag,
+                                    int max_sweeps) {
+  if (rows <= 64) onesided_jacobi_f32_t<4>(G, ldg, rows, cols, V, ldv, flag, max_sweeps);
+  else onesided_jacobi_f32_t<0>(G, ldg, rows, cols, V, ldv, flag, max_sweeps);
 }
 
 // Back substitution Rf11 x = y for the NQ columns y_c (c = warp + nw q) of Y owned by one warp,
