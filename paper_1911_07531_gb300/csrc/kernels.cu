@@ -686,11 +686,16 @@ __global__ void __launch_bounds__(256) k_copy(const CopyOp* __restrict__ ops, Ba
 // ------------------------------------------------------------------------------ STACK
 __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
                                                const StackEntry* __restrict__ ent, Bases B) {
-  // CTA (op, y) copies rows [y m / Y, (y + 1) m / Y) of the stacked left factor and the same
+  // CTA (op, y) copies rows [y m / Y, (y + 1) m / Y) of the stacked left factor (Y: its share of
+  // the launch's CTAs, from its size) and the same
   // share of the right factor's rows; every CTA derives the column layout itself, CTA y = 0 also
   // publishes the stacked rank and clears the Gram matrices.
   const TruncOp op = ops[blockIdx.x];
   const int m = op.m, n = op.n, Kc = op.Kcap, tid = threadIdx.x;
+  // this rounded addition's share of the launch's CTAs along the rows: ~16k copied doubles each
+  // (the launch is sized for its largest one; the others leave the surplus CTAs at once)
+  const int ny = (int)min((int64_t)gridDim.y, max((int64_t)1, (int64_t)(m + n) * Kc / 16384));
+  if ((int)blockIdx.y >= ny) return;
   const int kself = (op.flags & TF_NOSELF) ? 0 : *iptr(B, op.rank);
   const int ne = min(op.n_entries, KMAX_ENTRIES);
   __shared__ int s_ke[KMAX_ENTRIES], s_col[KMAX_ENTRIES], s_K;
@@ -726,7 +731,7 @@ __global__ void __launch_bounds__(256) k_stack(const TruncOp* __restrict__ ops,
       Gz[i + (int64_t)j * Kc] = 0.0;
     }
   }
-  const int ny = gridDim.y, y = blockIdx.y;
+  const int y = blockIdx.y;
   const int w0 = (int)((int64_t)m * y / ny), wl = (int)((int64_t)m * (y + 1) / ny) - w0;
   const int z0 = (int)((int64_t)n * y / ny), zl = (int)((int64_t)n * (y + 1) / ny) - z0;
   const double* U = dptr(B, op.U);
