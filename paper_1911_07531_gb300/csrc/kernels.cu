@@ -1003,6 +1003,24 @@ __device__ int pivoted_cholesky(double* A, int lda, int n, int* perm, double tol
 // more accurate than QR", 1992). Round-robin pairing; one half-warp (16 lanes) handles one pair
 // of a round, so a block of 512 threads runs all pairs of a round concurrently for cols <= 64,
 // and a round costs one block barrier.
+// Rotation (c, s) of the one-sided Jacobi that orthogonalises two columns with squared norms al,
+// be and dot product g: tan 2 theta = 2 g / (al - be), and t = tan theta is the smaller root,
+// t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)) with d = be - al (the usual choice, written without
+// the quotient zeta = d / (2 g)). d and g are first scaled by the power of two that brings
+// max(al, be) into [1, 2) (exact), so d^2 + 4 g^2 stays in range; the chain has three dependent
+// special-function operations (square root, reciprocal, reciprocal square root).
+__device__ __forceinline__ void jacobi_cs(float al, float be, float g, float& c, float& s) {
+  const float mx = fmaxf(al, be);
+  const int ex = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+  const float sc = __int_as_float((127 - ex) << 23);
+  const float d = (be - al) * sc, gg = g * sc;
+  const float den = fabsf(d) + sqrtf(fmaf(d, d, 4.0f * gg * gg));
+  float t = den > 0.f ? __fdividef(2.0f * gg, den) : 0.f;
+  t = d < 0.f ? -t : t;
+  c = rsqrtf(fmaf(t, t, 1.0f));
+  s = t * c;
+}
+
 // NR: entries per lane of a column (rows <= 16 NR). A lane keeps its entries of the pair's two
 // columns in registers from the dot products to the rotation: one load pass per round, and no
 // store waits for a later load (the arithmetic is that of a load-compute-store pass).
@@ -1051,22 +1069,15 @@ __device__ void onesided_jacobi_f32_t(float* G, int ldg, int rows, int cols, flo
           be += __shfl_xor_sync(hmask, be, o);
           ga_b += __shfl_xor_sync(hmask, ga_b, o);
         }
-        // normalised quantities: gn = cos of the pair's angle, dn = (|b|^2 - |a|^2) / (|a| |b|)
+        // gn = cos of the pair's angle (the convergence test; the rotation uses al, be, ga_b)
         const float rab = (al > 0.f && be > 0.f) ? rsqrtf(al) * rsqrtf(be) : 0.f;
-        const float gn = ga_b * rab, dn = (be - al) * rab;
+        const float gn = ga_b * rab;
 #ifdef HM_CORE_TIMING
         if (hl == 0 && sweep < 8) atomicMax(&g_jac_maxcos[sweep], __float_as_int(fabsf(gn)));
 #endif
         if (fabsf(gn) > tol) {
-          // tan 2 theta = 2 g / (|a|^2 - |b|^2); t = tan theta of the smaller root
-          const float th = __fdividef(dn, 2.0f * gn);
-          float t;
-          if (!(fabsf(th) < 1e18f)) t = 0.0f;
-          else {
-            const float h = fmaf(th, th, 1.0f);
-            t = copysignf(__fdividef(1.0f, fabsf(th) + h * rsqrtf(h)), th);
-          }
-          const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+          float c, s;
+          jacobi_cs(al, be, ga_b, c, s);
           if (s != 0.f) {
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
@@ -1135,16 +1146,10 @@ __device__ void onesided_jacobi_f32_t<0>(float* G, int ldg, int rows, int cols, 
           ga_b += __shfl_xor_sync(hmask, ga_b, o);
         }
         const float rab = (al > 0.f && be > 0.f) ? rsqrtf(al) * rsqrtf(be) : 0.f;
-        const float gn = ga_b * rab, dn = (be - al) * rab;
+        const float gn = ga_b * rab;
         if (fabsf(gn) > tol) {
-          const float th = __fdividef(dn, 2.0f * gn);
-          float t;
-          if (!(fabsf(th) < 1e18f)) t = 0.0f;
-          else {
-            const float h = fmaf(th, th, 1.0f);
-            t = copysignf(__fdividef(1.0f, fabsf(th) + h * rsqrtf(h)), th);
-          }
-          const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+          float c, s;
+          jacobi_cs(al, be, ga_b, c, s);
           if (s != 0.f) {
             for (int l = hl; l < rows; l += 16) {
               const float u = ga[l], v = gb[l];
