@@ -670,9 +670,7 @@ __global__ void __launch_bounds__(256) k_copy(const CopyOp* __restrict__ ops, Ba
   double* dst = dptr(B, op.dst);
   const int64_t tot = (int64_t)m * n;
   const bool i_fast = op.d_rs <= op.d_cs;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    int i, j;
-    if (i_fast) { i = (int)(e % m); j = (int)(e / m); } else { j = (int)(e % n); i = (int)(e / n); }
+  auto put = [&](int i, int j) {
     double* d = dst + (int64_t)i * op.d_rs + (int64_t)j * op.d_cs;
     switch (op.mode) {
       case CM_ZERO: *d = 0.0; break;
@@ -680,6 +678,20 @@ __global__ void __launch_bounds__(256) k_copy(const CopyOp* __restrict__ ops, Ba
       case CM_COPY: *d = op.alpha * src[(int64_t)i * op.s_rs + (int64_t)j * op.s_cs]; break;
       default: *d += op.alpha * src[(int64_t)i * op.s_rs + (int64_t)j * op.s_cs]; break;
     }
+  };
+  if (tot <= 0x7fffffff) {   // 32-bit index arithmetic (64-bit division is a long software sequence)
+    const unsigned t = (unsigned)tot, fm = (unsigned)(i_fast ? m : n);
+    for (unsigned e = threadIdx.x; e < t; e += blockDim.x) {
+      const unsigned q = e / fm, r = e - q * fm;
+      if (i_fast) put((int)r, (int)q);
+      else put((int)q, (int)r);
+    }
+    return;
+  }
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    int i, j;
+    if (i_fast) { i = (int)(e % m); j = (int)(e / m); } else { j = (int)(e % n); i = (int)(e / n); }
+    put(i, j);
   }
 }
 
