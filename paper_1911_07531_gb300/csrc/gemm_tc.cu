@@ -6,18 +6,17 @@
 // a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs; the dropped a_lo b_lo term is ~2^-22 |a| |b|),
 // which keeps about FP32 accuracy (~1e-6 relative to |A| |B| over the reductions of an H-LU).
 //
-// One CTA (256 threads) computes one 128 x 64 tile of C for one micro-op:
-//   - the CTA's 64 TMEM columns hold the 128 x 64 FP32 accumulator (lane = row);
-//   - for every slice of 32 reduction steps all threads read the FP64 operands from global
-//     memory (any strides), split them and store them in shared memory in the K-major,
-//     unswizzled core-matrix layout the MMA reads (8 rows x 16 bytes per core matrix; core
-//     matrices along K 128 bytes apart, groups of 8 rows 1024 bytes apart), into one of two
-//     stage buffers;
-//   - one thread issues the 4 x 3 MMAs of the slice and commits them to the stage's mbarrier;
-//     a stage is refilled only after that commit completed (bounded wait), so the staging of
-//     slice s overlaps the MMAs of slice s - 1;
-//   - accumulating (atomic) micro-ops with long reductions spread their slices over blockIdx.z
-//     (at most 4 slices per CTA), each CTA adding its partial tile atomically;
+// A persistent grid (at most two CTAs of 256 threads per SM) walks the micro-ops; a CTA computes
+// all 128 x 64 C tiles of its micro-op in turn:
+//   - the CTA's 64 TMEM columns hold the 128 x 64 FP32 accumulator of the current tile
+//     (lane = row);
+//   - for every slice of 64 reduction steps all threads read the FP64 operands from global
+//     memory (any strides; groups of eight independent loads), split them and store them in
+//     shared memory in the K-major, unswizzled core-matrix layout the MMA reads (8 rows x 16
+//     bytes per core matrix; core matrices along K 128 bytes apart, groups of 8 rows 1024 bytes
+//     apart), in one stage buffer;
+//   - one thread issues the 8 x 3 MMAs of the slice and commits them to the stage's mbarrier;
+//     the stage is refilled only after that commit completed (bounded wait);
 //   - the 8 warps read the accumulator back (warp w: lanes 32 (w % 4).., columns 32 (w / 4)..)
 //     and apply alpha and the micro-op's write mode (atomic add, overwrite, or add).
 // A wait that does not end within its bound sets status[4] (the host reports HM_ETIMEOUT), the
