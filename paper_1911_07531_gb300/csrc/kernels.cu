@@ -237,6 +237,11 @@ __device__ __forceinline__ float f64_to_f32(double x) {
 template <typename CT>
 __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ ops, Bases B) {
   constexpr bool F32 = sizeof(CT) == 4;
+  // CTAs beyond this micro-op's budget (the launch is sized for its largest) leave before any
+  // other load
+  const int split = ops[blockIdx.x].split;
+  const int budget = max(1, split & 0xffff) * max(1, split >> 16);
+  if ((int)blockIdx.y >= budget) return;
   const GemmOp op = ops[blockIdx.x];
   const int m = dimv(B, op.m, op.md), n = dimv(B, op.n, op.nd), k = max(dimv(B, op.k, op.kd), 0);
   const bool atomic = op.flags & GF_ATOMIC, overwrite = op.flags & GF_OVERWRITE;
@@ -249,7 +254,6 @@ __global__ void __launch_bounds__(256, 3) k_gemm_t(const GemmOp* __restrict__ op
   // per CTA for the actual sizes and factored here into C tiles (sy) times reduction slices (sz,
   // atomic micro-ops only), sy * sz <= budget. The factoring follows the actual sizes, so a Gram
   // product whose dynamic K x K output fits in a few tiles spreads its rows over the slices.
-  const int budget = max(1, op.split & 0xffff) * max(1, op.split >> 16);
   const double work = (double)m * n * max(k, 1);
   const double per_cta = B.gemm_work > 0.f ? (double)B.gemm_work : 4096.0;
   const int want = min(budget, max(1, (int)ceil(work / per_cta)));
